@@ -1,0 +1,351 @@
+"""Throughput of the fused curvilinear LBM update on GB300.
+
+Workload (default): circular Couette flow in the annulus 1 <= r <= 2 with the
+App. C contracted radial grid (CR = 0.35), D2Q21, FP32 compute and storage,
+N_r x N_theta = 1024 x 4096, inner wall at u_theta = 0.01, outer wall at rest,
+tau = 0.8, from rest.  One bench step = `--chunk` time steps of the whole hot
+path (boundary fill + fused stream-collide-force per time step) followed by
+one residual / conservation reduction.  Metric: million lattice-cell updates
+per second (MLUPS), whole job over all ranks.
+
+The state (2 x 352 MB) is larger than the 129 MB L2, so no flush is needed
+between steps.  Under torchrun every rank advances its own replica (weak
+scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle instead (the only reference this
+paper has): each of its steps is one oracle time step of the same annulus at
+a bounded size.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import clbm_inputs as I  # noqa: E402
+
+WORKLOADS = {
+    # name: (Q, precision, n1, n2, R1, R2, CR, tau, u_wall)
+    "circular_couette_d2q21_fp32_1024x4096": (21, "fp32", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "circular_couette_d2q21_f16_1024x4096": (21, "fp16", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "circular_couette_d2q21_bf16_1024x4096": (21, "bf16", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "circular_couette_d2q21_fp64_1024x4096": (21, "fp64", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "circular_couette_d2q9_fp32_1024x4096": (9, "fp32", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "circular_couette_d2q21_fp32_128x512": (21, "fp32", 128, 512, 1.0, 2.0, 0.35, 0.8, 0.01),
+}
+DEFAULT = "circular_couette_d2q21_fp32_1024x4096"
+METRIC = "D2Q21 curvilinear MLUPS and % HBM roofline; served solves/s, p99 latency"
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+KERNEL_SOURCES = ["paper_2301_01868_gb300/csrc/k_step.cu",
+                  "paper_2301_01868_gb300/csrc/clbm_cell.cuh",
+                  "paper_2301_01868_gb300/csrc/clbm_internal.cuh",
+                  "paper_2301_01868_gb300/csrc/clbm_lattice.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(workload):
+    """Per-launch DRAM bytes of the fused kernel from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smi_index(local):
+    """nvidia-smi index (or UUID) of this rank's GPU."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if not vis:
+        return local
+    return vis.split(",")[local].strip()
+
+
+def annulus(wl):
+    Q, prec, n1, n2, R1, R2, CR, tau, uw = WORKLOADS[wl]
+    e = I.polar_edges(R1, R2, n1, CR)
+    dx = (R2 - R1) / n1
+    U0 = uw * dx / (R1 * math.sin(2.0 * math.pi / n2))
+    return Q, prec, n1, n2, e, tau, U0
+
+
+def cpu_baseline(wl, target_s=12.0, max_steps=50):
+    """The FP64 oracle as it stands on this host's cores: MLUPS on the full
+    workload grid, as many whole time steps as fit in about target_s."""
+    from oracle import oracle as O
+    Q, prec, n1, n2, e, tau, U0 = annulus(wl)
+    o = O.Grid(Q, n1, n2, O.POLAR, edges=e, bc_lo=O.MOVING, bc_hi=O.NOSLIP)
+    o.set_case(tau, 1.0, U0, 0.0)
+    o.init_rest()
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(max_steps, int(target_s / max(t1, 1e-9)) - 1))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    steps = n
+    return {"value": n1 * n2 * steps / dt / 1e6, "unit": "MLUPS", "cores": O.threads(),
+            "kind": "oracle",
+            "sample": "%d time steps of the full %dx%d D2Q21 FP64 oracle grid (%.1f s), "
+                      "after one untimed step" % (steps, n1, n2, dt)}
+
+
+def run_reference(args):
+    """--impl reference: the oracle, each step one time step of the same
+    annulus at 128 x 512 (a bounded sample of the workload)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    wl = args.workload
+    Q, prec, _, _, R1, R2, CR, tau, uw = WORKLOADS[wl]
+    n1, n2 = 128, 512
+    e = I.polar_edges(R1, R2, n1, CR)
+    U0 = uw * ((R2 - R1) / n1) / (R1 * math.sin(2.0 * math.pi / n2))
+    o = O.Grid(Q, n1, n2, O.POLAR, edges=e, bc_lo=O.MOVING, bc_hi=O.NOSLIP)
+    o.set_case(tau, 1.0, U0, 0.0)
+    o.init_rest()
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n1 * n2 * args.steps / dt / 1e6
+    cfg = config_of(wl, args)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
+                            "sample": "%d oracle time steps of the same annulus at %dx%d"
+                                      % (args.steps, n1, n2)},
+           "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def config_of(wl, args):
+    Q, prec, n1, n2, R1, R2, CR, tau, uw = WORKLOADS[wl]
+    return {"workload": wl, "lattice": "D2Q%d" % Q, "n1": n1, "n2": n2, "geometry":
+            "annulus R2/R1=%g, radial CR=%g" % (R2 / R1, CR), "tau": tau, "u_wall": uw,
+            "storage": prec, "chunk": args.chunk,
+            "l2": "inputs larger than L2 (state %d MB)" % (2 * Q * n1 * n2 * STORAGE_BYTES[prec] >> 20),
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=100, help="time steps per bench step")
+    ap.add_argument("--impl", default="clbm", choices=["clbm", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2301_01868_gb300 import clbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = args.workload
+    Q, prec, n1, n2, e, tau, U0 = annulus(wl)
+    stream = torch.cuda.Stream()
+    g = clbm.Grid(Q, n1, n2, e, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING,
+                  bc_hi=clbm.NOSLIP, device=local, stream=stream)
+    g.set_case(tau, 1.0, U0, 0.0)
+
+    def bench_step():
+        g.step(args.chunk)
+        return g.residual()
+
+    for _ in range(args.warmup):
+        bench_step()
+    clocks = Clocks(smi_index(local))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.set_profiling(True)
+    launches0 = g.launch_count()
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        last = bench_step()
+    ev1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    launches = g.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    kms, kl = g.kernel_time()
+    g.set_profiling(False)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    cells = n1 * n2
+    upd = cells * args.chunk * args.steps * world
+    value = upd / (ms_max * 1e-3) / 1e6
+    sb = STORAGE_BYTES[prec]
+    bytes_per_launch = 2 * Q * sb * cells
+    achieved = bytes_per_launch / (kms / kl * 1e-3) / 1e9 if kl else None
+    peak, peak_src = peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic_for(wl),
+            "peak_source": peak_src + " (hbm_gbs)", "algorithmic_bytes_per_launch": bytes_per_launch,
+            "kernel_ms_avg": kms / kl if kl else None}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(g, args, torch, stream, world, dist, cells, Q)
+
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 compute, f16 storage",
+                     "bf16": "f32 compute, bf16 storage"}[prec],
+           "data": "synthetic", "config": config_of(wl, args), "roofline": roof,
+           "gpu_launches": launches, "clocks": ck, "e2e": e2e,
+           "residual_last": last[0] if last else None}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(out))
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_e2e(g, args, torch, stream, world, dist, cells, Q):
+    """Same metric through the public API with host buffers: every step
+    uploads the state N' from pinned host memory, advances `chunk` time steps
+    and reads the moments rho, Ut^1, Ut^2 back to pinned host memory."""
+    n1, n2 = g.n1, g.n2
+    host_state = torch.empty((Q, n1, n2), dtype=torch.float64, pin_memory=True)
+    host_state.copy_(g.state(device=True).cpu())
+    state_np = host_state.numpy()
+
+    def one():
+        g.set_state(state_np)
+        g.step(args.chunk)
+        return g.moments(names=("rho", "Ut1", "Ut2"))
+
+    one()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dt = float(t.item())
+    return {"value": cells * args.chunk * args.steps * world / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": Q * cells * 8, "d2h_bytes_per_step": 3 * cells * 8,
+            "note": "per step: state upload (FP64 N'), %d time steps, moments download" % args.chunk}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * clbm.h -- C ABI of the GB300 library for the volumetric lattice Boltzmann
+ * method in general curvilinear coordinates (Chekhlov, Staroselsky, Zhang,
+ * Chen, arXiv:2301.01868).
+ *
+ * The library advances the populations N_alpha(q, t) of a 2-D coordinate-space
+ * lattice by the paper's update, Eq. 6 of Sec. 2:
+ *     N_alpha(q + c_alpha, t + 1) = N_alpha(q, t) + Omega_alpha + dN_alpha,
+ * with exact one-to-one advection (Eq. 12), BGK collision (Eq. 11) towards the
+ * curvilinear third-order equilibrium (Eq. 19), the lagged inertial force of
+ * Eq. 15 with the momentum-flux correction of Eq. 16 and the source of Eq. 17,
+ * and the periodic, no-slip and moving-wall boundaries of App. B.  Lattices
+ * are D2Q9 (T0 = 1/3) and D2Q21 (T0 = 2/3) of App. A.
+ *
+ * Index conventions.  q^1 = i is the wall-normal direction (1 <= i <= n1,
+ * walls at i = 1/2 and n1 + 1/2, App. B); q^2 = j is periodic (1 <= j <= n2).
+ * Every array crossing this interface is row-major and 0-based:
+ * populations are double [Q][n1][n2], cell fields double [n1][n2].
+ *
+ * Ownership.  The library owns the device state of a grid unless the caller
+ * passes a workspace; the caller owns every host pointer, which is read or
+ * written only during the call.  Device pointers passed in (workspace,
+ * outputs with dst_is_device) stay owned by the caller.
+ *
+ * Errors.  Every entry point returns a clbm_status; clbm_last_error() gives a
+ * thread-local message.  Asynchronous CUDA errors and device-side flags
+ * surface at the next synchronising call (moments, residual, get_state).
+ * Handles are not thread-safe; distinct handles are independent.
+ */
+#ifndef CLBM_H
+#define CLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct clbm_grid* clbm_handle;
+
+typedef enum {
+    CLBM_OK = 0,
+    CLBM_EINVAL = 1,     /* invalid argument or unsupported combination */
+    CLBM_ENOMEM = 2,     /* device or host allocation failed / workspace too small */
+    CLBM_ECUDA = 3,      /* a CUDA call failed */
+    CLBM_EUNSTABLE = 4,  /* a non-finite or non-positive density was found */
+    CLBM_ETIMEOUT = 5,   /* a bounded device wait gave up */
+    CLBM_EBUSY = 6       /* the handle is in use (e.g. captured in a graph) */
+} clbm_status;
+
+typedef enum { CLBM_D2Q9 = 9, CLBM_D2Q21 = 21 } clbm_lattice;
+
+/* Arithmetic of the bulk update and storage of the populations. */
+typedef enum {
+    CLBM_FP64 = 0,            /* FP64 compute, FP64 storage */
+    CLBM_FP32 = 1,            /* FP32 compute, FP32 storage */
+    CLBM_FP32_F16STORE = 2,   /* FP32 compute, FP16 storage (scaled) */
+    CLBM_FP32_BF16STORE = 3   /* FP32 compute, BF16 storage */
+} clbm_precision;
+
+/* Geometry of the coordinate map x(q) (Sec. 2, App. C, App. D). */
+typedef enum {
+    CLBM_GEOM_PLANAR = 0,  /* x = (x^1_i, (j - 1/2) step2), x^1_i edge midpoints */
+    CLBM_GEOM_POLAR = 1    /* x = r_i (cos th_j, sin th_j), th_j = (j - 1/2) 2 pi / n2 */
+} clbm_geom_kind;
+
+/* Wall conditions of App. B (direction q^2 is always periodic). */
+typedef enum {
+    CLBM_BC_NOSLIP = 0,  /* bounce-back of N through the mirrored node */
+    CLBM_BC_MOVING = 1   /* specular reflection plus the moving-wall correction */
+} clbm_wall_bc;
+
+typedef struct {
+    int lattice;            /* clbm_lattice */
+    int precision;          /* clbm_precision */
+    int n1, n2;             /* interior size: wall-normal x periodic; n1 >= 4, n2 >= 1 */
+    int kind;               /* clbm_geom_kind */
+    const double* edges1;   /* host, n1+1 increasing wall-normal edges x'_0..x'_n1
+                               (radii for POLAR, all > 0); nodes sit at midpoints,
+                               walls at edges1[0] and edges1[n1] */
+    double step2;           /* PLANAR: physical step along q^2 (> 0) */
+    double dx;              /* Delta x of the tangent vectors (Sec. 2); <= 0 picks
+                               the average wall-normal step (edges1[n1]-edges1[0])/n1 */
+    int bc_lo, bc_hi;       /* clbm_wall_bc of the walls at edges1[0] / edges1[n1] */
+    int device;             /* CUDA device ordinal */
+    void* stream;           /* cudaStream_t for all work of this grid (NULL: legacy default) */
+    void* workspace;        /* optional caller-owned device memory (NULL: library allocates) */
+    size_t workspace_bytes; /* size of workspace */
+} clbm_grid_desc;
+
+typedef struct {
+    double tau;             /* BGK relaxation time, > 1/2 (Eq. 11) */
+    double rho0;            /* reference density of the rest state (> 0) */
+    double u_wall_lo;       /* contravariant tangential velocity U0^2 of the low wall */
+    double u_wall_hi;       /* ... of the high wall (used by CLBM_BC_MOVING walls) */
+    double g_ext[2];        /* contravariant body acceleration g^k, added to F^k as rho g^k */
+    int force_iterations;   /* 0: the paper's lag, F from N'(q,t-1) (Sec. 2);
+                               n > 0: n extra passes of the implicit force relation */
+} clbm_case;
+
+/* Bytes of device workspace a grid with this description needs. */
+clbm_status clbm_workspace_bytes(const clbm_grid_desc* desc, size_t* bytes);
+
+/* Validate desc, allocate (or carve) device state, run the geometry / metric /
+ * Christoffel precompute (Sec. 2, Eqs. 1-5) on the device in FP64, and return
+ * a handle.  The state is undefined until clbm_set_case. */
+clbm_status clbm_create_grid(const clbm_grid_desc* desc, clbm_handle* out);
+
+/* Set the case and start from rest: N'(q,-1) = J f^eq(rho0, U = 0; g^{ij}(q)),
+ * previous-step wall moments (rho0, 0), t = 0.  Asynchronous. */
+clbm_status clbm_set_case(clbm_handle h, const clbm_case* cs);
+
+/* Replace the state N'(q, t-1) ([Q][n1][n2] FP64, host or device) and,
+ * optionally, the previous-step moments used by moving walls (rho, Ut^2 as
+ * [n1][n2]; NULL: rho0 and 0).  Synchronises. */
+clbm_status clbm_set_state(clbm_handle h, const double* Np, const double* rho_prev,
+                           const double* Ut2_prev, int src_is_device);
+
+/* Read the state N'(q, t-1) as [Q][n1][n2] FP64 into host or device memory.
+ * Synchronises. */
+clbm_status clbm_get_state(clbm_handle h, double* Np, int dst_is_device);
+
+/* Advance n time steps (boundary fill, then the fused stream-collide-force
+ * update, per step).  Asynchronous on the grid's stream. */
+clbm_status clbm_step(clbm_handle h, long long n);
+
+/* Moments of the current state, i.e. of the post-advection populations
+ * N(q, t) with the lagged force (what the next collision uses): rho, U^k
+ * (Eq. 10), Ut^k (Eq. 18), F^k (Eq. 15).  Each output is [n1][n2] FP64; any
+ * may be NULL.  Synchronises. */
+clbm_status clbm_moments(clbm_handle h, double* rho, double* U1, double* U2,
+                         double* Ut1, double* Ut2, double* F1, double* F2,
+                         int dst_is_device);
+
+/* Convergence and conservation diagnostics (Sec. 3.1: mass, kinetic energy,
+ * angular momentum).  res = ||u(t) - u(t')||_J / ((t - t') ||u(t)||_J) with
+ * physical u = Ut^k g_k and t' the time of the previous call (+inf on the
+ * first call).  cons = {sum N', sum c^1 N', sum c^2 N', kinetic energy
+ * 1/2 sum J rho |u|^2, angular momentum sum J rho (x cross u) (POLAR, else 0),
+ * max |u|}.  Returns CLBM_EUNSTABLE if a density is not finite and positive.
+ * Synchronises. */
+clbm_status clbm_residual(clbm_handle h, double* res, double cons[6]);
+
+/* "No flow" adjustment (Sec. 3.1, Eq. 23): in FP64, run the grid from rest
+ * with U0 = 0 and no body force for nsteps, then J <- J rho_nf / rho0 per
+ * row, and leave the state at that no-flow solution (a fixed point of the
+ * adjusted update).  rho_nf (host, may be NULL) receives the no-flow density
+ * [n1][n2].  Requires a prior clbm_set_case.  Synchronises. */
+clbm_status clbm_no_flow_adjust(clbm_handle h, long long nsteps, double* rho_nf);
+
+/* Time step counter t. */
+clbm_status clbm_time(clbm_handle h, long long* t);
+
+/* Change the stream the grid's work is issued on. */
+clbm_status clbm_set_stream(clbm_handle h, void* stream);
+
+/* When on, clbm_step records a CUDA event pair around every launch of the
+ * fused update; clbm_kernel_time returns their summed duration (ms) and the
+ * launch count since the last reset, and resets.  Synchronises. */
+clbm_status clbm_set_profiling(clbm_handle h, int on);
+clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
+
+/* Number of kernel launches this grid has issued since creation. */
+clbm_status clbm_launch_count(clbm_handle h, long long* launches);
+
+/* Free everything the grid owns.  NULL is accepted. */
+clbm_status clbm_destroy(clbm_handle h);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* clbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLBM_H */

@@ -1,0 +1,265 @@
+"""Python binding of ``libclbm.so`` (the C ABI in include/clbm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies device memory (the grid workspace and device
+outputs) and the CUDA stream.  If the library is missing the import fails;
+there is no CPU fallback.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libclbm.so")
+
+D2Q9, D2Q21 = 9, 21
+FP64, FP32, FP32_F16STORE, FP32_BF16STORE = 0, 1, 2, 3
+PLANAR, POLAR = 0, 1
+NOSLIP, MOVING = 0, 1
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP32_F16STORE, "bf16": FP32_BF16STORE}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "EBUSY"}
+
+
+class ClbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class UnstableError(ClbmError):
+    pass
+
+
+class _Desc(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("precision", C.c_int), ("n1", C.c_int), ("n2", C.c_int),
+                ("kind", C.c_int), ("edges1", C.POINTER(C.c_double)), ("step2", C.c_double),
+                ("dx", C.c_double), ("bc_lo", C.c_int), ("bc_hi", C.c_int), ("device", C.c_int),
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+class _Case(C.Structure):
+    _fields_ = [("tau", C.c_double), ("rho0", C.c_double), ("u_wall_lo", C.c_double),
+                ("u_wall_hi", C.c_double), ("g_ext", C.c_double * 2), ("force_iterations", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libclbm.so is not built; run __graft_entry__.build() "
+                              "(paper_2301_01868_gb300/_build.py) on a machine with nvcc")
+        L = C.CDLL(_LIB_PATH)
+        dp, vp, ll = C.POINTER(C.c_double), C.c_void_p, C.c_longlong
+        h = C.c_void_p
+        sig = {
+            "clbm_workspace_bytes": [C.POINTER(_Desc), C.POINTER(C.c_size_t)],
+            "clbm_create_grid": [C.POINTER(_Desc), C.POINTER(C.c_void_p)],
+            "clbm_set_case": [h, C.POINTER(_Case)],
+            "clbm_set_state": [h, vp, vp, vp, C.c_int],
+            "clbm_get_state": [h, vp, C.c_int],
+            "clbm_step": [h, ll],
+            "clbm_moments": [h, vp, vp, vp, vp, vp, vp, vp, C.c_int],
+            "clbm_residual": [h, dp, dp],
+            "clbm_no_flow_adjust": [h, ll, vp],
+            "clbm_time": [h, C.POINTER(ll)],
+            "clbm_set_stream": [h, vp],
+            "clbm_set_profiling": [h, C.c_int],
+            "clbm_kernel_time": [h, dp, C.POINTER(ll)],
+            "clbm_launch_count": [h, C.POINTER(ll)],
+            "clbm_destroy": [h],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.clbm_last_error.restype = C.c_char_p
+        L.clbm_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        msg = lib().clbm_last_error().decode()
+        if st == 4:
+            raise UnstableError(st, msg)
+        raise ClbmError(st, msg)
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _is_device(x):
+    return x is not None and not isinstance(x, np.ndarray) and x.is_cuda
+
+
+def _desc(lattice, precision, n1, n2, kind, edges, step2, dx, bc_lo, bc_hi, device, stream):
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    if e.shape != (n1 + 1,):
+        raise ValueError("edges must have n1+1 entries")
+    d = _Desc(lattice, precision, n1, n2, kind, e.ctypes.data_as(C.POINTER(C.c_double)),
+              float(step2), float(dx), bc_lo, bc_hi, device, stream, None, 0)
+    return d, e
+
+
+def workspace_bytes(lattice, precision, n1, n2):
+    """Device bytes a grid of this size needs."""
+    e = np.arange(n1 + 1, dtype=np.float64) + 1.0
+    d, _ = _desc(lattice, precision, n1, n2, PLANAR, e, 1.0, 0.0, 0, 0, 0, None)
+    out = C.c_size_t()
+    _check(lib().clbm_workspace_bytes(C.byref(d), C.byref(out)))
+    return out.value
+
+
+class Grid:
+    """A lattice advanced on one GPU by the fused curvilinear LBM update.
+
+    edges  : n1+1 wall-normal cell edges (radii for POLAR).
+    step2  : q^2 step of PLANAR grids.
+    precision : FP64, FP32, FP32_F16STORE or FP32_BF16STORE (or "fp64", ...).
+    The device workspace is a torch uint8 tensor; work goes on torch's
+    current stream of `device` unless `stream` (a torch.cuda.Stream) is given.
+    """
+
+    def __init__(self, lattice, n1, n2, edges, kind=PLANAR, step2=1.0, precision=FP64, dx=0.0,
+                 bc_lo=NOSLIP, bc_hi=NOSLIP, device=0, stream=None):
+        import torch
+
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.Q, self.n1, self.n2 = int(lattice), int(n1), int(n2)
+        self.precision, self.kind = int(precision), int(kind)
+        self.device = torch.device("cuda", device)
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        d, self._edges = _desc(self.Q, self.precision, self.n1, self.n2, self.kind, edges, step2, dx,
+                               int(bc_lo), int(bc_hi), self.device.index, self.stream.cuda_stream)
+        nb = C.c_size_t()
+        _check(lib().clbm_workspace_bytes(C.byref(d), C.byref(nb)))
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        d.workspace = self.workspace.data_ptr()
+        d.workspace_bytes = nb.value
+        h = C.c_void_p()
+        _check(lib().clbm_create_grid(C.byref(d), C.byref(h)))
+        self._h = h
+
+    # lifetime ----------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().clbm_destroy(self._h)
+            self._h = None
+            self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # case and state ----------------------------------------------------------
+    def set_case(self, tau, rho0=1.0, u_wall_lo=0.0, u_wall_hi=0.0, g_ext=(0.0, 0.0),
+                 force_iterations=0):
+        c = _Case(float(tau), float(rho0), float(u_wall_lo), float(u_wall_hi),
+                  (C.c_double * 2)(float(g_ext[0]), float(g_ext[1])), int(force_iterations))
+        _check(lib().clbm_set_case(self._h, C.byref(c)))
+
+    def set_state(self, Np, rho_prev=None, ut2_prev=None):
+        """N'(q, t-1) as (Q, n1, n2) float64, numpy (host) or torch (either)."""
+        dev = _is_device(Np)
+        arrs = []
+        for x in (Np, rho_prev, ut2_prev):
+            if x is None:
+                arrs.append(None)
+            elif dev:
+                arrs.append(x.to(self._torch.float64).contiguous())
+            else:
+                x = x.cpu().numpy() if hasattr(x, "cpu") else x
+                arrs.append(np.ascontiguousarray(x, dtype=np.float64))
+        if arrs[0].shape != (self.Q, self.n1, self.n2):
+            raise ValueError("state must be (Q, n1, n2)")
+        _check(lib().clbm_set_state(self._h, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), int(dev)))
+
+    def state(self, device=False):
+        """N'(q, t-1) as float64 (Q, n1, n2): numpy, or a torch CUDA tensor."""
+        if device:
+            out = self._torch.empty((self.Q, self.n1, self.n2), dtype=self._torch.float64,
+                                    device=self.device)
+        else:
+            out = np.empty((self.Q, self.n1, self.n2))
+        _check(lib().clbm_get_state(self._h, _ptr(out), int(device)))
+        return out
+
+    def step(self, n=1):
+        _check(lib().clbm_step(self._h, int(n)))
+
+    @property
+    def t(self):
+        v = C.c_longlong()
+        _check(lib().clbm_time(self._h, C.byref(v)))
+        return v.value
+
+    # diagnostics --------------------------------------------------------------
+    def moments(self, device=False, names=("rho", "U1", "U2", "Ut1", "Ut2", "F1", "F2")):
+        """Moments of the current state (what the next collision uses)."""
+        all_names = ("rho", "U1", "U2", "Ut1", "Ut2", "F1", "F2")
+        out = {}
+        for k in names:
+            if device:
+                out[k] = self._torch.empty((self.n1, self.n2), dtype=self._torch.float64,
+                                           device=self.device)
+            else:
+                out[k] = np.empty((self.n1, self.n2))
+        ptrs = [_ptr(out.get(k)) for k in all_names]
+        _check(lib().clbm_moments(self._h, *ptrs, int(device)))
+        return out
+
+    def residual(self):
+        """(res, cons): cons = mass, P1, P2, kinetic energy, angular momentum, max|u|."""
+        r = C.c_double()
+        cons = (C.c_double * 6)()
+        _check(lib().clbm_residual(self._h, C.byref(r), cons))
+        return r.value, np.array(list(cons))
+
+    def no_flow_adjust(self, nsteps):
+        rho_nf = np.empty((self.n1, self.n2))
+        _check(lib().clbm_no_flow_adjust(self._h, int(nsteps), rho_nf.ctypes.data))
+        return rho_nf
+
+    def set_profiling(self, on=True):
+        _check(lib().clbm_set_profiling(self._h, int(bool(on))))
+
+    def kernel_time(self):
+        """(ms, launches) of the fused update since profiling was switched on."""
+        ms = C.c_double()
+        n = C.c_longlong()
+        _check(lib().clbm_kernel_time(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self):
+        n = C.c_longlong()
+        _check(lib().clbm_launch_count(self._h, C.byref(n)))
+        return n.value
+
+
+def wall_speed_planar(u_phys, step2, dx):
+    """Contravariant U0^2 of a planar wall moving at physical speed u_phys
+    (|g_2| = step2 / dx)."""
+    return u_phys * dx / step2
+
+
+def wall_speed_polar(u_phys, R_wall, n2, dx):
+    """Contravariant U0^2 of a rigidly rotating circle of radius R_wall with
+    surface speed u_phys (|g_2| = R sin(2 pi / n2) / dx, App. D)."""
+    return u_phys * dx / (R_wall * math.sin(2.0 * math.pi / n2))

@@ -1,0 +1,192 @@
+// clbm_cell.cuh -- per-cell pieces of the update shared by the fused step
+// and the diagnostics kernels: pull with the lagged read, moments and force
+// (Eqs. 7-15), and the collision of Sec. 2 (Eqs. 16-19, 11), written in
+// deviations from the rest equilibrium.
+//
+// The state buffer holds sigma_a(r) = N'_a(r) - ref_a(r), zero at rest, with
+// ghost rows (walls) and ghost columns (periodic copies) around the interior,
+// so a pull is a load at a constant offset from the cell.  A pulled value
+// becomes a deviation from the cell's own reference by adding
+// Delta_a = ref_a(i - c1) - ref_a(i); the rest parts of every sum are
+// FP64-evaluated per-row constants of the table.
+#pragma once
+
+#include "clbm_internal.cuh"
+
+namespace clbm {
+
+// Per-launch scalars in the compute type (converted once on the host).
+template <typename C> struct Consts;
+template <> struct Consts<double> {
+    double rho0, g1, g2, tau_inv, omt, pref;
+    __device__ static Consts make(const StepScalars& s) {
+        return {s.rho0, s.g1, s.g2, s.tau_inv, s.omt, s.pref};
+    }
+};
+template <> struct Consts<float> {
+    float rho0, g1, g2, tau_inv, omt, pref;
+    __device__ static Consts make(const StepScalars& s) {
+        return {s.frho0, s.fg1, s.fg2, s.ftau_inv, s.fomt, s.fpref};
+    }
+};
+
+template <int Q, typename C>
+struct Cell {
+    C d[Q];                                   // pulled deviations from this row's reference
+    C drho, rho, irho, U1, U2, F1, F2, Ut1, Ut2;
+};
+
+// Advection (Eq. 12) with the lagged read of N'(q, t-1), moments (Eqs. 7, 8,
+// 10) and the lagged inertial force (Eq. 15 with N'(q, t-1)):
+//   F^k = -1/(2J) sum_b a^k_b [N'_b(q, t-1) + N_{opp b}(q, t)] + rho g^k.
+// p points at this cell in population plane 0 of the buffer; P is the plane
+// stride and ld the row stride (elements).
+template <int Q, typename S, typename C>
+__device__ __forceinline__ void pull_cell(const S* __restrict__ p, long long P, int ld, float isc,
+                                          const C* __restrict__ tb, const Consts<C>& k,
+                                          Cell<Q, C>& c) {
+    using L = Lat<Q>;
+    using T = Tab<Q>;
+    C Sd = tb[T::D0], S1 = tb[T::M1], S2 = tb[T::M2];
+    C f1 = tb[T::F01], f2 = tb[T::F02];
+    c.d[0] = C(Store<S>::ld(p, isc));
+    Sd += c.d[0];
+#pragma unroll
+    for (int q = 0; q < L::NP; ++q) {
+        const int a = L::plus(q), b = opp_of(a);
+        const int c1 = c1_of(a), c2 = c2_of(a);
+        // pulled: N_a(q) from q - c_a, N_b(q) from q + c_a; lagged: own values
+        const C pa = C(Store<S>::ld(p + a * P - (long long)c1 * ld - c2, isc));
+        const C pb = C(Store<S>::ld(p + b * P + (long long)c1 * ld + c2, isc));
+        const C la = C(Store<S>::ld(p + a * P, isc));
+        const C lb = C(Store<S>::ld(p + b * P, isc));
+        Sd += pa + pb;
+        const C dp = pa - pb;
+        if (c1 != 0) S1 += C(c1) * dp;
+        if (c2 != 0) S2 += C(c2) * dp;
+        const C ta = la + pb, tbv = lb + pa;
+        f1 += tb[T::a1(a)] * ta + tb[T::a1(b)] * tbv;
+        f2 += tb[T::a2(a)] * ta + tb[T::a2(b)] * tbv;
+        c.d[a] = c1 != 0 ? pa + tb[T::dpull(a)] : pa;
+        c.d[b] = c1 != 0 ? pb + tb[T::dpull(b)] : pb;
+    }
+    const C invJ = tb[T::INVJ];
+    c.drho = Sd * invJ;
+    c.rho = k.rho0 + c.drho;
+    c.irho = C(1) / c.rho;
+    c.U1 = S1 * invJ * c.irho;
+    c.U2 = S2 * invJ * c.irho;
+    c.F1 = -C(0.5) * invJ * f1 + c.rho * k.g1;
+    c.F2 = -C(0.5) * invJ * f2 + c.rho * k.g2;
+}
+
+// The force of Eq. 15 re-evaluated with the newest N'(q, t) (own-row
+// deviations out[]) for one fixed-point pass of the implicit relation.
+template <int Q, typename C>
+__device__ __forceinline__ void force_again(const C* __restrict__ tb, const C (&out)[Q],
+                                            const Consts<C>& k, Cell<Q, C>& c) {
+    using T = Tab<Q>;
+    C f1 = tb[T::FI1], f2 = tb[T::FI2];
+#pragma unroll
+    for (int b = 1; b < Q; ++b) {
+        const C t = out[b] + c.d[opp_of(b)];
+        f1 += tb[T::a1(b)] * t;
+        f2 += tb[T::a2(b)] * t;
+    }
+    const C invJ = tb[T::INVJ];
+    c.F1 = -C(0.5) * invJ * f1 + c.rho * k.g1;
+    c.F2 = -C(0.5) * invJ * f2 + c.rho * k.g2;
+}
+
+// Ut (Eq. 18), equilibrium coefficients (Eq. 19), odd parts, the momentum-flux
+// correction (Eq. 16, symmetric part), source (Eq. 17) and BGK (Eqs. 6, 11).
+// emit(alpha, value) receives every new post-collision deviation.
+template <int Q, typename C, typename Emit>
+__device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C>& c,
+                                             const Consts<C>& k, Emit&& emit) {
+    using L = Lat<Q>;
+    using T = Tab<Q>;
+    constexpr C T0 = C(L::T0);
+    constexpr C iT0 = C(1.0 / L::T0);
+    constexpr C i2T02 = C(0.5 / (L::T0 * L::T0));
+    constexpr C i6T03 = C(1.0 / (6.0 * L::T0 * L::T0 * L::T0));
+    const C U1 = c.U1, U2 = c.U2;
+    const C Ut1 = U1 + C(0.5) * c.F1 * c.irho;
+    const C Ut2 = U2 + C(0.5) * c.F2 * c.irho;
+    c.Ut1 = Ut1;
+    c.Ut2 = Ut2;
+    const C gi11 = tb[T::G11], gi12 = tb[T::G12], gi22 = tb[T::G22];
+    // Third-order Hermite coefficients C^{ijk} of Eq. 19 (symmetric).
+    const C C111 = T0 * (C(3) * gi11 * Ut1 - C(3) * U1) + Ut1 * Ut1 * Ut1;
+    const C C112 = T0 * (gi11 * Ut2 + C(2) * gi12 * Ut1 - U2) + Ut1 * Ut1 * Ut2;
+    const C C122 = T0 * (C(2) * gi12 * Ut2 + gi22 * Ut1 - U1) + Ut1 * Ut2 * Ut2;
+    const C C222 = T0 * (C(3) * gi22 * Ut2 - C(3) * U2) + Ut2 * Ut2 * Ut2;
+    const C K11 = U1 * iT0 - (C111 + C122) * i2T02;
+    const C K12 = U2 * iT0 - (C112 + C222) * i2T02;
+    const C K111 = C111 * i6T03, K112 = C(3) * C112 * i6T03;
+    const C K122 = C(3) * C122 * i6T03, K222 = C222 * i6T03;
+    const C dK0 = -(Ut1 * Ut1 + Ut2 * Ut2) * (C(0.5) * iT0);
+    const C dK11 = Ut1 * Ut1 * i2T02, dK12 = C(2) * Ut1 * Ut2 * i2T02, dK22 = Ut2 * Ut2 * i2T02;
+
+    // Odd part of f^eq / (rho w) per +/- pair; only odd parts survive the pair
+    // sums of the momentum-flux correction.
+    C O[L::NP];
+    C S11 = C(0), S22 = C(0), S12 = C(0);
+#pragma unroll
+    for (int q = 0; q < L::NP; ++q) {
+        const int a = L::plus(q);
+        const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
+        O[q] = K11 * c1 + K12 * c2 + K111 * (c1 * c1 * c1) + K112 * (c1 * c1 * c2) +
+               K122 * (c1 * c2 * c2) + K222 * (c2 * c2 * c2);
+        S11 += tb[T::e11(q)] * O[q];
+        S22 += tb[T::e22(q)] * O[q];
+        S12 += tb[T::e12(q)] * O[q];
+    }
+    const C pr = k.pref * c.rho;
+    S11 *= pr;
+    S22 *= pr;
+    S12 *= pr;
+    const C trS = S11 + S22;
+    const C J = tb[T::J];
+    const C omt = k.omt;
+    const C drt = c.drho * k.tau_inv, rt = c.rho * k.tau_inv;
+    const C Fa = c.F1 * iT0, Fb = c.F2 * iT0;
+    const C base = rt * dK0 - trS * iT0;
+    const C Ea = rt * dK11 + S11 * (iT0 * iT0);
+    const C Eb = rt * dK12 + C(2) * S12 * (iT0 * iT0);
+    const C Ec = rt * dK22 + S22 * (iT0 * iT0);
+    emit(0, c.d[0] * omt + J * C(L::w(0)) * (drt * tb[T::P00] + base));
+#pragma unroll
+    for (int q = 0; q < L::NP; ++q) {
+        const int a = L::plus(q), b = opp_of(a);
+        const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
+        const C X = drt * tb[T::p0(q)] + base + Ea * (c1 * c1) + Eb * (c1 * c2) + Ec * (c2 * c2);
+        const C Y = rt * O[q] + Fa * c1 + Fb * c2;
+        const C Jw = J * C(L::w(a));
+        emit(a, c.d[a] * omt + Jw * (X + Y));
+        emit(b, c.d[b] * omt + Jw * (X - Y));
+    }
+}
+
+// Reference N of direction a at 1-based row r (FP64 geometry table); rows
+// beyond a wall are the mirror image of the row inside, which flips c^1.
+template <int Q>
+__device__ __forceinline__ double ref_at(const double* geo, int n1, int a, int r) {
+    int m = r, b = a;
+    if (r < 1) { m = 1 - r; b = hat_of(a); }
+    else if (r > n1) { m = 2 * n1 + 1 - r; b = hat_of(a); }
+    return geo[(size_t)(m - 1) * Geo::stride(Q) + Geo::ref(Q, b)];
+}
+
+// Store a value of interior column j (0..n2-1) and its periodic copies in
+// the ghost columns (state column = j + GC).
+template <typename S, typename C>
+__device__ __forceinline__ void store_periodic(S* __restrict__ rowp, int j, int n2, C v, float isc) {
+    Store<S>::st(rowp + j + GC, v, isc);
+    if (j < GC)
+        for (int jj = j + n2; jj < n2 + GC; jj += n2) Store<S>::st(rowp + jj + GC, v, isc);
+    if (j >= n2 - GC)
+        for (int jj = j - n2; jj >= -GC; jj -= n2) Store<S>::st(rowp + jj + GC, v, isc);
+}
+
+}  // namespace clbm

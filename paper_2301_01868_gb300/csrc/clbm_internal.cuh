@@ -1,0 +1,131 @@
+// clbm_internal.cuh -- device-side data layout and kernel launchers shared by
+// the translation units of the CUDA library (not part of the C ABI).
+//
+// Layout in HBM (one grid):
+//   state A, B : [Q][n1 + 2h][ld] in the storage type, ld = n2 + 2 GC rounded
+//                up to 32 elements; rows 0..h-1 and n1+h..n1+2h-1 are the
+//                ghost rows the boundary kernel fills, columns 0..GC-1 and
+//                n2+GC.. hold periodic copies (interior column j sits at
+//                j + GC), written by whichever kernel writes the row.  A population is stored as
+//                its deviation from the rest equilibrium of its own row,
+//                sigma_alpha(i) = N'_alpha(i) - ref_alpha(i), zero at rest
+//                (ghost rows use the mirrored row's reference).
+//   tab        : [n1][Tab<Q>::S] per-row coefficients in the compute type.
+//   geo        : [n1][Geo::stride(Q)] per-row FP64 geometry + references.
+//   wall       : [2 walls][h][n2] x {rho, Ut^2} of the last collision.
+//   ghost      : [2 walls][h][Q] x {offset, correction coefficient}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "clbm_lattice.cuh"
+
+namespace clbm {
+
+// Storage conversions (deviation scaled by a power of two for FP16).
+template <typename S> struct Store;
+template <> struct Store<double> {
+    __device__ static __forceinline__ double ld(const double* p, float) { return __ldg(p); }
+    __device__ static __forceinline__ void st(double* p, double v, float) { *p = v; }
+};
+template <> struct Store<float> {
+    __device__ static __forceinline__ float ld(const float* p, float) { return __ldg(p); }
+    __device__ static __forceinline__ void st(float* p, float v, float) { *p = v; }
+};
+template <> struct Store<__half> {
+    __device__ static __forceinline__ float ld(const __half* p, float inv_scale) {
+        return __half2float(__ldg(p)) * inv_scale;
+    }
+    __device__ static __forceinline__ void st(__half* p, float v, float inv_scale) {
+        *p = __float2half_rn(v / inv_scale);
+    }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ static __forceinline__ float ld(const __nv_bfloat16* p, float inv_scale) {
+        return __bfloat162float(__ldg(p)) * inv_scale;
+    }
+    __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, float inv_scale) {
+        *p = __float2bfloat16_rn(v / inv_scale);
+    }
+};
+
+constexpr int GC = 4;  // ghost columns on each side (>= widest |c^2| = 3)
+
+// Scalars of the case, in both compute types (converted once on the host).
+struct StepScalars {
+    double rho0, g1, g2, tau_inv, omt, pref;
+    float frho0, fg1, fg2, ftau_inv, fomt, fpref;
+};
+
+// Everything one launch of the fused update or of the boundary fill needs.
+struct StepArgs {
+    StepScalars k;
+    const void* src;        // state A (read)
+    void* dst;              // state B (written)
+    const void* tab;        // per-row coefficients, compute type
+    void* wall_rho;         // [2][h][n2] compute type
+    void* wall_ut2;
+    const double* ghost;    // [2][h][Q][2]
+    int n1, n2, ld, h;
+    long long plane;        // elements per population plane = (n1+2h)*ld
+    double tau, rho0, g1, g2, U0_lo, U0_hi;
+    float inv_scale;        // 1/scale of 16-bit storage (1 otherwise)
+    int bc_lo, bc_hi;
+    int iters;              // extra passes of the implicit force
+};
+
+// Diagnostics launch arguments.
+struct MomArgs {
+    StepScalars k;
+    const void* src;
+    const void* tab;
+    const double* geo;
+    int n1, n2, ld, h;
+    long long plane;
+    double tau, rho0, g1, g2;
+    float inv_scale;
+    // outputs (device, [n1][n2] FP64, may be null)
+    double *rho, *U1, *U2, *Ut1, *Ut2, *F1, *F2;
+    // residual mode
+    double* ut_prev;        // [2][n1][n2] FP64 snapshot of Ut^k
+    double* partial;        // [blocks][NRED]
+    int have_prev;
+};
+
+constexpr int NRED = 10;  // reduced quantities per block
+
+// Launchers (defined in the .cu files); all asynchronous on `stream`.
+void launch_geometry(int Q, const double* pos, int n1, double dx, int polar,
+                     double* geo, cudaStream_t stream);
+void launch_reference(int Q, double* geo, int n1, double rho0, cudaStream_t stream);
+void launch_tables(int Q, int prec, const double* geo, void* tab, double* ghost, int n1,
+                   double tau, int bc_lo, int bc_hi, cudaStream_t stream);
+void launch_boundary(int Q, int prec, const StepArgs& a, void* state, cudaStream_t stream);
+void launch_step(int Q, int prec, const StepArgs& a, cudaStream_t stream);
+void launch_moments(int Q, int prec, const MomArgs& a, int iters, int reduce,
+                    cudaStream_t stream);
+int moments_blocks(int n1, int n2);
+void launch_reduce_final(const double* partial, int nblocks, double* out, cudaStream_t stream);
+void launch_state_from_fp64(int Q, int prec, const double* Np, const double* geo, void* state,
+                            int n1, int n2, int ld, int h, float inv_scale, cudaStream_t stream);
+void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo, double* Np,
+                          int n1, int n2, int ld, int h, float inv_scale, cudaStream_t stream);
+void launch_wall_copy(int prec, void* wall_rho, void* wall_ut2, const double* src_rho,
+                      const double* src_ut2, const double* rho_nf_row, int n1, int n2, int h,
+                      double rho0, cudaStream_t stream);
+void launch_wall_init(int prec, void* wall_rho, void* wall_ut2, const double* rho,
+                      const double* ut2, int n1, int n2, int h, double rho0, cudaStream_t stream);
+void launch_scale_volume(int Q, double* geo, const double* rho_nf_row, int n1, double rho0,
+                         cudaStream_t stream);
+void launch_rescale_wall(int prec, void* wall_rho, const double* rho_nf_row, int n1, int n2,
+                         int h, double rho0, cudaStream_t stream);
+void launch_row_mean(const double* field, int n1, int n2, double* out, cudaStream_t stream);
+
+// Size in bytes of one stored population.
+inline int storage_bytes(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
+inline int compute_bytes(int prec) { return prec == 0 ? 8 : 4; }
+
+}  // namespace clbm

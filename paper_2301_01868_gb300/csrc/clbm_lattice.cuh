@@ -1,0 +1,112 @@
+// clbm_lattice.cuh -- D2Q9 / D2Q21 constants of the CUDA path (App. A).
+//
+// Velocity order follows the index maps of App. B (first component is the
+// wall-normal one); the two outer D2Q21 shells carry 1/432 and 1/1620, the
+// values that make the App. A isotropy conditions hold exactly (the printed
+// 7/432 and 7/1620 do not sum to one).  Everything is constexpr so that, in
+// unrolled loops, every c_alpha folds into the arithmetic.
+#pragma once
+
+namespace clbm {
+
+__host__ __device__ __forceinline__ constexpr int c1_of(int a) {
+    return (a == 1 || a == 5 || a == 8) ? 1
+         : (a == 3 || a == 6 || a == 7) ? -1
+         : (a == 9 || a == 13 || a == 16) ? 2
+         : (a == 11 || a == 14 || a == 15) ? -2
+         : (a == 17) ? 3
+         : (a == 19) ? -3 : 0;
+}
+
+__host__ __device__ __forceinline__ constexpr int c2_of(int a) {
+    return (a == 2 || a == 5 || a == 6) ? 1
+         : (a == 4 || a == 7 || a == 8) ? -1
+         : (a == 10 || a == 13 || a == 14) ? 2
+         : (a == 12 || a == 15 || a == 16) ? -2
+         : (a == 18) ? 3
+         : (a == 20) ? -3 : 0;
+}
+
+// Reverse direction (bounce-back map alpha*).
+__host__ __device__ __forceinline__ constexpr int opp_of(int a) {
+    return a == 0 ? 0
+         : (a <= 4) ? ((a + 1) % 4 + 1)                 // 1<->3, 2<->4
+         : (a <= 8) ? ((a - 5 + 2) % 4 + 5)             // 5<->7, 6<->8
+         : (a <= 12) ? ((a - 9 + 2) % 4 + 9)            // 9<->11, 10<->12
+         : (a <= 16) ? ((a - 13 + 2) % 4 + 13)          // 13<->15, 14<->16
+         : ((a - 17 + 2) % 4 + 17);                     // 17<->19, 18<->20
+}
+
+// Direction with the wall-normal component flipped (specular map alpha-hat).
+__host__ __device__ __forceinline__ constexpr int hat_of(int a) {
+    return (a == 1) ? 3 : (a == 3) ? 1 : (a == 5) ? 6 : (a == 6) ? 5
+         : (a == 7) ? 8 : (a == 8) ? 7 : (a == 9) ? 11 : (a == 11) ? 9
+         : (a == 13) ? 14 : (a == 14) ? 13 : (a == 15) ? 16 : (a == 16) ? 15
+         : (a == 17) ? 19 : (a == 19) ? 17 : a;
+}
+
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+    static constexpr int H = 1;          // stencil reach = ghost depth
+    static constexpr int NP = 4;         // +/- pairs
+    static constexpr double T0 = 1.0 / 3.0;
+    __host__ __device__ static constexpr double w(int a) {
+        return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+    // "+" member of pair p; its partner is opp_of(plus(p)).
+    __host__ __device__ static constexpr int plus(int p) { return p == 0 ? 1 : p == 1 ? 2 : p == 2 ? 5 : 6; }
+};
+
+template <> struct Lat<21> {
+    static constexpr int H = 3;
+    static constexpr int NP = 10;
+    static constexpr double T0 = 2.0 / 3.0;
+    __host__ __device__ static constexpr double w(int a) {
+        return a == 0 ? 91.0 / 324.0
+             : a <= 4 ? 1.0 / 12.0
+             : a <= 8 ? 2.0 / 27.0
+             : a <= 12 ? 7.0 / 360.0
+             : a <= 16 ? 1.0 / 432.0
+             : 1.0 / 1620.0;
+    }
+    __host__ __device__ static constexpr int plus(int p) {
+        return p == 0 ? 1 : p == 1 ? 2 : p == 2 ? 5 : p == 3 ? 6 : p == 4 ? 9
+             : p == 5 ? 10 : p == 6 ? 13 : p == 7 ? 14 : p == 8 ? 17 : 18;
+    }
+};
+
+// Per-row coefficient table of the fused update, in the compute type.
+// Slots: header (metric, rest-state sums evaluated in FP64), then a^k_alpha
+// for alpha = 1..Q-1, then four values per +/- pair, then the pull offsets
+// Delta_alpha = ref_alpha(i - c1) - ref_alpha(i) for alpha = 1..Q-1.
+template <int Q> struct Tab {
+    static constexpr int INVJ = 0, J = 1, G11 = 2, G12 = 3, G22 = 4;
+    static constexpr int F01 = 5, F02 = 6, P00 = 7, FI1 = 8, FI2 = 9;
+    static constexpr int D0 = 10, M1 = 11, M2 = 12;
+    static constexpr int A0 = 16;                               // a1, a2 of alpha=1..Q-1
+    static constexpr int PB = A0 + 2 * (Q - 1);                 // P0, E11, E22, E12 per pair
+    static constexpr int DB = PB + 4 * Lat<Q>::NP;              // Delta_alpha, alpha=1..Q-1
+    static constexpr int S = DB + (Q - 1) + ((Q - 1) % 4 ? 4 - (Q - 1) % 4 : 0);  // stride
+    __host__ __device__ static constexpr int a1(int a) { return A0 + 2 * (a - 1); }
+    __host__ __device__ static constexpr int a2(int a) { return A0 + 2 * (a - 1) + 1; }
+    __host__ __device__ static constexpr int p0(int p) { return PB + 4 * p; }
+    __host__ __device__ static constexpr int e11(int p) { return PB + 4 * p + 1; }
+    __host__ __device__ static constexpr int e22(int p) { return PB + 4 * p + 2; }
+    __host__ __device__ static constexpr int e12(int p) { return PB + 4 * p + 3; }
+    __host__ __device__ static constexpr int dpull(int a) { return DB + (a - 1); }
+};
+
+// Per-row FP64 geometry (geometry precompute output, plus the deviation
+// reference).  a^k_alpha = c^m_alpha Theta^k_m(q + c_alpha, q) (Eq. 5).
+struct Geo {
+    static constexpr int J = 0, JGEO = 1, GI11 = 2, GI12 = 3, GI22 = 4;
+    static constexpr int G11 = 5, G12 = 6, G22 = 7, M1 = 8, M2 = 9, G2N = 10, R = 11;
+    static constexpr int A0 = 12;                       // a1, a2 per alpha (2Q)
+    __host__ __device__ static constexpr int a1(int a) { return A0 + 2 * a; }
+    __host__ __device__ static constexpr int a2(int a) { return A0 + 2 * a + 1; }
+    __host__ __device__ static constexpr int ref(int Q, int a) { return A0 + 2 * Q + a; }
+    __host__ __device__ static constexpr int stride(int Q) { return A0 + 3 * Q; }
+};
+
+}  // namespace clbm

@@ -1,0 +1,317 @@
+// k_reduce.cu -- diagnostics (moments, residual and conservation sums with a
+// warp-shuffle reduction in a fixed order) and the state conversions between
+// FP64 populations and the stored deviations.
+#include "clbm_cell.cuh"
+
+namespace clbm {
+
+namespace {
+
+constexpr int RB = 128;  // threads per block of the diagnostics kernels
+
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters, int reduce) {
+    using T = Tab<Q>;
+    constexpr int H = Lat<Q>::H;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    const bool live = j < a.n2;
+    double v[NRED];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) v[k] = 0.0;
+    if (live) {
+        const C* tb = (const C*)a.tab + (size_t)i * T::S;
+        const Consts<C> kc = Consts<C>::make(a.k);
+        const long long off = (long long)(i + H) * a.ld + j + GC;
+        const S* p = (const S*)a.src + off;
+        Cell<Q, C> c;
+        pull_cell<Q, S, C>(p, a.plane, a.ld, a.inv_scale, tb, kc, c);
+        if (iters > 0) {
+            C out[Q];
+            collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
+            for (int it = 0; it < iters; ++it) {
+                force_again<Q, C>(tb, out, kc, c);
+                collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
+            }
+        } else {
+            collide_emit<Q, C>(tb, c, kc, [](int, C) {});
+        }
+        const size_t m = (size_t)i * a.n2 + j;
+        if (a.rho) a.rho[m] = double(c.rho);
+        if (a.U1) a.U1[m] = double(c.U1);
+        if (a.U2) a.U2[m] = double(c.U2);
+        if (a.Ut1) a.Ut1[m] = double(c.Ut1);
+        if (a.Ut2) a.Ut2[m] = double(c.Ut2);
+        if (a.F1) a.F1[m] = double(c.F1);
+        if (a.F2) a.F2[m] = double(c.F2);
+        if (reduce) {
+            const double* g = a.geo + (size_t)i * Geo::stride(Q);
+            const double u1 = double(c.Ut1), u2 = double(c.Ut2), rho = double(c.rho);
+            const double J = g[Geo::J];
+            const double uu = g[Geo::G11] * u1 * u1 + 2.0 * g[Geo::G12] * u1 * u2 + g[Geo::G22] * u2 * u2;
+            double dd = 0.0;
+            const size_t nc = (size_t)a.n1 * a.n2;
+            if (a.have_prev) {
+                const double e1 = u1 - a.ut_prev[m], e2 = u2 - a.ut_prev[nc + m];
+                dd = g[Geo::G11] * e1 * e1 + 2.0 * g[Geo::G12] * e1 * e2 + g[Geo::G22] * e2 * e2;
+            }
+            a.ut_prev[m] = u1;
+            a.ut_prev[nc + m] = u2;
+            double mass = 0.0, p1 = 0.0, p2 = 0.0;
+#pragma unroll
+            for (int al = 0; al < Q; ++al) {
+                const double Np = double(Store<S>::ld(p + al * a.plane, a.inv_scale)) +
+                                  g[Geo::ref(Q, al)];
+                mass += Np;
+                p1 += c1_of(al) * Np;
+                p2 += c2_of(al) * Np;
+            }
+            v[0] = J * dd;
+            v[1] = J * uu;
+            v[2] = mass;
+            v[3] = p1;
+            v[4] = p2;
+            v[5] = 0.5 * J * rho * uu;
+            v[6] = J * rho * (g[Geo::M1] * u1 + g[Geo::M2] * u2);
+            v[7] = sqrt(uu);
+            v[8] = (rho > 0.0 && isfinite(rho) && isfinite(uu)) ? 0.0 : 1.0;
+        }
+    }
+    if (!reduce) return;
+    // Warp shuffle, then the four warp results in order: a fixed summation
+    // tree, so repeated runs give identical bits.
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, off);
+            x = (k == 7) ? fmax(x, y) : x + y;
+        }
+        v[k] = x;
+    }
+    __shared__ double sh[RB / 32][NRED];
+    const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (ln == 0)
+        for (int k = 0; k < NRED; ++k) sh[w][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NRED) {
+        const int k = threadIdx.x;
+        double x = sh[0][k];
+        for (int q = 1; q < RB / 32; ++q) x = (k == 7) ? fmax(x, sh[q][k]) : x + sh[q][k];
+        a.partial[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * NRED + k] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ partial,
+                                                      int nblocks, double* __restrict__ out) {
+    __shared__ double sh[256];
+    for (int k = 0; k < NRED; ++k) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += 256) {
+            const double y = partial[(size_t)b * NRED + k];
+            x = (k == 7) ? fmax(x, y) : x + y;
+        }
+        sh[threadIdx.x] = x;
+        __syncthreads();
+        for (int st = 128; st > 0; st >>= 1) {
+            if (threadIdx.x < st)
+                sh[threadIdx.x] = (k == 7) ? fmax(sh[threadIdx.x], sh[threadIdx.x + st])
+                                           : sh[threadIdx.x] + sh[threadIdx.x + st];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sh[0];
+        __syncthreads();
+    }
+}
+
+template <int Q, typename S>
+__global__ void k_from_fp64(const double* __restrict__ Np, const double* __restrict__ geo,
+                            S* __restrict__ st, int n1, int n2, int ld, int h, float inv_scale) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= n2) return;
+    const long long P = (long long)(n1 + 2 * h) * ld;
+#pragma unroll
+    for (int al = 0; al < Q; ++al) {
+        // Np == nullptr: the rest state N' = J f^eq(rho0, 0) of this row.
+        const double Nv = Np ? Np[((size_t)al * n1 + i) * n2 + j]
+                             : geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
+        const double v = Nv - geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
+        using CT = decltype(Store<S>::ld(st, 1.f));
+        store_periodic<S, CT>(st + al * P + (long long)(i + h) * ld, j, n2, CT(v), inv_scale);
+    }
+}
+
+template <int Q, typename S>
+__global__ void k_to_fp64(const S* __restrict__ st, const double* __restrict__ geo,
+                          double* __restrict__ Np, int n1, int n2, int ld, int h, float inv_scale) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= n2) return;
+    const long long P = (long long)(n1 + 2 * h) * ld;
+#pragma unroll
+    for (int al = 0; al < Q; ++al) {
+        const double s = double(Store<S>::ld(st + al * P + (long long)(i + h) * ld + j + GC, inv_scale));
+        Np[((size_t)al * n1 + i) * n2 + j] = s + geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
+    }
+}
+
+template <typename C>
+__global__ void k_wall_init(C* __restrict__ wr, C* __restrict__ wu, const double* __restrict__ rho,
+                            const double* __restrict__ ut2, int n1, int n2, int h, double rho0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int wk = blockIdx.y;  // wall * h + (k - 1)
+    if (j >= n2) return;
+    const int wall = wk / h, k = wk % h + 1;
+    const int row = wall == 0 ? k - 1 : n1 - k;  // 0-based fluid row
+    const size_t m = (size_t)row * n2 + j;
+    wr[(size_t)wk * n2 + j] = C(rho ? rho[m] : rho0);
+    wu[(size_t)wk * n2 + j] = C(ut2 ? ut2[m] : 0.0);
+}
+
+template <typename C>
+__global__ void k_wall_copy(C* __restrict__ wr, C* __restrict__ wu, const double* __restrict__ sr,
+                            const double* __restrict__ su, const double* __restrict__ rnf, int n1,
+                            int n2, int h, double rho0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int wk = blockIdx.y;
+    if (j >= n2) return;
+    const int wall = wk / h, k = wk % h + 1;
+    const int row = wall == 0 ? k - 1 : n1 - k;
+    const size_t m = (size_t)wk * n2 + j;
+    wr[m] = C(sr[m] * (rnf ? rho0 / rnf[row] : 1.0));
+    wu[m] = C(su[m]);
+}
+
+template <typename C>
+__global__ void k_rescale_wall(C* __restrict__ wr, const double* __restrict__ rnf, int n1, int n2,
+                               int h, double rho0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int wk = blockIdx.y;
+    if (j >= n2) return;
+    const int wall = wk / h, k = wk % h + 1;
+    const int row = wall == 0 ? k - 1 : n1 - k;
+    wr[(size_t)wk * n2 + j] = C(double(wr[(size_t)wk * n2 + j]) * rho0 / rnf[row]);
+}
+
+__global__ void k_scale_volume(double* __restrict__ geo, int stride, const double* __restrict__ rnf,
+                               int n1, double rho0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n1) return;
+    geo[(size_t)r * stride + Geo::J] *= rnf[r] / rho0;  // Eq. 23
+}
+
+__global__ void __launch_bounds__(256) k_row_mean(const double* __restrict__ f, int n2,
+                                                  double* __restrict__ out) {
+    __shared__ double sh[256];
+    const int i = blockIdx.x;
+    double x = 0.0;
+    for (int j = threadIdx.x; j < n2; j += 256) x += f[(size_t)i * n2 + j];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sh[0] / n2;
+}
+
+template <int Q, typename S, typename C>
+void run_moments(const MomArgs& a, int iters, int reduce, cudaStream_t s) {
+    dim3 b(RB), g((a.n2 + RB - 1) / RB, a.n1);
+    k_moments<Q, S, C><<<g, b, 0, s>>>(a, iters, reduce);
+}
+
+}  // namespace
+
+int moments_blocks(int n1, int n2) { return ((n2 + RB - 1) / RB) * n1; }
+
+void launch_moments(int Q, int prec, const MomArgs& a, int iters, int reduce, cudaStream_t s) {
+    if (Q == 9) {
+        switch (prec) {
+            case 0: run_moments<9, double, double>(a, iters, reduce, s); break;
+            case 1: run_moments<9, float, float>(a, iters, reduce, s); break;
+            case 2: run_moments<9, __half, float>(a, iters, reduce, s); break;
+            default: run_moments<9, __nv_bfloat16, float>(a, iters, reduce, s); break;
+        }
+    } else {
+        switch (prec) {
+            case 0: run_moments<21, double, double>(a, iters, reduce, s); break;
+            case 1: run_moments<21, float, float>(a, iters, reduce, s); break;
+            case 2: run_moments<21, __half, float>(a, iters, reduce, s); break;
+            default: run_moments<21, __nv_bfloat16, float>(a, iters, reduce, s); break;
+        }
+    }
+}
+
+void launch_reduce_final(const double* partial, int nblocks, double* out, cudaStream_t s) {
+    k_reduce_final<<<1, 256, 0, s>>>(partial, nblocks, out);
+}
+
+template <int Q>
+static void from64(int prec, const double* Np, const double* geo, void* st, int n1, int n2, int ld,
+                   int h, float isc, cudaStream_t s) {
+    dim3 b(128), g((n2 + 127) / 128, n1);
+    switch (prec) {
+        case 0: k_from_fp64<Q, double><<<g, b, 0, s>>>(Np, geo, (double*)st, n1, n2, ld, h, isc); break;
+        case 1: k_from_fp64<Q, float><<<g, b, 0, s>>>(Np, geo, (float*)st, n1, n2, ld, h, isc); break;
+        case 2: k_from_fp64<Q, __half><<<g, b, 0, s>>>(Np, geo, (__half*)st, n1, n2, ld, h, isc); break;
+        default: k_from_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>(Np, geo, (__nv_bfloat16*)st, n1, n2, ld, h, isc); break;
+    }
+}
+
+template <int Q>
+static void to64(int prec, const void* st, const double* geo, double* Np, int n1, int n2, int ld,
+                 int h, float isc, cudaStream_t s) {
+    dim3 b(128), g((n2 + 127) / 128, n1);
+    switch (prec) {
+        case 0: k_to_fp64<Q, double><<<g, b, 0, s>>>((const double*)st, geo, Np, n1, n2, ld, h, isc); break;
+        case 1: k_to_fp64<Q, float><<<g, b, 0, s>>>((const float*)st, geo, Np, n1, n2, ld, h, isc); break;
+        case 2: k_to_fp64<Q, __half><<<g, b, 0, s>>>((const __half*)st, geo, Np, n1, n2, ld, h, isc); break;
+        default: k_to_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>((const __nv_bfloat16*)st, geo, Np, n1, n2, ld, h, isc); break;
+    }
+}
+
+void launch_state_from_fp64(int Q, int prec, const double* Np, const double* geo, void* state,
+                            int n1, int n2, int ld, int h, float isc, cudaStream_t s) {
+    if (Q == 9) from64<9>(prec, Np, geo, state, n1, n2, ld, h, isc, s);
+    else from64<21>(prec, Np, geo, state, n1, n2, ld, h, isc, s);
+}
+
+void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo, double* Np,
+                          int n1, int n2, int ld, int h, float isc, cudaStream_t s) {
+    if (Q == 9) to64<9>(prec, state, geo, Np, n1, n2, ld, h, isc, s);
+    else to64<21>(prec, state, geo, Np, n1, n2, ld, h, isc, s);
+}
+
+void launch_wall_init(int prec, void* wr, void* wu, const double* rho, const double* ut2, int n1,
+                      int n2, int h, double rho0, cudaStream_t s) {
+    dim3 b(128), g((n2 + 127) / 128, 2 * h);
+    if (prec == 0) k_wall_init<double><<<g, b, 0, s>>>((double*)wr, (double*)wu, rho, ut2, n1, n2, h, rho0);
+    else k_wall_init<float><<<g, b, 0, s>>>((float*)wr, (float*)wu, rho, ut2, n1, n2, h, rho0);
+}
+
+void launch_rescale_wall(int prec, void* wr, const double* rnf, int n1, int n2, int h, double rho0,
+                         cudaStream_t s) {
+    dim3 b(128), g((n2 + 127) / 128, 2 * h);
+    if (prec == 0) k_rescale_wall<double><<<g, b, 0, s>>>((double*)wr, rnf, n1, n2, h, rho0);
+    else k_rescale_wall<float><<<g, b, 0, s>>>((float*)wr, rnf, n1, n2, h, rho0);
+}
+
+void launch_wall_copy(int prec, void* wr, void* wu, const double* sr, const double* su,
+                      const double* rnf, int n1, int n2, int h, double rho0, cudaStream_t s) {
+    dim3 b(128), g((n2 + 127) / 128, 2 * h);
+    if (prec == 0) k_wall_copy<double><<<g, b, 0, s>>>((double*)wr, (double*)wu, sr, su, rnf, n1, n2, h, rho0);
+    else k_wall_copy<float><<<g, b, 0, s>>>((float*)wr, (float*)wu, sr, su, rnf, n1, n2, h, rho0);
+}
+
+void launch_scale_volume(int Q, double* geo, const double* rnf, int n1, double rho0, cudaStream_t s) {
+    k_scale_volume<<<(n1 + 127) / 128, 128, 0, s>>>(geo, Geo::stride(Q), rnf, n1, rho0);
+}
+
+void launch_row_mean(const double* f, int n1, int n2, double* out, cudaStream_t s) {
+    k_row_mean<<<n1, 256, 0, s>>>(f, n2, out);
+}
+
+}  // namespace clbm

@@ -1,0 +1,155 @@
+// k_step.cu -- the fused stream-collide-force update (Sec. 2, Eqs. 6-19)
+// and the boundary ghost fill (App. B).
+//
+// One thread per cell; a warp covers 32 consecutive cells of one row, so every
+// per-row coefficient is a warp-uniform load and every population access is a
+// coalesced row segment at a constant offset (ghost rows and periodic ghost
+// columns surround the interior).  Lagged values are consumed as they are
+// loaded and new populations are stored as they are produced, so a thread
+// holds only the Q pulled deviations and the pair odd parts.  Populations are
+// deviations from the rest equilibrium of their own row (zero at rest), so
+// the large rest part never enters a rounding-sensitive difference.
+#include "clbm_cell.cuh"
+
+namespace clbm {
+
+namespace {
+
+template <int Q, typename S, typename C, bool ITER>
+__global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs a) {
+    using L = Lat<Q>;
+    using T = Tab<Q>;
+    constexpr int H = L::H;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= a.n2) return;
+    const C* __restrict__ tb = (const C*)a.tab + (size_t)i * T::S;
+    const Consts<C> k = Consts<C>::make(a.k);
+    const int row = i + H;
+    const long long off = (long long)row * a.ld + j + GC;
+    Cell<Q, C> c;
+    pull_cell<Q, S, C>((const S*)a.src + off, a.plane, a.ld, a.inv_scale, tb, k, c);
+    S* dst = (S*)a.dst + off;
+    const bool edge = j < GC || j >= a.n2 - GC;
+    if (!ITER) {
+        if (!edge) {
+            collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
+                Store<S>::st(dst + al * a.plane, v, a.inv_scale);
+            });
+        } else {
+            S* rowp = (S*)a.dst + (long long)row * a.ld;
+            collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
+                store_periodic<S, C>(rowp + al * a.plane, j, a.n2, v, a.inv_scale);
+            });
+        }
+    } else {
+        C out[Q];
+        collide_emit<Q, C>(tb, c, k, [&](int al, C v) { out[al] = v; });
+        for (int it = 0; it < a.iters; ++it) {
+            force_again<Q, C>(tb, out, k, c);
+            collide_emit<Q, C>(tb, c, k, [&](int al, C v) { out[al] = v; });
+        }
+        S* rowp = (S*)a.dst + (long long)row * a.ld;
+#pragma unroll
+        for (int al = 0; al < Q; ++al)
+            store_periodic<S, C>(rowp + al * a.plane, j, a.n2, out[al], a.inv_scale);
+    }
+    // Near-wall rows keep rho and Ut^2 for the moving-wall correction (App. B).
+    if (i < H) {
+        const int idx = (0 * H + i) * a.n2 + j;
+        ((C*)a.wall_rho)[idx] = c.rho;
+        ((C*)a.wall_ut2)[idx] = c.Ut2;
+    }
+    if (i >= a.n1 - H) {
+        const int idx = (1 * H + (a.n1 - 1 - i)) * a.n2 + j;
+        ((C*)a.wall_rho)[idx] = c.rho;
+        ((C*)a.wall_ut2)[idx] = c.Ut2;
+    }
+}
+
+// Ghost rows of both walls (App. B): for every direction that enters the
+// fluid through a wall, the ghost value is the mirrored fluid node's N' of
+// the reversed (no-slip) or reflected (moving wall) direction, plus the
+// moving-wall correction.  One thread per (wall, column).
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(128) k_boundary(const StepArgs a, S* __restrict__ st) {
+    constexpr int H = Lat<Q>::H;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int wall = blockIdx.y;
+    if (j >= a.n2) return;
+    const long long P = a.plane;
+    const int bc = wall == 0 ? a.bc_lo : a.bc_hi;
+    const C U0 = C(wall == 0 ? a.U0_lo : a.U0_hi);
+    const float isc = a.inv_scale;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        const int gr = wall == 0 ? H - k : a.n1 + H + k - 1;    // ghost state row
+        const int mr = wall == 0 ? H + k - 1 : a.n1 + H - k;    // mirrored fluid state row
+        const int widx = (wall * H + (k - 1)) * a.n2 + j;
+        const C wr = ((const C*)a.wall_rho)[widx];
+        const C wu = ((const C*)a.wall_ut2)[widx];
+#pragma unroll
+        for (int al = 1; al < Q; ++al) {
+            const int c1 = c1_of(al);
+            if (wall == 0 ? (c1 < k) : (c1 > -k)) continue;
+            const int b = bc == 0 ? opp_of(al) : hat_of(al);
+            const double* gt = a.ghost + 2 * ((wall * H + (k - 1)) * Q + al);
+            C v = C(Store<S>::ld(st + b * P + (long long)mr * a.ld + j + GC, isc));
+            v += C(gt[0]) + C(gt[1]) * wr * (U0 - wu);
+            store_periodic<S, C>(st + al * P + (long long)gr * a.ld, j, a.n2, v, isc);
+        }
+    }
+}
+
+template <int Q, typename S, typename C>
+void run_step(const StepArgs& a, cudaStream_t s) {
+    dim3 b(128), g((a.n2 + 127) / 128, a.n1);
+    if (a.iters > 0) k_fused_step<Q, S, C, true><<<g, b, 0, s>>>(a);
+    else k_fused_step<Q, S, C, false><<<g, b, 0, s>>>(a);
+}
+
+template <int Q, typename S, typename C>
+void run_boundary(const StepArgs& a, void* st, cudaStream_t s) {
+    dim3 b(128), g((a.n2 + 127) / 128, 2);
+    k_boundary<Q, S, C><<<g, b, 0, s>>>(a, (S*)st);
+}
+
+}  // namespace
+
+void launch_step(int Q, int prec, const StepArgs& a, cudaStream_t s) {
+    if (Q == 9) {
+        switch (prec) {
+            case 0: run_step<9, double, double>(a, s); break;
+            case 1: run_step<9, float, float>(a, s); break;
+            case 2: run_step<9, __half, float>(a, s); break;
+            default: run_step<9, __nv_bfloat16, float>(a, s); break;
+        }
+    } else {
+        switch (prec) {
+            case 0: run_step<21, double, double>(a, s); break;
+            case 1: run_step<21, float, float>(a, s); break;
+            case 2: run_step<21, __half, float>(a, s); break;
+            default: run_step<21, __nv_bfloat16, float>(a, s); break;
+        }
+    }
+}
+
+void launch_boundary(int Q, int prec, const StepArgs& a, void* st, cudaStream_t s) {
+    if (Q == 9) {
+        switch (prec) {
+            case 0: run_boundary<9, double, double>(a, st, s); break;
+            case 1: run_boundary<9, float, float>(a, st, s); break;
+            case 2: run_boundary<9, __half, float>(a, st, s); break;
+            default: run_boundary<9, __nv_bfloat16, float>(a, st, s); break;
+        }
+    } else {
+        switch (prec) {
+            case 0: run_boundary<21, double, double>(a, st, s); break;
+            case 1: run_boundary<21, float, float>(a, st, s); break;
+            case 2: run_boundary<21, __half, float>(a, st, s); break;
+            default: run_boundary<21, __nv_bfloat16, float>(a, st, s); break;
+        }
+    }
+}
+
+}  // namespace clbm
