@@ -160,6 +160,12 @@ clbm_status clbm_set_stream(clbm_handle h, void* stream);
 clbm_status clbm_set_profiling(clbm_handle h, int on);
 clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
 
+/* Kernel of the bulk update: 0 automatic (TMA-staged tiles where available),
+ * 1 one thread per cell with direct loads, 2 TMA-staged tiles (FP32 / FP16 /
+ * BF16 storage; the implicit-force passes always use variant 1).  Both run
+ * the same arithmetic. */
+clbm_status clbm_set_kernel(clbm_handle h, int variant);
+
 /* Number of kernel launches this grid has issued since creation. */
 clbm_status clbm_launch_count(clbm_handle h, long long* launches);
 

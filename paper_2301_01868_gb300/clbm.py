@@ -72,6 +72,7 @@ def lib():
             "clbm_set_profiling": [h, C.c_int],
             "clbm_kernel_time": [h, dp, C.POINTER(ll)],
             "clbm_launch_count": [h, C.POINTER(ll)],
+            "clbm_set_kernel": [h, C.c_int],
             "clbm_destroy": [h],
         }
         for name, args in sig.items():
@@ -246,6 +247,10 @@ class Grid:
         n = C.c_longlong()
         _check(lib().clbm_kernel_time(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def set_kernel(self, variant):
+        """0 automatic, 1 one thread per cell, 2 TMA-staged tiles."""
+        _check(lib().clbm_set_kernel(self._h, int(variant)))
 
     def launch_count(self):
         n = C.c_longlong()

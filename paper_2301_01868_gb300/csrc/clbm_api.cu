@@ -34,10 +34,12 @@ clbm_status fail(clbm_status st, const char* fmt, ...) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t stA, stB, tab, geo, wall_r, wall_u, ghost, pos, partial, red, prev, total;
+    size_t stA, stB, tab, geo, wall_r, wall_u, ghost, pos, partial, red, prev, err, total;
 };
 
 }  // namespace
+
+void clbm::set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
 struct clbm_grid {
     int Q, prec, n1, n2, ld, h, kind, bc_lo, bc_hi, device;
@@ -59,6 +61,11 @@ struct clbm_grid {
     std::vector<double> edges;
     double step2;
     double* stage;          // lazily allocated FP64 staging buffer for host transfers
+    void* phys[2];          // the two state buffers (stA / stB alternate over them)
+    TmaMaps* tma;           // tensor maps of the TMA-staged update (16/32-bit storage)
+    int nsm;                // SM count of the device
+    int variant;            // 0 auto, 1 per-cell loads, 2 TMA-staged tiles
+    int* err;               // device error word of bounded waits
 };
 
 namespace {
@@ -87,6 +94,7 @@ clbm_status layout_of(const clbm_grid_desc* d, Layout* L, int* ld_out, int* h_ou
     L->partial = take((size_t)moments_blocks(d->n1, d->n2) * NRED * 8);
     L->red = take(16 * 8);
     L->prev = take((size_t)2 * d->n1 * d->n2 * 8);
+    L->err = take(16);
     L->total = o;
     *ld_out = ld;
     *h_out = h;
@@ -143,7 +151,25 @@ StepArgs step_args(const clbm_grid* g, const void* src, void* dst) {
     a.bc_lo = g->bc_lo;
     a.bc_hi = g->bc_hi;
     a.iters = g->cs.force_iterations;
+    a.err = g->err;
     return a;
+}
+
+bool use_tma(const clbm_grid* g) {
+    if (!g->tma || g->cs.force_iterations > 0) return false;
+    return g->variant != 1;
+}
+
+// Device-side failures recorded by bounded waits since the last check.
+clbm_status check_err(clbm_grid* g) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, g->err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (e != 0) {
+        CK(cudaMemsetAsync(g->err, 0, sizeof(int), g->stream));
+        return fail(CLBM_ETIMEOUT, "a bounded device wait gave up (code %d)", e);
+    }
+    return CLBM_OK;
 }
 
 MomArgs mom_args(const clbm_grid* g) {
@@ -322,6 +348,11 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
     g->partial = (double*)(g->ws + L.partial);
     g->red = (double*)(g->ws + L.red);
     g->prev = (double*)(g->ws + L.prev);
+    g->err = (int*)(g->ws + L.err);
+    g->phys[0] = g->stA;
+    g->phys[1] = g->stB;
+    cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, d->device);
+    if (g->nsm <= 0) g->nsm = 1;
     ce = cudaMemsetAsync(g->ws, 0, L.total, g->stream);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(g->pos, pos.data(), pos.size() * 8, cudaMemcpyHostToDevice, g->stream);
@@ -334,6 +365,13 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
     if (ce != cudaSuccess) {
         clbm_destroy(g);
         return fail(CLBM_ECUDA, "geometry precompute: %s", cudaGetErrorString(ce));
+    }
+    if (g->prec != CLBM_FP64) {
+        int major = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, d->device);
+        if (major >= 9 && make_tma_maps(g->Q, g->prec, &g->tma, g->phys[0], g->phys[1], g->n1, g->n2,
+                                        g->ld) != 0)
+            g->tma = nullptr;
     }
     // every cell volume must be positive
     std::vector<double> geo((size_t)g->n1 * Geo::stride(g->Q));
@@ -463,7 +501,13 @@ clbm_status clbm_step(clbm_handle g, long long n) {
             }
             CK(cudaEventRecord(g->ev[g->ev_used], g->stream));
         }
-        launch_step(g->Q, g->prec, a, g->stream);
+        if (use_tma(g)) {
+            const int src = g->stA == g->phys[0] ? 0 : 1;
+            if (launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->stream) != 0)
+                return fail(CLBM_ECUDA, "TMA-staged update could not be launched");
+        } else {
+            launch_step(g->Q, g->prec, a, g->stream);
+        }
         if (g->profiling) {
             CK(cudaEventRecord(g->ev[g->ev_used + 1], g->stream));
             g->ev_used += 2;
@@ -513,7 +557,7 @@ clbm_status clbm_moments(clbm_handle g, double* rho, double* U1, double* U2, dou
         for (int k = 0; k < 7; ++k)
             if (outs[k]) CK(cudaMemcpyAsync(outs[k], dev[k], nc * 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
-    return CLBM_OK;
+    return check_err(g);
 }
 
 clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
@@ -531,6 +575,8 @@ clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
     double v[NRED];
     CK(cudaMemcpyAsync(v, g->red, sizeof(v), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    st = check_err(g);
+    if (st != CLBM_OK) return st;
     const long long dt = g->t - g->t_prev;
     double r = INFINITY;
     if (g->have_prev && dt > 0) r = v[1] > 0.0 ? sqrt(v[0]) / (dt * sqrt(v[1])) : (v[0] > 0 ? INFINITY : 0.0);
@@ -649,6 +695,15 @@ clbm_status clbm_kernel_time(clbm_handle g, double* ms, long long* launches) {
     return CLBM_OK;
 }
 
+clbm_status clbm_set_kernel(clbm_handle g, int variant) {
+    if (!g) return fail(CLBM_EINVAL, "handle is NULL");
+    if (variant < 0 || variant > 2) return fail(CLBM_EINVAL, "variant must be 0, 1 or 2");
+    if (variant == 2 && !g->tma)
+        return fail(CLBM_EINVAL, "the TMA-staged update needs 16/32-bit storage on sm_90 or newer");
+    g->variant = variant;
+    return CLBM_OK;
+}
+
 clbm_status clbm_launch_count(clbm_handle g, long long* launches) {
     if (!g || !launches) return fail(CLBM_EINVAL, "NULL argument");
     *launches = g->launches;
@@ -662,6 +717,7 @@ clbm_status clbm_destroy(clbm_handle g) {
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     if (g->stage) cudaFree(g->stage);
+    if (g->tma) free_tma_maps(g->tma);
     if (g->owns_ws) cudaFree(g->ws);
     delete g;
     return CLBM_OK;

@@ -39,27 +39,26 @@ struct Cell {
 // Advection (Eq. 12) with the lagged read of N'(q, t-1), moments (Eqs. 7, 8,
 // 10) and the lagged inertial force (Eq. 15 with N'(q, t-1)):
 //   F^k = -1/(2J) sum_b a^k_b [N'_b(q, t-1) + N_{opp b}(q, t)] + rho g^k.
-// p points at this cell in population plane 0 of the buffer; P is the plane
-// stride and ld the row stride (elements).
-template <int Q, typename S, typename C>
-__device__ __forceinline__ void pull_cell(const S* __restrict__ p, long long P, int ld, float isc,
-                                          const C* __restrict__ tb, const Consts<C>& k,
+// ld(alpha, dr, dc) returns the stored value of population alpha at the cell
+// offset by (dr, dc) rows / columns; dr and dc are compile-time after unrolling.
+template <int Q, typename C, typename LD>
+__device__ __forceinline__ void pull_cell(LD&& ld, const C* __restrict__ tb, const Consts<C>& k,
                                           Cell<Q, C>& c) {
     using L = Lat<Q>;
     using T = Tab<Q>;
     C Sd = tb[T::D0], S1 = tb[T::M1], S2 = tb[T::M2];
     C f1 = tb[T::F01], f2 = tb[T::F02];
-    c.d[0] = C(Store<S>::ld(p, isc));
+    c.d[0] = ld(0, 0, 0);
     Sd += c.d[0];
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const int c1 = c1_of(a), c2 = c2_of(a);
         // pulled: N_a(q) from q - c_a, N_b(q) from q + c_a; lagged: own values
-        const C pa = C(Store<S>::ld(p + a * P - (long long)c1 * ld - c2, isc));
-        const C pb = C(Store<S>::ld(p + b * P + (long long)c1 * ld + c2, isc));
-        const C la = C(Store<S>::ld(p + a * P, isc));
-        const C lb = C(Store<S>::ld(p + b * P, isc));
+        const C pa = ld(a, -c1, -c2);
+        const C pb = ld(b, c1, c2);
+        const C la = ld(a, 0, 0);
+        const C lb = ld(b, 0, 0);
         Sd += pa + pb;
         const C dp = pa - pb;
         if (c1 != 0) S1 += C(c1) * dp;
@@ -79,6 +78,19 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ p, long long P, 
     c.F1 = -C(0.5) * invJ * f1 + c.rho * k.g1;
     c.F2 = -C(0.5) * invJ * f2 + c.rho * k.g2;
 }
+
+// Loader of the global buffer: p points at the cell in population plane 0,
+// P is the plane stride and ld the row stride (elements).
+template <typename S>
+struct GlobalLoad {
+    const S* p;
+    long long P;
+    int ld;
+    float isc;
+    __device__ __forceinline__ typename Store<S>::C operator()(int al, int dr, int dc) const {
+        return Store<S>::ld(p + al * P + (long long)dr * ld + dc, isc);
+    }
+};
 
 // The force of Eq. 15 re-evaluated with the newest N'(q, t) (own-row
 // deviations out[]) for one fixed-point pass of the implicit relation.

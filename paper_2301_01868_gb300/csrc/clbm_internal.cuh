@@ -25,34 +25,47 @@
 
 namespace clbm {
 
-// Storage conversions (deviation scaled by a power of two for FP16).
+// Storage conversions (deviation scaled by a power of two for FP16).  ld
+// reads global memory through the read-only path, lds any address.
 template <typename S> struct Store;
 template <> struct Store<double> {
+    using C = double;
     __device__ static __forceinline__ double ld(const double* p, float) { return __ldg(p); }
+    __device__ static __forceinline__ double lds(const double* p, float) { return *p; }
     __device__ static __forceinline__ void st(double* p, double v, float) { *p = v; }
 };
 template <> struct Store<float> {
+    using C = float;
     __device__ static __forceinline__ float ld(const float* p, float) { return __ldg(p); }
+    __device__ static __forceinline__ float lds(const float* p, float) { return *p; }
     __device__ static __forceinline__ void st(float* p, float v, float) { *p = v; }
 };
 template <> struct Store<__half> {
+    using C = float;
     __device__ static __forceinline__ float ld(const __half* p, float inv_scale) {
         return __half2float(__ldg(p)) * inv_scale;
+    }
+    __device__ static __forceinline__ float lds(const __half* p, float inv_scale) {
+        return __half2float(*p) * inv_scale;
     }
     __device__ static __forceinline__ void st(__half* p, float v, float inv_scale) {
         *p = __float2half_rn(v / inv_scale);
     }
 };
 template <> struct Store<__nv_bfloat16> {
+    using C = float;
     __device__ static __forceinline__ float ld(const __nv_bfloat16* p, float inv_scale) {
         return __bfloat162float(__ldg(p)) * inv_scale;
+    }
+    __device__ static __forceinline__ float lds(const __nv_bfloat16* p, float inv_scale) {
+        return __bfloat162float(*p) * inv_scale;
     }
     __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, float inv_scale) {
         *p = __float2bfloat16_rn(v / inv_scale);
     }
 };
 
-constexpr int GC = 4;  // ghost columns on each side (>= widest |c^2| = 3)
+constexpr int GC = 8;  // ghost columns on each side (>= widest |c^2| = 3; 16-byte TMA origins)
 
 // Scalars of the case, in both compute types (converted once on the host).
 struct StepScalars {
@@ -75,6 +88,7 @@ struct StepArgs {
     float inv_scale;        // 1/scale of 16-bit storage (1 otherwise)
     int bc_lo, bc_hi;
     int iters;              // extra passes of the implicit force
+    int* err;               // device error word (bounded waits that gave up)
 };
 
 // Diagnostics launch arguments.
@@ -123,6 +137,17 @@ void launch_scale_volume(int Q, double* geo, const double* rho_nf_row, int n1, d
 void launch_rescale_wall(int prec, void* wall_rho, const double* rho_nf_row, int n1, int n2,
                          int h, double rho0, cudaStream_t stream);
 void launch_row_mean(const double* field, int n1, int n2, double* out, cudaStream_t stream);
+
+// TMA-staged fused update (k_step_tma.cu): tensor maps of the two state
+// buffers, their construction, and the launch (src = physical source buffer).
+struct TmaMaps;
+int make_tma_maps(int Q, int prec, TmaMaps** out, void* bufA, void* bufB, int n1, int n2, int ld);
+void free_tma_maps(TmaMaps* m);
+int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
+                    cudaStream_t s);
+
+// Set the thread-local message returned by clbm_last_error (clbm_api.cu).
+void set_last_error(const char* msg);
 
 // Size in bytes of one stored population.
 inline int storage_bytes(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters, int 
         const long long off = (long long)(i + H) * a.ld + j + GC;
         const S* p = (const S*)a.src + off;
         Cell<Q, C> c;
-        pull_cell<Q, S, C>(p, a.plane, a.ld, a.inv_scale, tb, kc, c);
+        pull_cell<Q, C>(GlobalLoad<S>{p, a.plane, a.ld, a.inv_scale}, tb, kc, c);
         if (iters > 0) {
             C out[Q];
             collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });

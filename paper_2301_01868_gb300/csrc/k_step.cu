@@ -28,20 +28,13 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs
     const int row = i + H;
     const long long off = (long long)row * a.ld + j + GC;
     Cell<Q, C> c;
-    pull_cell<Q, S, C>((const S*)a.src + off, a.plane, a.ld, a.inv_scale, tb, k, c);
+    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld, a.inv_scale}, tb, k, c);
+    // Interior only: the boundary kernel refreshes the ghost rows and the
+    // periodic ghost columns before the next step reads this buffer.
     S* dst = (S*)a.dst + off;
-    const bool edge = j < GC || j >= a.n2 - GC;
+    auto put = [&](int al, C v) { Store<S>::st(dst + al * a.plane, v, a.inv_scale); };
     if (!ITER) {
-        if (!edge) {
-            collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
-                Store<S>::st(dst + al * a.plane, v, a.inv_scale);
-            });
-        } else {
-            S* rowp = (S*)a.dst + (long long)row * a.ld;
-            collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
-                store_periodic<S, C>(rowp + al * a.plane, j, a.n2, v, a.inv_scale);
-            });
-        }
+        collide_emit<Q, C>(tb, c, k, put);
     } else {
         C out[Q];
         collide_emit<Q, C>(tb, c, k, [&](int al, C v) { out[al] = v; });
@@ -49,10 +42,8 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs
             force_again<Q, C>(tb, out, k, c);
             collide_emit<Q, C>(tb, c, k, [&](int al, C v) { out[al] = v; });
         }
-        S* rowp = (S*)a.dst + (long long)row * a.ld;
 #pragma unroll
-        for (int al = 0; al < Q; ++al)
-            store_periodic<S, C>(rowp + al * a.plane, j, a.n2, out[al], a.inv_scale);
+        for (int al = 0; al < Q; ++al) put(al, out[al]);
     }
     // Near-wall rows keep rho and Ut^2 for the moving-wall correction (App. B).
     if (i < H) {
@@ -67,20 +58,36 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs
     }
 }
 
-// Ghost rows of both walls (App. B): for every direction that enters the
-// fluid through a wall, the ghost value is the mirrored fluid node's N' of
-// the reversed (no-slip) or reflected (moving wall) direction, plus the
-// moving-wall correction.  One thread per (wall, column).
+// Ghost rows of both walls (App. B), blockIdx.y = 0 / 1: for every direction
+// that enters the fluid through a wall, the ghost value is the mirrored
+// fluid node's N' of the reversed (no-slip) or reflected (moving wall)
+// direction, plus the moving-wall correction; one thread per column.
+// blockIdx.y = 2: periodic ghost columns of the interior rows, one thread per
+// (row, population).  Together they make the buffer ready to be pulled from.
 template <int Q, typename S, typename C>
 __global__ void __launch_bounds__(128) k_boundary(const StepArgs a, S* __restrict__ st) {
     constexpr int H = Lat<Q>::H;
+    const long long P = a.plane;
+    const float isc = a.inv_scale;
+    if (blockIdx.y == 2) {
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        if (t >= a.n1 * Q) return;
+        const int al = t / a.n1, i = t % a.n1;
+        S* rowp = st + al * P + (long long)(i + H) * a.ld;
+#pragma unroll
+        for (int e = 0; e < 2 * GC; ++e) {
+            const int cs = e < GC ? e : a.n2 + e;  // ghost state column
+            int jw = (cs - GC) % a.n2;
+            if (jw < 0) jw += a.n2;
+            rowp[cs] = rowp[jw + GC];
+        }
+        return;
+    }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int wall = blockIdx.y;
     if (j >= a.n2) return;
-    const long long P = a.plane;
     const int bc = wall == 0 ? a.bc_lo : a.bc_hi;
     const C U0 = C(wall == 0 ? a.U0_lo : a.U0_hi);
-    const float isc = a.inv_scale;
 #pragma unroll
     for (int k = 1; k <= H; ++k) {
         const int gr = wall == 0 ? H - k : a.n1 + H + k - 1;    // ghost state row
@@ -110,7 +117,8 @@ void run_step(const StepArgs& a, cudaStream_t s) {
 
 template <int Q, typename S, typename C>
 void run_boundary(const StepArgs& a, void* st, cudaStream_t s) {
-    dim3 b(128), g((a.n2 + 127) / 128, 2);
+    const int nx = (a.n2 + 127) / 128, ny = (a.n1 * Q + 127) / 128;
+    dim3 b(128), g(nx > ny ? nx : ny, 3);
     k_boundary<Q, S, C><<<g, b, 0, s>>>(a, (S*)st);
 }
 

@@ -1,0 +1,345 @@
+// k_step_tma.cu -- the fused stream-collide-force update with TMA staging.
+//
+// Same arithmetic as k_fused_step (clbm_cell.cuh), organised for sm_103a:
+// persistent CTAs, one per SM, walk tiles of TR x TJ cells.  For every tile
+// one thread issues one TMA box per population: rows [i0 - max(c1,0),
+// i0 + TR + max(-c1,0)) and the columns the pull reaches (8-column halo only
+// where c2 != 0), so each population plane brings exactly the rows and columns
+// its pull and its lagged read touch (about 1.33 x the tile for D2Q21).  Tiles
+// are double buffered behind mbarriers, so the loads of tile k+1 overlap the
+// arithmetic of tile k.  Every shared-memory offset of a pull is a compile-time
+// constant.  New populations go to a shared output tile that one TMA store
+// writes back.  Waits on mbarriers are bounded: on time-out the kernel records
+// an error code and returns.
+#include <cuda.h>
+
+#include "clbm_cell.cuh"
+
+namespace clbm {
+
+// Shared-memory layout of one tile (elements of the storage type S).
+template <int Q, typename S>
+struct TileGeom {
+    static constexpr int TR = 8, TJ = 64, NT = TR * TJ;
+    static constexpr int HX = 8;                                  // column halo where c2 != 0
+    static constexpr int ALIGN = 128 / (int)sizeof(S);            // keep sub-tiles 128-B aligned
+    __host__ __device__ static constexpr int iabs(int x) { return x < 0 ? -x : x; }
+    __host__ __device__ static constexpr int rows(int a) { return TR + iabs(c1_of(a)); }
+    __host__ __device__ static constexpr int width(int a) { return c2_of(a) == 0 ? TJ : TJ + 2 * HX; }
+    __host__ __device__ static constexpr int row0(int a) { return c1_of(a) > 0 ? c1_of(a) : 0; }
+    __host__ __device__ static constexpr int col0(int a) { return c2_of(a) == 0 ? 0 : HX; }
+    __host__ __device__ static constexpr int size(int a) {
+        return (rows(a) * width(a) + ALIGN - 1) / ALIGN * ALIGN;
+    }
+    __host__ __device__ static constexpr int off(int a) {
+        int s = 0;
+        for (int b = 0; b < a; ++b) s += size(b);
+        return s;
+    }
+    __host__ __device__ static constexpr int shape(int a) { return iabs(c1_of(a)) * 2 + (c2_of(a) != 0); }
+    static constexpr int BUF = off(Q);                            // elements per input buffer
+    static constexpr int OUT = Q * TR * TJ;                       // elements of the output tile
+    static constexpr int TABB = TR * Tab<Q>::S * 4;               // bytes of one table block
+    static constexpr int SMEM = 2 * BUF * (int)sizeof(S) + OUT * (int)sizeof(S) + 2 * TABB + 64 + 128;
+};
+
+// Tensor maps of both state buffers: per buffer, the 8 box shapes of the loads
+// (|c1| = 0..3, c2 zero / nonzero) and the interior map of the tile store.
+struct TmaMaps {
+    CUtensorMap ld[2][8];
+    CUtensorMap st[2];
+};
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store3(const CUtensorMap* map, int x, int y, int z, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_addr(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int Q, typename S, typename C>
+__device__ __forceinline__ void issue_tile(const TmaMaps& maps, int buf, int tile, int tiles_j,
+                                           const StepArgs& a, unsigned char* sm_in, unsigned char* sm_tab,
+                                           uint64_t* bar) {
+    using G = TileGeom<Q, S>;
+    constexpr int H = Lat<Q>::H;
+    const int i0 = (tile / tiles_j) * G::TR, j0 = (tile % tiles_j) * G::TJ;
+    const int nrows = a.n1 - i0 < G::TR ? a.n1 - i0 : G::TR;
+    uint32_t bytes = (uint32_t)nrows * Tab<Q>::S * 4;
+#pragma unroll
+    for (int al = 0; al < Q; ++al) bytes += G::rows(al) * G::width(al) * (int)sizeof(S);
+    mbar_expect(bar, bytes);
+    S* in = (S*)sm_in;
+#pragma unroll
+    for (int al = 0; al < Q; ++al)
+        tma_load3(in + G::off(al), &maps.ld[buf][G::shape(al)], j0 + GC - G::col0(al),
+                  i0 + H - G::row0(al), al, bar);
+    bulk_load(sm_tab, (const C*)a.tab + (size_t)i0 * Tab<Q>::S, (uint32_t)nrows * Tab<Q>::S * 4, bar);
+}
+
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
+    k_fused_tma(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
+    using G = TileGeom<Q, S>;
+    using T = Tab<Q>;
+    constexpr int H = Lat<Q>::H;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    unsigned char* const in_base = smem;
+    S* const sm_out = (S*)(smem + 2 * G::BUF * sizeof(S));
+    unsigned char* const tab_base = smem + 2 * G::BUF * sizeof(S) + G::OUT * sizeof(S);
+    uint64_t* const bar = (uint64_t*)(tab_base + 2 * G::TABB);
+    int* const s_abort_p = (int*)(bar + 2);
+#define s_abort (*s_abort_p)
+    auto sm_in = [&](int b) { return in_base + b * (G::BUF * sizeof(S)); };
+    auto sm_tab = [&](int b) { return tab_base + b * G::TABB; };
+
+    const int tid = threadIdx.x;
+    const int r = tid / G::TJ, cc = tid % G::TJ;
+    const int tiles_j = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * tiles_j;
+    const Consts<C> k = Consts<C>::make(a.k);
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int tile = blockIdx.x;
+    int it = 0;
+    bool next_issued = false;
+    if (tid == 0 && tile < ntiles)
+        issue_tile<Q, S, C>(maps, src, tile, tiles_j, a, sm_in(0), sm_tab(0), &bar[0]);
+    for (; tile < ntiles; ++it, tile += gridDim.x) {
+        const int buf = it & 1;
+        const int next = tile + gridDim.x;
+        next_issued = next < ntiles;
+        if (tid == 0 && next_issued)
+            issue_tile<Q, S, C>(maps, src, next, tiles_j, a, sm_in(buf ^ 1), sm_tab(buf ^ 1),
+                                &bar[buf ^ 1]);
+        if (!mbar_wait(&bar[buf], (it >> 1) & 1)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+        const int i0 = (tile / tiles_j) * G::TR, j0 = (tile % tiles_j) * G::TJ;
+        const int i = i0 + r, j = j0 + cc;
+        if (i < a.n1 && j < a.n2) {
+            const C* tb = (const C*)sm_tab(buf) + r * T::S;
+            const S* in = (const S*)sm_in(buf);
+            const float isc = a.inv_scale;
+            Cell<Q, C> c;
+            pull_cell<Q, C>(
+                [&](int al, int dr, int dc) -> C {
+                    return C(Store<S>::lds(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) +
+                                               cc + G::col0(al) + dc,
+                                           isc));
+                },
+                tb, k, c);
+            S* out = sm_out + r * G::TJ + cc;
+            collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
+                Store<S>::st(out + al * (G::TR * G::TJ), v, isc);
+            });
+            if (i < H) {
+                const int idx = i * a.n2 + j;
+                ((C*)a.wall_rho)[idx] = c.rho;
+                ((C*)a.wall_ut2)[idx] = c.Ut2;
+            }
+            if (i >= a.n1 - H) {
+                const int idx = (H + (a.n1 - 1 - i)) * a.n2 + j;
+                ((C*)a.wall_rho)[idx] = c.rho;
+                ((C*)a.wall_ut2)[idx] = c.Ut2;
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tma_store3(&maps.st[src ^ 1], j0, i0, 0, sm_out);
+            bulk_wait_read();
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        bulk_wait_all();
+        if (s_abort) {
+            atomicExch(a.err, 1);
+            // let the loads that may still be in flight land before the CTA exits
+            const int buf = it & 1;
+            mbar_wait(&bar[buf], (it >> 1) & 1);
+            if (next_issued) mbar_wait(&bar[buf ^ 1], ((it + 1) >> 1) & 1);
+        }
+    }
+#undef s_abort
+}
+
+}  // namespace
+
+template <int Q, typename S>
+static int run_tma(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cudaStream_t s) {
+    using G = TileGeom<Q, S>;
+    using C = typename Store<S>::C;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_fused_tma<Q, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 G::SMEM) != cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    const int tiles = ((a.n1 + G::TR - 1) / G::TR) * ((a.n2 + G::TJ - 1) / G::TJ);
+    const int grid = tiles < nsm ? tiles : nsm;
+    k_fused_tma<Q, S, C><<<grid, G::NT, G::SMEM, s>>>(maps, a, src);
+    return 0;
+}
+
+int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
+                    cudaStream_t s) {
+    if (Q == 9) {
+        switch (prec) {
+            case 1: return run_tma<9, float>(maps, a, src, nsm, s);
+            case 2: return run_tma<9, __half>(maps, a, src, nsm, s);
+            case 3: return run_tma<9, __nv_bfloat16>(maps, a, src, nsm, s);
+            default: return -1;
+        }
+    }
+    switch (prec) {
+        case 1: return run_tma<21, float>(maps, a, src, nsm, s);
+        case 2: return run_tma<21, __half>(maps, a, src, nsm, s);
+        case 3: return run_tma<21, __nv_bfloat16>(maps, a, src, nsm, s);
+        default: return -1;
+    }
+}
+
+// Encode the tensor maps of both state buffers (host).
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+
+template <int Q, typename S>
+static int encode_maps(EncodeFn enc, TmaMaps* m, void* bufA, void* bufB, int n1, int n2, int ld,
+                       CUtensorMapDataType dt) {
+    using G = TileGeom<Q, S>;
+    constexpr int H = Lat<Q>::H;
+    const cuuint64_t es = sizeof(S);
+    cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)(n1 + 2 * H), (cuuint64_t)Q};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * es, (cuuint64_t)(n1 + 2 * H) * ld * es};
+    cuuint32_t estr[3] = {1, 1, 1};
+    void* bases[2] = {bufA, bufB};
+    for (int b = 0; b < 2; ++b) {
+        for (int shape = 0; shape < 8; ++shape) {
+            const int ac1 = shape / 2, has2 = shape & 1;
+            cuuint32_t box[3] = {(cuuint32_t)(has2 ? G::TJ + 2 * G::HX : G::TJ), (cuuint32_t)(G::TR + ac1), 1};
+            if (enc(&m->ld[b][shape], dt, 3, bases[b], dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return -1;
+        }
+        // interior view for the tile store: origin at (row H, column GC)
+        char* ib = (char*)bases[b] + ((size_t)H * ld + GC) * es;
+        cuuint64_t idims[3] = {(cuuint64_t)n2, (cuuint64_t)n1, (cuuint64_t)Q};
+        cuuint32_t obox[3] = {(cuuint32_t)G::TJ, (cuuint32_t)G::TR, (cuuint32_t)Q};
+        if (enc(&m->st[b], dt, 3, ib, idims, strides, obox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -1;
+    }
+    return 0;
+}
+
+int make_tma_maps(int Q, int prec, TmaMaps** out, void* bufA, void* bufB, int n1, int n2, int ld) {
+    static EncodeFn enc = nullptr;
+    if (!enc) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return -1;
+        enc = (EncodeFn)fn;
+    }
+    TmaMaps* m = new TmaMaps();
+    int rc = -1;
+    if (Q == 9) {
+        if (prec == 1) rc = encode_maps<9, float>(enc, m, bufA, bufB, n1, n2, ld, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+        else if (prec == 2) rc = encode_maps<9, __half>(enc, m, bufA, bufB, n1, n2, ld, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+        else if (prec == 3) rc = encode_maps<9, __nv_bfloat16>(enc, m, bufA, bufB, n1, n2, ld, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    } else {
+        if (prec == 1) rc = encode_maps<21, float>(enc, m, bufA, bufB, n1, n2, ld, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+        else if (prec == 2) rc = encode_maps<21, __half>(enc, m, bufA, bufB, n1, n2, ld, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+        else if (prec == 3) rc = encode_maps<21, __nv_bfloat16>(enc, m, bufA, bufB, n1, n2, ld, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    }
+    if (rc != 0) {
+        delete m;
+        return -1;
+    }
+    *out = m;
+    return 0;
+}
+
+void free_tma_maps(TmaMaps* m) { delete m; }
+
+}  // namespace clbm
