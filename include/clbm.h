@@ -169,6 +169,24 @@ clbm_status clbm_set_kernel(clbm_handle h, int variant);
 /* Number of kernel launches this grid has issued since creation. */
 clbm_status clbm_launch_count(clbm_handle h, long long* launches);
 
+/* Totals of a population array without allocating device memory: out[0] =
+ * sum N', out[1] = sum c^1 N', out[2] = sum c^2 N' over Np, a device array of
+ * FP64 populations [Q][n1][n2] (the layout clbm_get_state writes).  out is 3
+ * doubles in device memory (out_is_device = 1, asynchronous) or host memory
+ * (synchronises).  Work goes on `stream` of the current device.
+ * The paper has no counterpart: this is for callers that must not allocate,
+ * such as code running while a stream is captured into a CUDA graph
+ * (cudaMalloc cannot be captured) or a process confined to a fixed memory
+ * budget.  It calls no cudaMalloc or cudaFree; its scratch is a static device
+ * array of 8192 * 3 + 3 doubles (196 632 bytes) that every GPU which loads
+ * the library keeps until exit, so n1 * n2 may not exceed 2 097 152 (larger
+ * grids get CLBM_EINVAL).  The first call on each device looks up that
+ * array's device address; make that first call before any stream capture.
+ * All calls share the scratch: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. */
+clbm_status clbm_totals_noalloc(int lattice, const double* Np, int n1, int n2, double* out,
+                                int out_is_device, void* stream);
+
 /* Free everything the grid owns.  NULL is accepted. */
 clbm_status clbm_destroy(clbm_handle h);
 
