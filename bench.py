@@ -47,6 +47,7 @@ DEFAULT = "circular_couette_d2q21_fp32_1024x4096"
 METRIC = "D2Q21 curvilinear MLUPS and % HBM roofline; served solves/s, p99 latency"
 STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
 KERNEL_SOURCES = ["paper_2301_01868_gb300/csrc/k_step.cu",
+                  "paper_2301_01868_gb300/csrc/k_step_tma.cu",
                   "paper_2301_01868_gb300/csrc/clbm_cell.cuh",
                   "paper_2301_01868_gb300/csrc/clbm_internal.cuh",
                   "paper_2301_01868_gb300/csrc/clbm_lattice.cuh"]
@@ -69,9 +70,11 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def traffic_for(workload):
-    """Per-launch DRAM bytes of the fused kernel from the committed ncu summary,
-    only if it was taken on the current kernel source."""
+def traffic_for(workload, kernel):
+    """Per-launch DRAM bytes of the timed update kernel from the committed ncu
+    summary, only if it was taken on the current kernel source (kernel 1: the
+    per-cell kernel; otherwise the TMA-staged one, the automatic choice for
+    16/32-bit storage)."""
     p = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
     if not os.path.exists(p):
         return None
@@ -80,7 +83,7 @@ def traffic_for(workload):
     e = d.get(workload)
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
-    return e.get("bytes_per_launch")
+    return e.get("bytes_per_launch_per_cell_kernel" if kernel == 1 else "bytes_per_launch")
 
 
 class Clocks:
@@ -135,6 +138,20 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells, chunk, steps, world, ms_max):
+    """Cell updates of every rank's replica per second of the slowest rank, in millions."""
+    return cells * chunk * steps * world / (ms_max * 1e-3) / 1e6
 
 
 def smi_index(local):
@@ -212,6 +229,7 @@ def config_of(wl, args):
     return {"workload": wl, "lattice": "D2Q%d" % Q, "n1": n1, "n2": n2, "geometry":
             "annulus R2/R1=%g, radial CR=%g" % (R2 / R1, CR), "tau": tau, "u_wall": uw,
             "storage": prec, "chunk": args.chunk,
+            "kernel": {0: "auto", 1: "per-cell", 2: "tma-tiles"}[args.kernel],
             "l2": "inputs larger than L2 (state %d MB)" % (2 * Q * n1 * n2 * STORAGE_BYTES[prec] >> 20),
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -226,9 +244,18 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="0 automatic, 1 one thread per cell, 2 TMA-staged tiles")
+    ap.add_argument("--serve", action="store_true",
+                    help="only the serving comparison (continuous batching vs serial solves)")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        print(json.dumps(run_serving(args.serve_requests, verbose=True)))
+        return
 
     import torch
     from paper_2301_01868_gb300 import clbm
@@ -253,6 +280,8 @@ def main():
     g = clbm.Grid(Q, n1, n2, e, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING,
                   bc_hi=clbm.NOSLIP, device=local, stream=stream)
     g.set_case(tau, 1.0, U0, 0.0)
+    if args.kernel:
+        g.set_kernel(args.kernel)
 
     def bench_step():
         g.step(args.chunk)
@@ -278,19 +307,15 @@ def main():
     ms = ev0.elapsed_time(ev1)
     kms, kl = g.kernel_time()
     g.set_profiling(False)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
     cells = n1 * n2
-    upd = cells * args.chunk * args.steps * world
-    value = upd / (ms_max * 1e-3) / 1e6
+    value = whole_job_mlups(cells, args.chunk, args.steps, world, ms_max)
     sb = STORAGE_BYTES[prec]
     bytes_per_launch = 2 * Q * sb * cells
     achieved = bytes_per_launch / (kms / kl * 1e-3) / 1e9 if kl else None
     peak, peak_src = peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": traffic_for(wl),
+            "frac": achieved / peak if achieved else None, "traffic": traffic_for(wl, args.kernel) if prec != "fp64" else None,
             "peak_source": peak_src + " (hbm_gbs)", "algorithmic_bytes_per_launch": bytes_per_launch,
             "kernel_ms_avg": kms / kl if kl else None}
 
@@ -308,11 +333,37 @@ def main():
            "residual_last": last[0] if last else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0 and world == 1 and not args.no_serve:
+        out["serving"] = run_serving(args.serve_requests)
     if rank == 0:
         print(json.dumps(out))
     g.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_serving(n, verbose=False):
+    """Served solves/s and time-to-converged: a seeded Poisson stream of solve
+    requests (the four flows, D2Q9 / D2Q21 at random, sizes log-uniform on a
+    scaled ladder 8..32 x 8..64, tau in [0.55, 1], target speed in
+    [1e-3, 1e-2], residual tolerance 1e-8, FP32 state, 150 GB budget) through
+    the continuous-batching server and, as the baseline, the same requests
+    solved one after another with single-lattice launches."""
+    from paper_2301_01868_gb300 import serve
+    rate = 200.0
+    kw = dict(n1_range=(8, 32), n2_range=(8, 64), tol=1e-8, max_steps=150000)
+    srv = serve.Server(precision="fp32", hbm_budget=150e9, chunk=100)
+    for r in serve.poisson_requests(n, rate, **kw):
+        srv.submit(r)
+    batched = srv.run()
+    _, serial = serve.serve_serial(serve.poisson_requests(n, rate, **kw), precision="fp32", chunk=100)
+    out = {"requests": n, "arrival_rate_per_s": rate,
+           "ladder": "n1 8..32, n2 8..64 log-uniform; tol 1e-8; cap 150000 steps",
+           "batched": batched, "serial": serial,
+           "speedup_solves_per_s": batched["solves_per_s"] / serial["solves_per_s"],
+           "speedup_converged_per_s": (batched["converged_per_s"] / serial["converged_per_s"]
+                                       if serial["converged_per_s"] > 0 else None)}
+    return out
 
 
 def run_e2e(g, args, torch, stream, world, dist, cells, Q):
@@ -337,11 +388,7 @@ def run_e2e(g, args, torch, stream, world, dist, cells, Q):
     for _ in range(args.steps):
         one()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dt = float(t.item())
+    dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     return {"value": cells * args.chunk * args.steps * world / dt / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": Q * cells * 8, "d2h_bytes_per_step": 3 * cells * 8,
             "note": "per step: state upload (FP64 N'), %d time steps, moments download" % args.chunk}

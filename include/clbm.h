@@ -187,6 +187,34 @@ clbm_status clbm_launch_count(clbm_handle h, long long* launches);
 clbm_status clbm_totals_noalloc(int lattice, const double* Np, int n1, int n2, double* out,
                                 int out_is_device, void* stream);
 
+/* ---- Batches: many lattices advanced together (one persistent launch per
+ * phase over a work-list of tiles, two steps per CUDA graph).  The grids
+ * share lattice, precision, device and stream and are not owned by the
+ * batch; step them only through the batch while it exists (a grid stepped on
+ * its own is picked up again on the next batch step).  Grids whose case sets
+ * force_iterations > 0 (the implicit force of Sec. 2) are updated by a second
+ * persistent launch per step with a fixed 128 x 1 tile; the variant and the
+ * autotuner apply to the lagged-force grids.  Each grid gives the same
+ * result as its own clbm_step.  Work goes on the first grid's stream
+ * (graphs need a non-default stream). */
+typedef struct clbm_batch* clbm_batch_handle;
+clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle* out);
+/* Advance every grid of the batch n time steps.  Asynchronous. */
+clbm_status clbm_batch_step(clbm_batch_handle b, long long n);
+/* clbm_residual for every grid in one pass: res[n], cons[n][6].  Synchronises. */
+clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons);
+/* Update tile of the batched kernel: 0 = 128 x 1 cells, 1 = 256 x 1 cells
+ * (2 per thread), 2 = 32 x 4 cells, 3 = 64 x 1 cells. */
+clbm_status clbm_batch_set_variant(clbm_batch_handle b, int variant);
+/* Autotuner: times every variant for `steps` steps on this batch (advancing
+ * every grid by 4 (steps + 1) steps), keeps the fastest and caches the choice
+ * for batches of the same lattice, precision and shape class in this process.
+ * best (may be NULL) receives the variant, ms_per_step[4] (may be NULL) the
+ * timings.  Synchronises. */
+clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* ms_per_step);
+clbm_status clbm_batch_launch_count(clbm_batch_handle b, long long* launches);
+clbm_status clbm_batch_destroy(clbm_batch_handle b);
+
 /* Free everything the grid owns.  NULL is accepted. */
 clbm_status clbm_destroy(clbm_handle h);
 

@@ -73,6 +73,13 @@ def lib():
             "clbm_kernel_time": [h, dp, C.POINTER(ll)],
             "clbm_launch_count": [h, C.POINTER(ll)],
             "clbm_set_kernel": [h, C.c_int],
+            "clbm_batch_create": [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)],
+            "clbm_batch_step": [h, ll],
+            "clbm_batch_residual": [h, vp, vp],
+            "clbm_batch_set_variant": [h, C.c_int],
+            "clbm_batch_tune": [h, C.c_int, C.POINTER(C.c_int), vp],
+            "clbm_batch_launch_count": [h, C.POINTER(ll)],
+            "clbm_batch_destroy": [h],
             "clbm_destroy": [h],
         }
         for name, args in sig.items():
@@ -256,6 +263,58 @@ class Grid:
         n = C.c_longlong()
         _check(lib().clbm_launch_count(self._h, C.byref(n)))
         return n.value
+
+
+class Batch:
+    """Several grids (same lattice, precision and device) advanced together by
+    one persistent launch per phase, two steps per CUDA graph.  The grids stay
+    owned by the caller and must outlive the batch."""
+
+    VARIANTS = 4
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (C.c_void_p * len(self.grids))(*[g._h.value for g in self.grids])
+        h = C.c_void_p()
+        _check(lib().clbm_batch_create(arr, len(self.grids), C.byref(h)))
+        self._h = h
+
+    def step(self, n=1):
+        _check(lib().clbm_batch_step(self._h, int(n)))
+
+    def residual(self):
+        """(res[n], cons[n, 6]) for every grid, as clbm_residual gives them."""
+        n = len(self.grids)
+        res = np.empty(n)
+        cons = np.empty((n, 6))
+        _check(lib().clbm_batch_residual(self._h, res.ctypes.data, cons.ctypes.data))
+        return res, cons
+
+    def set_variant(self, v):
+        _check(lib().clbm_batch_set_variant(self._h, int(v)))
+
+    def tune(self, steps=5):
+        """Time every tile variant on this batch; keeps and returns the fastest."""
+        best = C.c_int()
+        ms = np.empty(self.VARIANTS)
+        _check(lib().clbm_batch_tune(self._h, int(steps), C.byref(best), ms.ctypes.data))
+        return best.value, ms
+
+    def launch_count(self):
+        n = C.c_longlong()
+        _check(lib().clbm_batch_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().clbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def wall_speed_planar(u_phys, step2, dx):

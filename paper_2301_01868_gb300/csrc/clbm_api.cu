@@ -6,7 +6,13 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "../../include/clbm.h"
+#include "clbm_batch.cuh"
 #include "clbm_internal.cuh"
 
 using namespace clbm;
@@ -50,8 +56,8 @@ struct clbm_grid {
     Layout L;
     void *stA, *stB, *tab, *wall_r, *wall_u;
     double *geo, *ghost, *pos, *partial, *red, *prev;
-    float inv_scale;
     clbm_case cs;
+    bool ghosts_ok;         // ghost rows / columns of the current state are filled
     bool have_case;
     long long t, t_prev, launches;
     bool have_prev;
@@ -147,7 +153,6 @@ StepArgs step_args(const clbm_grid* g, const void* src, void* dst) {
     a.g2 = g->cs.g_ext[1];
     a.U0_lo = g->cs.u_wall_lo;
     a.U0_hi = g->cs.u_wall_hi;
-    a.inv_scale = g->inv_scale;
     a.bc_lo = g->bc_lo;
     a.bc_hi = g->bc_hi;
     a.iters = g->cs.force_iterations;
@@ -188,7 +193,6 @@ MomArgs mom_args(const clbm_grid* g) {
     m.rho0 = g->cs.rho0;
     m.g1 = g->cs.g_ext[0];
     m.g2 = g->cs.g_ext[1];
-    m.inv_scale = g->inv_scale;
     m.ut_prev = g->prev;
     m.partial = g->partial;
     return m;
@@ -214,11 +218,15 @@ clbm_status staging(clbm_grid* g, double** out) {
     return CLBM_OK;
 }
 
-// Ghost rows of the current state (what the next collision pulls).
+// Ghost rows and columns of the current state (what the next collision
+// pulls), rebuilt only after the state or the case was set from outside:
+// every update fills those of the buffer it writes.
 void fill_ghosts(clbm_grid* g) {
+    if (g->ghosts_ok) return;
     StepArgs a = step_args(g, g->stA, g->stB);
     launch_boundary(g->Q, g->prec, a, g->stA, g->stream);
     g->launches++;
+    g->ghosts_ok = true;
 }
 
 clbm_status rebuild_tables(clbm_grid* g) {
@@ -313,7 +321,6 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
     g->dx = dx;
     g->stream = (cudaStream_t)d->stream;
     g->L = L;
-    g->inv_scale = d->precision == CLBM_FP32_F16STORE ? 1.0f / 4096.0f : 1.0f;
     g->edges = e;
     g->step2 = d->step2;
     cudaError_t ce = cudaSetDevice(d->device);
@@ -400,13 +407,14 @@ clbm_status clbm_set_case(clbm_handle g, const clbm_case* c) {
     st = rebuild_tables(g);
     if (st != CLBM_OK) return st;
     launch_state_from_fp64(g->Q, g->prec, nullptr, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
-                           g->inv_scale, g->stream);
+                           g->stream);
     launch_wall_init(g->prec, g->wall_r, g->wall_u, nullptr, nullptr, g->n1, g->n2, g->h,
                      c->rho0, g->stream);
     g->launches += 2;
     CK(cudaGetLastError());
     g->t = 0;
     g->have_prev = false;
+    g->ghosts_ok = false;
     return CLBM_OK;
 }
 
@@ -439,7 +447,7 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
             }
         }
         launch_state_from_fp64(g->Q, g->prec, dN, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
-                               g->inv_scale, g->stream);
+                               g->stream);
         launch_wall_init(g->prec, g->wall_r, g->wall_u, dr, du, g->n1, g->n2, g->h, g->cs.rho0,
                          g->stream);
         g->launches += 2;
@@ -448,7 +456,7 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
         cudaFree(extra);
     } else {
         launch_state_from_fp64(g->Q, g->prec, dN, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
-                               g->inv_scale, g->stream);
+                               g->stream);
         launch_wall_init(g->prec, g->wall_r, g->wall_u, dr, du, g->n1, g->n2, g->h, g->cs.rho0,
                          g->stream);
         g->launches += 2;
@@ -456,6 +464,7 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
         CK(cudaStreamSynchronize(g->stream));
     }
     g->have_prev = false;
+    g->ghosts_ok = false;
     return CLBM_OK;
 }
 
@@ -470,7 +479,7 @@ clbm_status clbm_get_state(clbm_handle g, double* Np, int dst_is_device) {
         if (st != CLBM_OK) return st;
     }
     launch_state_to_fp64(g->Q, g->prec, g->stA, g->geo, dN, g->n1, g->n2, g->ld, g->h,
-                         g->inv_scale, g->stream);
+                         g->stream);
     g->launches++;
     CK(cudaGetLastError());
     if (!dst_is_device) {
@@ -488,9 +497,9 @@ clbm_status clbm_step(clbm_handle g, long long n) {
     if (n < 0) return fail(CLBM_EINVAL, "n < 0");
     clbm_status st = select(g);
     if (st != CLBM_OK) return st;
+    fill_ghosts(g);
     for (long long s = 0; s < n; ++s) {
         StepArgs a = step_args(g, g->stA, g->stB);
-        launch_boundary(g->Q, g->prec, a, g->stA, g->stream);
         if (g->profiling) {
             if (g->ev_used + 2 > g->ev.size()) {
                 for (int k = 0; k < 256; ++k) {
@@ -512,7 +521,7 @@ clbm_status clbm_step(clbm_handle g, long long n) {
             CK(cudaEventRecord(g->ev[g->ev_used + 1], g->stream));
             g->ev_used += 2;
         }
-        g->launches += 2;
+        g->launches += 1;
         void* t = g->stA;
         g->stA = g->stB;
         g->stB = t;
@@ -638,7 +647,7 @@ clbm_status clbm_no_flow_adjust(clbm_handle g, long long nsteps, double* rho_nf)
     if (st == CLBM_OK) {
         // keep the no-flow state; its last-collision densities scale by rho0/rho_nf
         launch_state_from_fp64(g->Q, g->prec, Np, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
-                               g->inv_scale, g->stream);
+                               g->stream);
         launch_wall_copy(g->prec, g->wall_r, g->wall_u, (const double*)nf->wall_r,
                          (const double*)nf->wall_u, rowm, g->n1, g->n2, g->h, g->cs.rho0, g->stream);
         g->launches += 2;
@@ -656,6 +665,7 @@ clbm_status clbm_no_flow_adjust(clbm_handle g, long long nsteps, double* rho_nf)
     clbm_destroy(nf);
     g->t = 0;
     g->have_prev = false;
+    g->ghosts_ok = false;
     return st;
 }
 
@@ -720,6 +730,413 @@ clbm_status clbm_destroy(clbm_handle g) {
     if (g->tma) free_tma_maps(g->tma);
     if (g->owns_ws) cudaFree(g->ws);
     delete g;
+    return CLBM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct clbm_batch {
+    std::vector<clbm_grid*> g;
+    int Q, prec, device;
+    cudaStream_t stream;
+    int variant;
+    int phase;                       // time steps taken through the batch, mod 2
+    BatchGrid* d_grids;
+    std::vector<BatchGrid> h_grids;
+    int4* d_step[BATCH_VARIANTS];    // update tiles of lagged-force lattices, per variant
+    int nstep[BATCH_VARIANTS];
+    int4* d_iter;                    // update tiles of lattices that iterate the force
+    int niter;
+    int4* d_bnd;
+    int nbnd;
+    int4* d_mom;
+    int nmom;
+    int2* d_range;
+    double* d_partial;
+    double* d_out;
+    int nblk;
+    cudaGraphExec_t graph[2];
+    long long launches;
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;  // (Q, prec, width class, size class)
+
+std::tuple<int, int, int, int> shape_class(const clbm_batch* b) {
+    std::vector<int> w;
+    long long cells = 0;
+    for (clbm_grid* g : b->g) {
+        w.push_back(g->n2);
+        cells += (long long)g->n1 * g->n2;
+    }
+    std::sort(w.begin(), w.end());
+    int wc = 0, sc = 0;
+    for (int m = w[w.size() / 2]; m > 32; m >>= 1) ++wc;
+    for (long long c = cells; c > 65536; c >>= 2) ++sc;
+    return std::make_tuple(b->Q, b->prec, wc, sc);
+}
+
+void fill_desc(clbm_batch* b) {
+    b->h_grids.resize(b->g.size());
+    for (size_t k = 0; k < b->g.size(); ++k) {
+        clbm_grid* g = b->g[k];
+        BatchGrid& d = b->h_grids[k];
+        d.phys[0] = g->phys[0];
+        d.phys[1] = g->phys[1];
+        d.tab = g->tab;
+        d.wall_rho = g->wall_r;
+        d.wall_ut2 = g->wall_u;
+        d.ghost = g->ghost;
+        d.geo = g->geo;
+        d.prev = g->prev;
+        d.k = scalars(g->cs);
+        d.U0_lo = g->cs.u_wall_lo;
+        d.U0_hi = g->cs.u_wall_hi;
+        d.plane = (long long)(g->n1 + 2 * g->h) * g->ld;
+        d.n1 = g->n1;
+        d.n2 = g->n2;
+        d.ld = g->ld;
+        // source buffer at batch phase 0 given the grid's current source now
+        const int cur = g->stA == g->phys[0] ? 0 : 1;
+        d.parity = cur ^ b->phase;
+        d.bc_lo = g->bc_lo;
+        d.bc_hi = g->bc_hi;
+        d.have_prev = g->have_prev ? 1 : 0;
+        d.iters = g->cs.force_iterations;
+    }
+}
+
+clbm_status upload_desc(clbm_batch* b) {
+    fill_desc(b);
+    CK(cudaMemcpyAsync(b->d_grids, b->h_grids.data(), b->h_grids.size() * sizeof(BatchGrid),
+                       cudaMemcpyHostToDevice, b->stream));
+    return CLBM_OK;
+}
+
+void drop_graphs(clbm_batch* b) {
+    for (int p = 0; p < 2; ++p)
+        if (b->graph[p]) {
+            cudaGraphExecDestroy(b->graph[p]);
+            b->graph[p] = nullptr;
+        }
+}
+
+// One time step of every lattice at batch phase p: the update tiles of the
+// current variant, then those of iterated-force lattices (each update fills
+// the ghost rows and columns of the buffer it writes).  Returns the number of
+// kernels launched.
+int batch_one(clbm_batch* b, int p) {
+    launch_batch(b->Q, b->prec, 1, b->variant, b->d_grids, b->d_step[b->variant], b->nstep[b->variant],
+                 p, b->nblk, nullptr, b->stream);
+    launch_batch(b->Q, b->prec, 3, 0, b->d_grids, b->d_iter, b->niter, p, b->nblk, nullptr, b->stream);
+    return (b->nstep[b->variant] > 0) + (b->niter > 0);
+}
+
+// Lattices stepped on their own since the last batch call: new descriptors.
+clbm_status refresh(clbm_batch* b) {
+    bool stale = false;
+    for (size_t k = 0; k < b->g.size(); ++k) {
+        const int cur = b->g[k]->stA == b->g[k]->phys[0] ? 0 : 1;
+        if ((b->h_grids[k].parity ^ b->phase) != cur) stale = true;
+    }
+    if (!stale) return CLBM_OK;
+    clbm_status st = upload_desc(b);
+    if (st == CLBM_OK) drop_graphs(b);
+    return st;
+}
+
+// Ghost rows and columns of every lattice's current state, when some
+// lattice's state or case was set from outside since its last update.
+void batch_ghosts(clbm_batch* b) {
+    bool stale = false;
+    for (clbm_grid* g : b->g) stale = stale || !g->ghosts_ok;
+    if (!stale) return;
+    launch_batch(b->Q, b->prec, 0, 0, b->d_grids, b->d_bnd, b->nbnd, b->phase, b->nblk, nullptr, b->stream);
+    b->launches++;
+    for (clbm_grid* g : b->g) g->ghosts_ok = true;
+}
+
+clbm_status batch_graph(clbm_batch* b, int p) {
+    if (b->graph[p]) return CLBM_OK;
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    batch_one(b, p);
+    batch_one(b, p ^ 1);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &gr);
+    if (e != cudaSuccess) return fail(CLBM_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph[p], gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+        b->graph[p] = nullptr;
+        return fail(CLBM_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return CLBM_OK;
+}
+
+// Advance every lattice's host-side bookkeeping by n steps.
+void batch_advance(clbm_batch* b, long long n) {
+    for (clbm_grid* g : b->g) {
+        if (n & 1) std::swap(g->stA, g->stB);
+        g->t += n;
+    }
+    b->phase = (int)((b->phase + n) & 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle* out) {
+    if (!grids || n < 1 || !out) return fail(CLBM_EINVAL, "need grids, n >= 1 and out");
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!grids[k]) return fail(CLBM_EINVAL, "grid %d is NULL", k);
+        if (!grids[k]->have_case) return fail(CLBM_EINVAL, "grid %d has no case", k);
+        if (grids[k]->Q != grids[0]->Q || grids[k]->prec != grids[0]->prec ||
+            grids[k]->device != grids[0]->device || grids[k]->stream != grids[0]->stream)
+            return fail(CLBM_EINVAL, "grids of a batch share lattice, precision, device and stream");
+    }
+    clbm_batch* b = new (std::nothrow) clbm_batch();
+    if (!b) return fail(CLBM_ENOMEM, "host allocation failed");
+    b->g.assign(grids, grids + n);
+    b->Q = grids[0]->Q;
+    b->prec = grids[0]->prec;
+    b->device = grids[0]->device;
+    b->stream = grids[0]->stream;
+    b->variant = 0;
+    b->phase = 0;
+    clbm_status st = select(grids[0]);
+    if (st != CLBM_OK) {
+        delete b;
+        return st;
+    }
+    // work-lists
+    std::vector<int4> wb, wm;
+    std::vector<int2> range;
+    std::vector<int4> ws[BATCH_VARIANTS], wi;
+    int tj0, tr0;
+    batch_tile_shape(0, &tj0, &tr0);
+    for (int k = 0; k < n; ++k) {
+        clbm_grid* g = grids[k];
+        for (int j = 0; j < g->n2; j += 128) {
+            wb.push_back(make_int4(k, 0, j, 0));
+            wb.push_back(make_int4(k, 1, j, 0));
+        }
+        for (int t = 0; t < g->n1 * b->Q; t += 128 / (2 * GC)) wb.push_back(make_int4(k, 2, t, 0));
+        const int r0 = (int)wm.size();
+        for (int i = 0; i < g->n1; ++i)
+            for (int j = 0; j < g->n2; j += 128) wm.push_back(make_int4(k, i, j, 0));
+        range.push_back(make_int2(r0, (int)wm.size()));
+        if (g->cs.force_iterations > 0) {
+            for (int i = 0; i < g->n1; i += tr0)
+                for (int j = 0; j < g->n2; j += tj0) wi.push_back(make_int4(k, i, j, 0));
+            continue;
+        }
+        for (int v = 0; v < BATCH_VARIANTS; ++v) {
+            int tj, tr;
+            batch_tile_shape(v, &tj, &tr);
+            for (int i = 0; i < g->n1; i += tr)
+                for (int j = 0; j < g->n2; j += tj) ws[v].push_back(make_int4(k, i, j, 0));
+        }
+    }
+    b->nbnd = (int)wb.size();
+    b->nmom = (int)wm.size();
+    size_t bytes = n * sizeof(BatchGrid) + wb.size() * sizeof(int4) + wm.size() * sizeof(int4) +
+                   range.size() * sizeof(int2) + wm.size() * NRED * 8 + (size_t)n * NRED * 8;
+    for (int v = 0; v < BATCH_VARIANTS; ++v) {
+        b->nstep[v] = (int)ws[v].size();
+        bytes += ws[v].size() * sizeof(int4);
+    }
+    b->niter = (int)wi.size();
+    bytes += wi.size() * sizeof(int4);
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc((void**)&b->d_grids, n * sizeof(BatchGrid));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_bnd, wb.size() * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_mom, wm.size() * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_range, range.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_partial, wm.size() * NRED * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_out, (size_t)n * NRED * 8);
+    for (int v = 0; v < BATCH_VARIANTS && e == cudaSuccess; ++v)
+        if (!ws[v].empty()) e = cudaMalloc((void**)&b->d_step[v], ws[v].size() * sizeof(int4));
+    if (e == cudaSuccess && !wi.empty()) e = cudaMalloc((void**)&b->d_iter, wi.size() * sizeof(int4));
+    if (e != cudaSuccess) {
+        clbm_batch_destroy(b);
+        return fail(CLBM_ENOMEM, "batch work-lists (%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    cudaMemcpyAsync(b->d_bnd, wb.data(), wb.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(b->d_mom, wm.data(), wm.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(b->d_range, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                    b->stream);
+    for (int v = 0; v < BATCH_VARIANTS; ++v)
+        if (!ws[v].empty())
+            cudaMemcpyAsync(b->d_step[v], ws[v].data(), ws[v].size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (!wi.empty())
+        cudaMemcpyAsync(b->d_iter, wi.data(), wi.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+    st = upload_desc(b);
+    if (st == CLBM_OK && cudaStreamSynchronize(b->stream) != cudaSuccess)
+        st = fail(CLBM_ECUDA, "batch set-up failed");
+    if (st != CLBM_OK) {
+        clbm_batch_destroy(b);
+        return st;
+    }
+    int nsm = grids[0]->nsm;
+    b->nblk = nsm * 8;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(shape_class(b));
+        if (it != g_tune_cache.end()) b->variant = it->second;
+    }
+    *out = b;
+    return CLBM_OK;
+}
+
+clbm_status clbm_batch_step(clbm_batch_handle b, long long n) {
+    if (!b) return fail(CLBM_EINVAL, "batch is NULL");
+    if (n < 0) return fail(CLBM_EINVAL, "n < 0");
+    clbm_status st = select(b->g[0]);
+    if (st != CLBM_OK) return st;
+    st = refresh(b);
+    if (st != CLBM_OK) return st;
+    batch_ghosts(b);
+    const bool graphs = b->stream != nullptr;
+    long long left = n;
+    while (left >= 2 && graphs) {
+        st = batch_graph(b, b->phase);
+        if (st != CLBM_OK) return st;
+        CK(cudaGraphLaunch(b->graph[b->phase], b->stream));
+        b->launches += 2 * ((b->nstep[b->variant] > 0) + (b->niter > 0));
+        batch_advance(b, 2);
+        left -= 2;
+    }
+    while (left > 0) {
+        b->launches += batch_one(b, b->phase);
+        batch_advance(b, 1);
+        --left;
+    }
+    CK(cudaGetLastError());
+    return CLBM_OK;
+}
+
+clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons) {
+    if (!b) return fail(CLBM_EINVAL, "batch is NULL");
+    clbm_status st = select(b->g[0]);
+    if (st != CLBM_OK) return st;
+    // the per-cell sums over the current buffers, then one reduction per lattice
+    st = refresh(b);
+    if (st != CLBM_OK) return st;
+    batch_ghosts(b);
+    launch_batch(b->Q, b->prec, 2, 0, b->d_grids, b->d_mom, b->nmom, b->phase, b->nblk, b->d_partial,
+                 b->stream);
+    launch_batch_reduce(b->d_partial, b->d_range, (int)b->g.size(), b->d_out, b->stream);
+    b->launches += 2;
+    CK(cudaGetLastError());
+    std::vector<double> v(b->g.size() * NRED);
+    CK(cudaMemcpyAsync(v.data(), b->d_out, v.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    bool unstable = false, changed = false;
+    for (size_t k = 0; k < b->g.size(); ++k) {
+        clbm_grid* g = b->g[k];
+        const double* x = &v[k * NRED];
+        const long long dt = g->t - g->t_prev;
+        double r = INFINITY;
+        if (g->have_prev && dt > 0) r = x[1] > 0.0 ? sqrt(x[0]) / (dt * sqrt(x[1])) : (x[0] > 0 ? INFINITY : 0.0);
+        if (res) res[k] = r;
+        if (cons)
+            for (int q = 0; q < 6; ++q) cons[k * 6 + q] = x[2 + q];
+        if (!g->have_prev) changed = true;
+        g->have_prev = true;
+        g->t_prev = g->t;
+        if (x[8] > 0.0 || !std::isfinite(x[2])) unstable = true;
+    }
+    if (changed) {
+        st = upload_desc(b);
+        if (st != CLBM_OK) return st;
+    }
+    if (unstable) return fail(CLBM_EUNSTABLE, "a lattice of the batch has a non-finite or non-positive density");
+    return CLBM_OK;
+}
+
+clbm_status clbm_batch_set_variant(clbm_batch_handle b, int variant) {
+    if (!b) return fail(CLBM_EINVAL, "batch is NULL");
+    if (variant < 0 || variant >= BATCH_VARIANTS) return fail(CLBM_EINVAL, "variant out of range");
+    if (variant != b->variant) drop_graphs(b);
+    b->variant = variant;
+    return CLBM_OK;
+}
+
+clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* ms_per_step) {
+    if (!b || steps < 1) return fail(CLBM_EINVAL, "batch is NULL or steps < 1");
+    clbm_status st = select(b->g[0]);
+    if (st != CLBM_OK) return st;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double bestms = INFINITY;
+    int bestv = 0;
+    const int keep = b->variant;
+    st = refresh(b);
+    if (st != CLBM_OK) return st;
+    batch_ghosts(b);
+    for (int v = 0; v < BATCH_VARIANTS; ++v) {
+        b->variant = v;
+        b->launches += batch_one(b, b->phase);  // warm-up step
+        batch_advance(b, 1);
+        CK(cudaEventRecord(e0, b->stream));
+        for (int s = 0; s < steps; ++s) {
+            b->launches += batch_one(b, b->phase);
+            batch_advance(b, 1);
+        }
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / steps;
+        if (ms_per_step) ms_per_step[v] = per;
+        if (per < bestms) {
+            bestms = per;
+            bestv = v;
+        }
+    }
+    (void)keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    if (bestv != b->variant) drop_graphs(b);
+    b->variant = bestv;
+    drop_graphs(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[shape_class(b)] = bestv;
+    }
+    if (best) *best = bestv;
+    return CLBM_OK;
+}
+
+clbm_status clbm_batch_launch_count(clbm_batch_handle b, long long* launches) {
+    if (!b || !launches) return fail(CLBM_EINVAL, "NULL argument");
+    *launches = b->launches;
+    return CLBM_OK;
+}
+
+clbm_status clbm_batch_destroy(clbm_batch_handle b) {
+    if (!b) return CLBM_OK;
+    if (!b->g.empty()) cudaSetDevice(b->g[0]->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    cudaFree(b->d_grids);
+    cudaFree(b->d_bnd);
+    cudaFree(b->d_mom);
+    cudaFree(b->d_range);
+    cudaFree(b->d_partial);
+    cudaFree(b->d_out);
+    for (int v = 0; v < BATCH_VARIANTS; ++v) cudaFree(b->d_step[v]);
+    cudaFree(b->d_iter);
+    delete b;
     return CLBM_OK;
 }
 

@@ -34,6 +34,7 @@ template <int Q, typename C>
 struct Cell {
     C d[Q];                                   // pulled deviations from this row's reference
     C drho, rho, irho, U1, U2, F1, F2, Ut1, Ut2;
+    C ls, ls1, ls2;                           // sums of the lagged sigma: 1, c^1, c^2 weighted
 };
 
 // Advection (Eq. 12) with the lagged read of N'(q, t-1), moments (Eqs. 7, 8,
@@ -50,10 +51,14 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const C* __restrict__ tb, con
     C f1 = tb[T::F01], f2 = tb[T::F02];
     c.d[0] = ld(0, 0, 0);
     Sd += c.d[0];
+    c.ls = c.d[0];
+    c.ls1 = C(0);
+    c.ls2 = C(0);
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const int c1 = c1_of(a), c2 = c2_of(a);
+        const V4<C> A = ld4(tb + T::pa(q));
         // pulled: N_a(q) from q - c_a, N_b(q) from q + c_a; lagged: own values
         const C pa = ld(a, -c1, -c2);
         const C pb = ld(b, c1, c2);
@@ -64,10 +69,19 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const C* __restrict__ tb, con
         if (c1 != 0) S1 += C(c1) * dp;
         if (c2 != 0) S2 += C(c2) * dp;
         const C ta = la + pb, tbv = lb + pa;
-        f1 += tb[T::a1(a)] * ta + tb[T::a1(b)] * tbv;
-        f2 += tb[T::a2(a)] * ta + tb[T::a2(b)] * tbv;
-        c.d[a] = c1 != 0 ? pa + tb[T::dpull(a)] : pa;
-        c.d[b] = c1 != 0 ? pb + tb[T::dpull(b)] : pb;
+        f1 += A.x * ta + A.z * tbv;
+        f2 += A.y * ta + A.w * tbv;
+        c.ls += la + lb;
+        if (c1 != 0) c.ls1 += C(c1) * (la - lb);
+        if (c2 != 0) c.ls2 += C(c2) * (la - lb);
+        if (c1 != 0) {
+            const V4<C> D = ld4(tb + T::pd(q));
+            c.d[a] = pa + D.x;
+            c.d[b] = pb + D.y;
+        } else {
+            c.d[a] = pa;
+            c.d[b] = pb;
+        }
     }
     const C invJ = tb[T::INVJ];
     c.drho = Sd * invJ;
@@ -86,9 +100,8 @@ struct GlobalLoad {
     const S* p;
     long long P;
     int ld;
-    float isc;
     __device__ __forceinline__ typename Store<S>::C operator()(int al, int dr, int dc) const {
-        return Store<S>::ld(p + al * P + (long long)dr * ld + dc, isc);
+        return Store<S>::ld(p + al * P + (long long)dr * ld + dc);
     }
 };
 
@@ -98,12 +111,15 @@ template <int Q, typename C>
 __device__ __forceinline__ void force_again(const C* __restrict__ tb, const C (&out)[Q],
                                             const Consts<C>& k, Cell<Q, C>& c) {
     using T = Tab<Q>;
+    using L = Lat<Q>;
     C f1 = tb[T::FI1], f2 = tb[T::FI2];
 #pragma unroll
-    for (int b = 1; b < Q; ++b) {
-        const C t = out[b] + c.d[opp_of(b)];
-        f1 += tb[T::a1(b)] * t;
-        f2 += tb[T::a2(b)] * t;
+    for (int q = 0; q < L::NP; ++q) {
+        const int a = L::plus(q), b = opp_of(a);
+        const V4<C> A = ld4(tb + T::pa(q));
+        const C ta = out[a] + c.d[b], tbv = out[b] + c.d[a];
+        f1 += A.x * ta + A.z * tbv;
+        f2 += A.y * ta + A.w * tbv;
     }
     const C invJ = tb[T::INVJ];
     c.F1 = -C(0.5) * invJ * f1 + c.rho * k.g1;
@@ -150,9 +166,10 @@ __device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C
         const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
         O[q] = K11 * c1 + K12 * c2 + K111 * (c1 * c1 * c1) + K112 * (c1 * c1 * c2) +
                K122 * (c1 * c2 * c2) + K222 * (c2 * c2 * c2);
-        S11 += tb[T::e11(q)] * O[q];
-        S22 += tb[T::e22(q)] * O[q];
-        S12 += tb[T::e12(q)] * O[q];
+        const V4<C> B = ld4(tb + T::pb(q));
+        S11 += B.y * O[q];
+        S22 += B.z * O[q];
+        S12 += B.w * O[q];
     }
     const C pr = k.pref * c.rho;
     S11 *= pr;
@@ -172,7 +189,7 @@ __device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
-        const C X = drt * tb[T::p0(q)] + base + Ea * (c1 * c1) + Eb * (c1 * c2) + Ec * (c2 * c2);
+        const C X = drt * tb[T::pb(q)] + base + Ea * (c1 * c1) + Eb * (c1 * c2) + Ec * (c2 * c2);
         const C Y = rt * O[q] + Fa * c1 + Fb * c2;
         const C Jw = J * C(L::w(a));
         emit(a, c.d[a] * omt + Jw * (X + Y));
@@ -190,15 +207,95 @@ __device__ __forceinline__ double ref_at(const double* geo, int n1, int a, int r
     return geo[(size_t)(m - 1) * Geo::stride(Q) + Geo::ref(Q, b)];
 }
 
-// Store a value of interior column j (0..n2-1) and its periodic copies in
-// the ghost columns (state column = j + GC).
+// The periodic copies of interior column j (0..n2-1) in the ghost columns
+// (state column = j + GC), and the value with its copies.
 template <typename S, typename C>
-__device__ __forceinline__ void store_periodic(S* __restrict__ rowp, int j, int n2, C v, float isc) {
-    Store<S>::st(rowp + j + GC, v, isc);
+__device__ __forceinline__ void store_wrap(S* __restrict__ rowp, int j, int n2, C v) {
     if (j < GC)
-        for (int jj = j + n2; jj < n2 + GC; jj += n2) Store<S>::st(rowp + jj + GC, v, isc);
+        for (int jj = j + n2; jj < n2 + GC; jj += n2) Store<S>::st(rowp + jj + GC, v);
     if (j >= n2 - GC)
-        for (int jj = j - n2; jj >= -GC; jj -= n2) Store<S>::st(rowp + jj + GC, v, isc);
+        for (int jj = j - n2; jj >= -GC; jj -= n2) Store<S>::st(rowp + jj + GC, v);
 }
+template <typename S, typename C>
+__device__ __forceinline__ void store_periodic(S* __restrict__ rowp, int j, int n2, C v) {
+    Store<S>::st(rowp + j + GC, v);
+    store_wrap<S, C>(rowp, j, n2, v);
+}
+
+// Ghost value of App. B from the stored N' of the mirrored fluid node (x):
+// the offset between the two rows' references plus, at a moving wall, the
+// correction (2/T0) w J rho c^2 (U0^2 - Ut^2) of the mirrored node, whose
+// per-direction factor is coef.
+template <typename C>
+__device__ __forceinline__ C ghost_value(C x, const double* __restrict__ gt, C rho, C U0, C ut2) {
+    return x + (C(gt[0]) + C(gt[1]) * rho * (U0 - ut2));
+}
+
+// Periodic ghost column of interior column j when a row has at least 2 GC
+// columns: one copy, at column j + n2 (j < GC) or j - n2 (j >= n2 - GC), as
+// an offset from j; 0 when the cell has none.  Updates store it next to the
+// cell's own value.  Shorter rows need several copies: EdgeFill makes them.
+__device__ __forceinline__ int wrap_offset(int j, int n2) {
+    if (n2 < 2 * GC) return 0;
+    return j < GC ? n2 : (j >= n2 - GC ? -n2 : 0);
+}
+
+// Fills, from the cell that supplies them, the ghost rows of App. B that the
+// next update pulls from the buffer being written: at the first / last H rows
+// (depth k = i + 1 / n1 - i) the new N'_b of the mirrored node feeds ghost
+// population a = b* (no-slip) or a = b-hat (moving wall) of depth k when a
+// crosses the wall that deep (c^1_a >= k at the low wall, <= -k at the high
+// wall; * and hat are involutions), with the moving-wall correction from the
+// cell's own rho and Ut^2.  The values are those the boundary kernel would
+// compute from the stored state.  With own_wrap (rows shorter than 2 GC in
+// the per-cell kernels) it also makes the periodic ghost columns of the
+// cell's own row.
+//
+// Called once per edge cell after the collision with vp pointing at the
+// cell's new stored N'_0 (N'_b at vp + b vstride, in global or shared
+// memory): a loop over b, not unrolled, in a function of its own, since edge
+// rows are few and the interior update should keep its registers and code
+// small.
+template <int Q, typename S>
+struct EdgeFill {
+    using C = typename Store<S>::C;
+    S* st;                   // state buffer being written (row 0, column 0)
+    const double* ghost;     // [2][H][Q] x {offset, coefficient}
+    long long plane;
+    int ld, n1, n2, bc_lo, bc_hi;
+    C U0_lo, U0_hi;
+    bool own_wrap;
+
+    __device__ static __forceinline__ bool needed(int i, int n1, int n2) {
+        return i < Lat<Q>::H || i >= n1 - Lat<Q>::H || n2 < 2 * GC;
+    }
+
+    __device__ __noinline__ void fill(int i, int j, const S* vp, long long vstride, C rho, C ut2) const {
+        constexpr int H = Lat<Q>::H;
+#pragma unroll 1
+        for (int b = 0; b < Q; ++b) {
+            const C v = Store<S>::lds(vp + b * vstride);
+            if (own_wrap) store_wrap<S, C>(st + b * plane + (long long)(i + H) * ld, j, n2, v);
+            if (i < H) {
+                const int k = i + 1;
+                const int a = bc_lo == 0 ? opp_of(b) : hat_of(b);
+                if (c1_of(a) >= k) {
+                    const double* gt = ghost + 2 * ((k - 1) * Q + a);
+                    store_periodic<S, C>(st + a * plane + (long long)(H - k) * ld, j, n2,
+                                         ghost_value<C>(v, gt, rho, U0_lo, ut2));
+                }
+            }
+            if (i >= n1 - H) {
+                const int k = n1 - i;
+                const int a = bc_hi == 0 ? opp_of(b) : hat_of(b);
+                if (c1_of(a) <= -k) {
+                    const double* gt = ghost + 2 * ((H + k - 1) * Q + a);
+                    store_periodic<S, C>(st + a * plane + (long long)(n1 + H + k - 1) * ld, j, n2,
+                                         ghost_value<C>(v, gt, rho, U0_hi, ut2));
+                }
+            }
+        }
+    }
+};
 
 }  // namespace clbm

@@ -12,7 +12,11 @@
 //                (ghost rows use the mirrored row's reference).
 //   tab        : [n1][Tab<Q>::S] per-row coefficients in the compute type.
 //   geo        : [n1][Geo::stride(Q)] per-row FP64 geometry + references.
-//   wall       : [2 walls][h][n2] x {rho, Ut^2} of the last collision.
+//   wall       : [2 walls][h][n2] x {rho, Ut^2} of the last collision (the
+//                boundary kernel's input when ghost rows must be rebuilt).
+// Each update writes the interior, the ghost rows and the periodic ghost
+// columns of the buffer it fills; the boundary kernel rebuilds them only
+// after the state or the case was set from outside.
 //   ghost      : [2 walls][h][Q] x {offset, correction coefficient}.
 #pragma once
 
@@ -25,44 +29,45 @@
 
 namespace clbm {
 
-// Storage conversions (deviation scaled by a power of two for FP16).  ld
-// reads global memory through the read-only path, lds any address.
+// Storage conversions.  FP16 keeps deviations scaled by 2^12 (out of the
+// subnormal range; scaling by a power of two is exact).  ld reads global
+// memory through the read-only path, lds any address, rt rounds a value the
+// way a store and a load would.
+constexpr float F16_SCALE = 4096.0f;
 template <typename S> struct Store;
 template <> struct Store<double> {
     using C = double;
-    __device__ static __forceinline__ double ld(const double* p, float) { return __ldg(p); }
-    __device__ static __forceinline__ double lds(const double* p, float) { return *p; }
-    __device__ static __forceinline__ void st(double* p, double v, float) { *p = v; }
+    __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
+    __device__ static __forceinline__ double lds(const double* p) { return *p; }
+    __device__ static __forceinline__ void st(double* p, double v) { *p = v; }
+    __device__ static __forceinline__ double rt(double v) { return v; }
 };
 template <> struct Store<float> {
     using C = float;
-    __device__ static __forceinline__ float ld(const float* p, float) { return __ldg(p); }
-    __device__ static __forceinline__ float lds(const float* p, float) { return *p; }
-    __device__ static __forceinline__ void st(float* p, float v, float) { *p = v; }
+    __device__ static __forceinline__ float ld(const float* p) { return __ldg(p); }
+    __device__ static __forceinline__ float lds(const float* p) { return *p; }
+    __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
+    __device__ static __forceinline__ float rt(float v) { return v; }
 };
 template <> struct Store<__half> {
     using C = float;
-    __device__ static __forceinline__ float ld(const __half* p, float inv_scale) {
-        return __half2float(__ldg(p)) * inv_scale;
+    __device__ static __forceinline__ float ld(const __half* p) {
+        return __half2float(__ldg(p)) * (1.0f / F16_SCALE);
     }
-    __device__ static __forceinline__ float lds(const __half* p, float inv_scale) {
-        return __half2float(*p) * inv_scale;
+    __device__ static __forceinline__ float lds(const __half* p) {
+        return __half2float(*p) * (1.0f / F16_SCALE);
     }
-    __device__ static __forceinline__ void st(__half* p, float v, float inv_scale) {
-        *p = __float2half_rn(v / inv_scale);
+    __device__ static __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v * F16_SCALE); }
+    __device__ static __forceinline__ float rt(float v) {
+        return __half2float(__float2half_rn(v * F16_SCALE)) * (1.0f / F16_SCALE);
     }
 };
 template <> struct Store<__nv_bfloat16> {
     using C = float;
-    __device__ static __forceinline__ float ld(const __nv_bfloat16* p, float inv_scale) {
-        return __bfloat162float(__ldg(p)) * inv_scale;
-    }
-    __device__ static __forceinline__ float lds(const __nv_bfloat16* p, float inv_scale) {
-        return __bfloat162float(*p) * inv_scale;
-    }
-    __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, float inv_scale) {
-        *p = __float2bfloat16_rn(v / inv_scale);
-    }
+    __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __forceinline__ float lds(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ float rt(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
 constexpr int GC = 8;  // ghost columns on each side (>= widest |c^2| = 3; 16-byte TMA origins)
@@ -85,7 +90,6 @@ struct StepArgs {
     int n1, n2, ld, h;
     long long plane;        // elements per population plane = (n1+2h)*ld
     double tau, rho0, g1, g2, U0_lo, U0_hi;
-    float inv_scale;        // 1/scale of 16-bit storage (1 otherwise)
     int bc_lo, bc_hi;
     int iters;              // extra passes of the implicit force
     int* err;               // device error word (bounded waits that gave up)
@@ -100,7 +104,6 @@ struct MomArgs {
     int n1, n2, ld, h;
     long long plane;
     double tau, rho0, g1, g2;
-    float inv_scale;
     // outputs (device, [n1][n2] FP64, may be null)
     double *rho, *U1, *U2, *Ut1, *Ut2, *F1, *F2;
     // residual mode
@@ -124,9 +127,9 @@ void launch_moments(int Q, int prec, const MomArgs& a, int iters, int reduce,
 int moments_blocks(int n1, int n2);
 void launch_reduce_final(const double* partial, int nblocks, double* out, cudaStream_t stream);
 void launch_state_from_fp64(int Q, int prec, const double* Np, const double* geo, void* state,
-                            int n1, int n2, int ld, int h, float inv_scale, cudaStream_t stream);
+                            int n1, int n2, int ld, int h, cudaStream_t stream);
 void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo, double* Np,
-                          int n1, int n2, int ld, int h, float inv_scale, cudaStream_t stream);
+                          int n1, int n2, int ld, int h, cudaStream_t stream);
 void launch_wall_copy(int prec, void* wall_rho, void* wall_ut2, const double* src_rho,
                       const double* src_ut2, const double* rho_nf_row, int n1, int n2, int h,
                       double rho0, cudaStream_t stream);

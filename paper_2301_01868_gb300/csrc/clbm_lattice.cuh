@@ -77,25 +77,34 @@ template <> struct Lat<21> {
 };
 
 // Per-row coefficient table of the fused update, in the compute type.
-// Slots: header (metric, rest-state sums evaluated in FP64), then a^k_alpha
-// for alpha = 1..Q-1, then four values per +/- pair, then the pull offsets
-// Delta_alpha = ref_alpha(i - c1) - ref_alpha(i) for alpha = 1..Q-1.
+// Slots: a 16-value header (metric, rest-state sums evaluated in FP64), then
+// 12 values per +/- pair (a = plus(p), b = opp(a)), each group of four read
+// as one vector:
+//   A = (a^1_a, a^2_a, a^1_b, a^2_b)          Christoffel contractions
+//   B = (P0_a, E11, E22, E12)                  rest polynomial, dPi weights
+//   D = (Delta_a, Delta_b, 0, 0)               pull offsets ref(i - c1) - ref(i)
 template <int Q> struct Tab {
     static constexpr int INVJ = 0, J = 1, G11 = 2, G12 = 3, G22 = 4;
     static constexpr int F01 = 5, F02 = 6, P00 = 7, FI1 = 8, FI2 = 9;
     static constexpr int D0 = 10, M1 = 11, M2 = 12;
-    static constexpr int A0 = 16;                               // a1, a2 of alpha=1..Q-1
-    static constexpr int PB = A0 + 2 * (Q - 1);                 // P0, E11, E22, E12 per pair
-    static constexpr int DB = PB + 4 * Lat<Q>::NP;              // Delta_alpha, alpha=1..Q-1
-    static constexpr int S = DB + (Q - 1) + ((Q - 1) % 4 ? 4 - (Q - 1) % 4 : 0);  // stride
-    __host__ __device__ static constexpr int a1(int a) { return A0 + 2 * (a - 1); }
-    __host__ __device__ static constexpr int a2(int a) { return A0 + 2 * (a - 1) + 1; }
-    __host__ __device__ static constexpr int p0(int p) { return PB + 4 * p; }
-    __host__ __device__ static constexpr int e11(int p) { return PB + 4 * p + 1; }
-    __host__ __device__ static constexpr int e22(int p) { return PB + 4 * p + 2; }
-    __host__ __device__ static constexpr int e12(int p) { return PB + 4 * p + 3; }
-    __host__ __device__ static constexpr int dpull(int a) { return DB + (a - 1); }
+    static constexpr int PB = 16;
+    static constexpr int S = PB + 12 * Lat<Q>::NP;              // stride (multiple of 4)
+    __host__ __device__ static constexpr int pa(int p) { return PB + 12 * p; }
+    __host__ __device__ static constexpr int pb(int p) { return PB + 12 * p + 4; }
+    __host__ __device__ static constexpr int pd(int p) { return PB + 12 * p + 8; }
 };
+
+// Four table values read with one vector load.
+template <typename C> struct V4 { C x, y, z, w; };
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+    const double2 u = reinterpret_cast<const double2*>(p)[0];
+    const double2 v = reinterpret_cast<const double2*>(p)[1];
+    return {u.x, u.y, v.x, v.y};
+}
 
 // Per-row FP64 geometry (geometry precompute output, plus the deviation
 // reference).  a^k_alpha = c^m_alpha Theta^k_m(q + c_alpha, q) (Eq. 5).

@@ -123,7 +123,6 @@ __global__ void k_tables(const double* __restrict__ geo, C* __restrict__ tab, in
         D0 += dl[a];
         M1 += c1_of(a) * dl[a];
         M2 += c2_of(a) * dl[a];
-        if (a > 0) t[T::dpull(a)] = C(dl[a]);
     }
     t[T::D0] = C(D0);
     t[T::M1] = C(M1);
@@ -142,8 +141,6 @@ __global__ void k_tables(const double* __restrict__ geo, C* __restrict__ tab, in
         F02 += ab2 * (own + in);
         FI1 += ab1 * (own + in - dl[ob]);
         FI2 += ab2 * (own + in - dl[ob]);
-        t[T::a1(b)] = C(ab1);
-        t[T::a2(b)] = C(ab2);
     }
     t[T::F01] = C(F01);
     t[T::F02] = C(F02);
@@ -156,10 +153,16 @@ __global__ void k_tables(const double* __restrict__ geo, C* __restrict__ tab, in
         const double c1 = c1_of(a), c2 = c2_of(a);
         const double D1 = g[Geo::a1(a)] + g[Geo::a1(ab)];
         const double D2 = g[Geo::a2(a)] + g[Geo::a2(ab)];
-        t[T::p0(p)] = C(rest_poly<Q>(a, g[Geo::GI11], g[Geo::GI12], g[Geo::GI22]));
-        t[T::e11(p)] = C(2.0 * w * c1 * D1);
-        t[T::e22(p)] = C(2.0 * w * c2 * D2);
-        t[T::e12(p)] = C(w * (c1 * D2 + c2 * D1));
+        t[T::pa(p) + 0] = C(g[Geo::a1(a)]);
+        t[T::pa(p) + 1] = C(g[Geo::a2(a)]);
+        t[T::pa(p) + 2] = C(g[Geo::a1(ab)]);
+        t[T::pa(p) + 3] = C(g[Geo::a2(ab)]);
+        t[T::pb(p) + 0] = C(rest_poly<Q>(a, g[Geo::GI11], g[Geo::GI12], g[Geo::GI22]));
+        t[T::pb(p) + 1] = C(2.0 * w * c1 * D1);
+        t[T::pb(p) + 2] = C(2.0 * w * c2 * D2);
+        t[T::pb(p) + 3] = C(w * (c1 * D2 + c2 * D1));
+        t[T::pd(p) + 0] = C(dl[a]);
+        t[T::pd(p) + 1] = C(dl[ab]);
     }
 }
 

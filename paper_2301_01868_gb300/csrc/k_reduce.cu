@@ -9,77 +9,90 @@ namespace {
 
 constexpr int RB = 128;  // threads per block of the diagnostics kernels
 
+// Persistent blocks of the residual reduction: enough to fill the GPU, never
+// more than there are (row, 128-column) items.
+int residual_blocks(int n1, int n2) {
+    const int items = n1 * ((n2 + RB - 1) / RB);
+    return items < 1216 ? items : 1216;
+}
+
 template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters, int reduce) {
+__device__ __forceinline__ void cell_moments(const MomArgs& a, int iters, int i, int j,
+                                             Cell<Q, C>& c) {
     using T = Tab<Q>;
     constexpr int H = Lat<Q>::H;
+    const C* tb = (const C*)a.tab + (size_t)i * T::S;
+    const Consts<C> kc = Consts<C>::make(a.k);
+    const long long off = (long long)(i + H) * a.ld + j + GC;
+    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld}, tb, kc, c);
+    if (iters > 0) {
+        C out[Q];
+        collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
+        for (int it = 0; it < iters; ++it) {
+            force_again<Q, C>(tb, out, kc, c);
+            collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
+        }
+    } else {
+        collide_emit<Q, C>(tb, c, kc, [](int, C) {});
+    }
+}
+
+// Field output of the moments: one thread per cell.
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
-    const bool live = j < a.n2;
+    if (j >= a.n2) return;
+    Cell<Q, C> c;
+    cell_moments<Q, S, C>(a, iters, i, j, c);
+    const size_t m = (size_t)i * a.n2 + j;
+    if (a.rho) a.rho[m] = double(c.rho);
+    if (a.U1) a.U1[m] = double(c.U1);
+    if (a.U2) a.U2[m] = double(c.U2);
+    if (a.Ut1) a.Ut1[m] = double(c.Ut1);
+    if (a.Ut2) a.Ut2[m] = double(c.Ut2);
+    if (a.F1) a.F1[m] = double(c.F1);
+    if (a.F2) a.F2[m] = double(c.F2);
+}
+
+// Residual and conservation sums: persistent blocks stride over (row, 128-column)
+// items; each thread accumulates its cells in FP64 in a fixed order, then a
+// warp-shuffle and block reduction in a fixed tree writes one partial per
+// block, so repeated runs give identical bits.  The rest parts of the totals
+// are exact per row: sum_a ref_a(i) = J rho0 and sum_a c_a ref_a(i) = 0.
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(RB) k_residual(const MomArgs a, int iters) {
+    const int bx = (a.n2 + RB - 1) / RB;
+    const int items = a.n1 * bx;
+    const size_t nc = (size_t)a.n1 * a.n2;
     double v[NRED];
 #pragma unroll
     for (int k = 0; k < NRED; ++k) v[k] = 0.0;
-    if (live) {
-        const C* tb = (const C*)a.tab + (size_t)i * T::S;
-        const Consts<C> kc = Consts<C>::make(a.k);
-        const long long off = (long long)(i + H) * a.ld + j + GC;
-        const S* p = (const S*)a.src + off;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int i = it / bx, j = (it % bx) * RB + threadIdx.x;
+        if (j >= a.n2) continue;
         Cell<Q, C> c;
-        pull_cell<Q, C>(GlobalLoad<S>{p, a.plane, a.ld, a.inv_scale}, tb, kc, c);
-        if (iters > 0) {
-            C out[Q];
-            collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
-            for (int it = 0; it < iters; ++it) {
-                force_again<Q, C>(tb, out, kc, c);
-                collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
-            }
-        } else {
-            collide_emit<Q, C>(tb, c, kc, [](int, C) {});
-        }
+        cell_moments<Q, S, C>(a, iters, i, j, c);
+        const double* g = a.geo + (size_t)i * Geo::stride(Q);
         const size_t m = (size_t)i * a.n2 + j;
-        if (a.rho) a.rho[m] = double(c.rho);
-        if (a.U1) a.U1[m] = double(c.U1);
-        if (a.U2) a.U2[m] = double(c.U2);
-        if (a.Ut1) a.Ut1[m] = double(c.Ut1);
-        if (a.Ut2) a.Ut2[m] = double(c.Ut2);
-        if (a.F1) a.F1[m] = double(c.F1);
-        if (a.F2) a.F2[m] = double(c.F2);
-        if (reduce) {
-            const double* g = a.geo + (size_t)i * Geo::stride(Q);
-            const double u1 = double(c.Ut1), u2 = double(c.Ut2), rho = double(c.rho);
-            const double J = g[Geo::J];
-            const double uu = g[Geo::G11] * u1 * u1 + 2.0 * g[Geo::G12] * u1 * u2 + g[Geo::G22] * u2 * u2;
-            double dd = 0.0;
-            const size_t nc = (size_t)a.n1 * a.n2;
-            if (a.have_prev) {
-                const double e1 = u1 - a.ut_prev[m], e2 = u2 - a.ut_prev[nc + m];
-                dd = g[Geo::G11] * e1 * e1 + 2.0 * g[Geo::G12] * e1 * e2 + g[Geo::G22] * e2 * e2;
-            }
-            a.ut_prev[m] = u1;
-            a.ut_prev[nc + m] = u2;
-            double mass = 0.0, p1 = 0.0, p2 = 0.0;
-#pragma unroll
-            for (int al = 0; al < Q; ++al) {
-                const double Np = double(Store<S>::ld(p + al * a.plane, a.inv_scale)) +
-                                  g[Geo::ref(Q, al)];
-                mass += Np;
-                p1 += c1_of(al) * Np;
-                p2 += c2_of(al) * Np;
-            }
-            v[0] = J * dd;
-            v[1] = J * uu;
-            v[2] = mass;
-            v[3] = p1;
-            v[4] = p2;
-            v[5] = 0.5 * J * rho * uu;
-            v[6] = J * rho * (g[Geo::M1] * u1 + g[Geo::M2] * u2);
-            v[7] = sqrt(uu);
-            v[8] = (rho > 0.0 && isfinite(rho) && isfinite(uu)) ? 0.0 : 1.0;
+        const double u1 = double(c.Ut1), u2 = double(c.Ut2), rho = double(c.rho);
+        const double J = g[Geo::J];
+        const double uu = g[Geo::G11] * u1 * u1 + 2.0 * g[Geo::G12] * u1 * u2 + g[Geo::G22] * u2 * u2;
+        if (a.have_prev) {
+            const double e1 = u1 - a.ut_prev[m], e2 = u2 - a.ut_prev[nc + m];
+            v[0] += J * (g[Geo::G11] * e1 * e1 + 2.0 * g[Geo::G12] * e1 * e2 + g[Geo::G22] * e2 * e2);
         }
+        a.ut_prev[m] = u1;
+        a.ut_prev[nc + m] = u2;
+        v[1] += J * uu;
+        v[2] += J * a.k.rho0 + double(c.ls);
+        v[3] += double(c.ls1);
+        v[4] += double(c.ls2);
+        v[5] += 0.5 * J * rho * uu;
+        v[6] += J * rho * (g[Geo::M1] * u1 + g[Geo::M2] * u2);
+        v[7] = fmax(v[7], sqrt(uu));
+        v[8] += (rho > 0.0 && isfinite(rho) && isfinite(uu)) ? 0.0 : 1.0;
     }
-    if (!reduce) return;
-    // Warp shuffle, then the four warp results in order: a fixed summation
-    // tree, so repeated runs give identical bits.
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
         double x = v[k];
@@ -99,7 +112,7 @@ __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters, int 
         const int k = threadIdx.x;
         double x = sh[0][k];
         for (int q = 1; q < RB / 32; ++q) x = (k == 7) ? fmax(x, sh[q][k]) : x + sh[q][k];
-        a.partial[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * NRED + k] = x;
+        a.partial[(size_t)blockIdx.x * NRED + k] = x;
     }
 }
 
@@ -127,7 +140,7 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__
 
 template <int Q, typename S>
 __global__ void k_from_fp64(const double* __restrict__ Np, const double* __restrict__ geo,
-                            S* __restrict__ st, int n1, int n2, int ld, int h, float inv_scale) {
+                            S* __restrict__ st, int n1, int n2, int ld, int h) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= n2) return;
@@ -138,21 +151,21 @@ __global__ void k_from_fp64(const double* __restrict__ Np, const double* __restr
         const double Nv = Np ? Np[((size_t)al * n1 + i) * n2 + j]
                              : geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
         const double v = Nv - geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
-        using CT = decltype(Store<S>::ld(st, 1.f));
-        store_periodic<S, CT>(st + al * P + (long long)(i + h) * ld, j, n2, CT(v), inv_scale);
+        using CT = typename Store<S>::C;
+        store_periodic<S, CT>(st + al * P + (long long)(i + h) * ld, j, n2, CT(v));
     }
 }
 
 template <int Q, typename S>
 __global__ void k_to_fp64(const S* __restrict__ st, const double* __restrict__ geo,
-                          double* __restrict__ Np, int n1, int n2, int ld, int h, float inv_scale) {
+                          double* __restrict__ Np, int n1, int n2, int ld, int h) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= n2) return;
     const long long P = (long long)(n1 + 2 * h) * ld;
 #pragma unroll
     for (int al = 0; al < Q; ++al) {
-        const double s = double(Store<S>::ld(st + al * P + (long long)(i + h) * ld + j + GC, inv_scale));
+        const double s = double(Store<S>::ld(st + al * P + (long long)(i + h) * ld + j + GC));
         Np[((size_t)al * n1 + i) * n2 + j] = s + geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
     }
 }
@@ -219,13 +232,17 @@ __global__ void __launch_bounds__(256) k_row_mean(const double* __restrict__ f, 
 
 template <int Q, typename S, typename C>
 void run_moments(const MomArgs& a, int iters, int reduce, cudaStream_t s) {
-    dim3 b(RB), g((a.n2 + RB - 1) / RB, a.n1);
-    k_moments<Q, S, C><<<g, b, 0, s>>>(a, iters, reduce);
+    if (reduce) {
+        k_residual<Q, S, C><<<residual_blocks(a.n1, a.n2), RB, 0, s>>>(a, iters);
+    } else {
+        dim3 b(RB), g((a.n2 + RB - 1) / RB, a.n1);
+        k_moments<Q, S, C><<<g, b, 0, s>>>(a, iters);
+    }
 }
 
 }  // namespace
 
-int moments_blocks(int n1, int n2) { return ((n2 + RB - 1) / RB) * n1; }
+int moments_blocks(int n1, int n2) { return residual_blocks(n1, n2); }
 
 void launch_moments(int Q, int prec, const MomArgs& a, int iters, int reduce, cudaStream_t s) {
     if (Q == 9) {
@@ -251,38 +268,38 @@ void launch_reduce_final(const double* partial, int nblocks, double* out, cudaSt
 
 template <int Q>
 static void from64(int prec, const double* Np, const double* geo, void* st, int n1, int n2, int ld,
-                   int h, float isc, cudaStream_t s) {
+                   int h, cudaStream_t s) {
     dim3 b(128), g((n2 + 127) / 128, n1);
     switch (prec) {
-        case 0: k_from_fp64<Q, double><<<g, b, 0, s>>>(Np, geo, (double*)st, n1, n2, ld, h, isc); break;
-        case 1: k_from_fp64<Q, float><<<g, b, 0, s>>>(Np, geo, (float*)st, n1, n2, ld, h, isc); break;
-        case 2: k_from_fp64<Q, __half><<<g, b, 0, s>>>(Np, geo, (__half*)st, n1, n2, ld, h, isc); break;
-        default: k_from_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>(Np, geo, (__nv_bfloat16*)st, n1, n2, ld, h, isc); break;
+        case 0: k_from_fp64<Q, double><<<g, b, 0, s>>>(Np, geo, (double*)st, n1, n2, ld, h); break;
+        case 1: k_from_fp64<Q, float><<<g, b, 0, s>>>(Np, geo, (float*)st, n1, n2, ld, h); break;
+        case 2: k_from_fp64<Q, __half><<<g, b, 0, s>>>(Np, geo, (__half*)st, n1, n2, ld, h); break;
+        default: k_from_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>(Np, geo, (__nv_bfloat16*)st, n1, n2, ld, h); break;
     }
 }
 
 template <int Q>
 static void to64(int prec, const void* st, const double* geo, double* Np, int n1, int n2, int ld,
-                 int h, float isc, cudaStream_t s) {
+                 int h, cudaStream_t s) {
     dim3 b(128), g((n2 + 127) / 128, n1);
     switch (prec) {
-        case 0: k_to_fp64<Q, double><<<g, b, 0, s>>>((const double*)st, geo, Np, n1, n2, ld, h, isc); break;
-        case 1: k_to_fp64<Q, float><<<g, b, 0, s>>>((const float*)st, geo, Np, n1, n2, ld, h, isc); break;
-        case 2: k_to_fp64<Q, __half><<<g, b, 0, s>>>((const __half*)st, geo, Np, n1, n2, ld, h, isc); break;
-        default: k_to_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>((const __nv_bfloat16*)st, geo, Np, n1, n2, ld, h, isc); break;
+        case 0: k_to_fp64<Q, double><<<g, b, 0, s>>>((const double*)st, geo, Np, n1, n2, ld, h); break;
+        case 1: k_to_fp64<Q, float><<<g, b, 0, s>>>((const float*)st, geo, Np, n1, n2, ld, h); break;
+        case 2: k_to_fp64<Q, __half><<<g, b, 0, s>>>((const __half*)st, geo, Np, n1, n2, ld, h); break;
+        default: k_to_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>((const __nv_bfloat16*)st, geo, Np, n1, n2, ld, h); break;
     }
 }
 
 void launch_state_from_fp64(int Q, int prec, const double* Np, const double* geo, void* state,
-                            int n1, int n2, int ld, int h, float isc, cudaStream_t s) {
-    if (Q == 9) from64<9>(prec, Np, geo, state, n1, n2, ld, h, isc, s);
-    else from64<21>(prec, Np, geo, state, n1, n2, ld, h, isc, s);
+                            int n1, int n2, int ld, int h, cudaStream_t s) {
+    if (Q == 9) from64<9>(prec, Np, geo, state, n1, n2, ld, h, s);
+    else from64<21>(prec, Np, geo, state, n1, n2, ld, h, s);
 }
 
 void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo, double* Np,
-                          int n1, int n2, int ld, int h, float isc, cudaStream_t s) {
-    if (Q == 9) to64<9>(prec, state, geo, Np, n1, n2, ld, h, isc, s);
-    else to64<21>(prec, state, geo, Np, n1, n2, ld, h, isc, s);
+                          int n1, int n2, int ld, int h, cudaStream_t s) {
+    if (Q == 9) to64<9>(prec, state, geo, Np, n1, n2, ld, h, s);
+    else to64<21>(prec, state, geo, Np, n1, n2, ld, h, s);
 }
 
 void launch_wall_init(int prec, void* wr, void* wu, const double* rho, const double* ut2, int n1,

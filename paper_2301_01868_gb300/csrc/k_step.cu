@@ -4,7 +4,10 @@
 // One thread per cell; a warp covers 32 consecutive cells of one row, so every
 // per-row coefficient is a warp-uniform load and every population access is a
 // coalesced row segment at a constant offset (ghost rows and periodic ghost
-// columns surround the interior).  Lagged values are consumed as they are
+// columns surround the interior).  Cells next to a periodic end also store
+// their value's periodic copy, and cells next to a wall the ghost values they
+// supply (EdgeFill), so one launch per time step leaves the written buffer
+// ready to be pulled from.  Lagged values are consumed as they are
 // loaded and new populations are stored as they are produced, so a thread
 // holds only the Q pulled deviations and the pair odd parts.  Populations are
 // deviations from the rest equilibrium of their own row (zero at rest), so
@@ -28,11 +31,13 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs
     const int row = i + H;
     const long long off = (long long)row * a.ld + j + GC;
     Cell<Q, C> c;
-    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld, a.inv_scale}, tb, k, c);
-    // Interior only: the boundary kernel refreshes the ghost rows and the
-    // periodic ghost columns before the next step reads this buffer.
+    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld}, tb, k, c);
     S* dst = (S*)a.dst + off;
-    auto put = [&](int al, C v) { Store<S>::st(dst + al * a.plane, v, a.inv_scale); };
+    const int dw = wrap_offset(j, a.n2);
+    auto put = [&](int al, C v) {
+        Store<S>::st(dst + al * a.plane, v);
+        if (dw != 0) Store<S>::st(dst + al * a.plane + dw, v);
+    };
     if (!ITER) {
         collide_emit<Q, C>(tb, c, k, put);
     } else {
@@ -44,6 +49,11 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs
         }
 #pragma unroll
         for (int al = 0; al < Q; ++al) put(al, out[al]);
+    }
+    if (EdgeFill<Q, S>::needed(i, a.n1, a.n2)) {
+        const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo, a.bc_hi,
+                                C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC};
+        ef.fill(i, j, dst, a.plane, c.rho, c.Ut2);
     }
     // Near-wall rows keep rho and Ut^2 for the moving-wall correction (App. B).
     if (i < H) {
@@ -62,25 +72,24 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs
 // that enters the fluid through a wall, the ghost value is the mirrored
 // fluid node's N' of the reversed (no-slip) or reflected (moving wall)
 // direction, plus the moving-wall correction; one thread per column.
-// blockIdx.y = 2: periodic ghost columns of the interior rows, one thread per
-// (row, population).  Together they make the buffer ready to be pulled from.
+// blockIdx.y = 2: periodic ghost columns of the interior rows; a half-warp
+// copies the 2 GC ghost columns of one (population, row).  Together they make
+// a buffer whose state was set from outside ready to be pulled from (the
+// update keeps them current afterwards).
 template <int Q, typename S, typename C>
 __global__ void __launch_bounds__(128) k_boundary(const StepArgs a, S* __restrict__ st) {
     constexpr int H = Lat<Q>::H;
     const long long P = a.plane;
-    const float isc = a.inv_scale;
     if (blockIdx.y == 2) {
         const int t = blockIdx.x * blockDim.x + threadIdx.x;
-        if (t >= a.n1 * Q) return;
-        const int al = t / a.n1, i = t % a.n1;
+        const int pr = t / (2 * GC), e = t % (2 * GC);
+        if (pr >= a.n1 * Q) return;
+        const int al = pr / a.n1, i = pr % a.n1;
         S* rowp = st + al * P + (long long)(i + H) * a.ld;
-#pragma unroll
-        for (int e = 0; e < 2 * GC; ++e) {
-            const int cs = e < GC ? e : a.n2 + e;  // ghost state column
-            int jw = (cs - GC) % a.n2;
-            if (jw < 0) jw += a.n2;
-            rowp[cs] = rowp[jw + GC];
-        }
+        const int cs = e < GC ? e : a.n2 + e;  // ghost state column
+        int jw = (cs - GC) % a.n2;
+        if (jw < 0) jw += a.n2;
+        rowp[cs] = rowp[jw + GC];
         return;
     }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,9 +110,9 @@ __global__ void __launch_bounds__(128) k_boundary(const StepArgs a, S* __restric
             if (wall == 0 ? (c1 < k) : (c1 > -k)) continue;
             const int b = bc == 0 ? opp_of(al) : hat_of(al);
             const double* gt = a.ghost + 2 * ((wall * H + (k - 1)) * Q + al);
-            C v = C(Store<S>::ld(st + b * P + (long long)mr * a.ld + j + GC, isc));
-            v += C(gt[0]) + C(gt[1]) * wr * (U0 - wu);
-            store_periodic<S, C>(st + al * P + (long long)gr * a.ld, j, a.n2, v, isc);
+            const C x = C(Store<S>::ld(st + b * P + (long long)mr * a.ld + j + GC));
+            store_periodic<S, C>(st + al * P + (long long)gr * a.ld, j, a.n2,
+                                 ghost_value<C>(x, gt, wr, U0, wu));
         }
     }
 }
@@ -117,7 +126,7 @@ void run_step(const StepArgs& a, cudaStream_t s) {
 
 template <int Q, typename S, typename C>
 void run_boundary(const StepArgs& a, void* st, cudaStream_t s) {
-    const int nx = (a.n2 + 127) / 128, ny = (a.n1 * Q + 127) / 128;
+    const int nx = (a.n2 + 127) / 128, ny = (a.n1 * Q * 2 * GC + 127) / 128;
     dim3 b(128), g(nx > ny ? nx : ny, 3);
     k_boundary<Q, S, C><<<g, b, 0, s>>>(a, (S*)st);
 }

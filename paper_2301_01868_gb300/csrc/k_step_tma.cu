@@ -9,13 +9,22 @@
 // are double buffered behind mbarriers, so the loads of tile k+1 overlap the
 // arithmetic of tile k.  Every shared-memory offset of a pull is a compile-time
 // constant.  New populations go to a shared output tile that one TMA store
-// writes back.  Waits on mbarriers are bounded: on time-out the kernel records
+// writes back; cells at the periodic ends store their periodic copies, the
+// cells after the last whole 16-byte chunk of a row store themselves, and
+// cells next to a wall write the ghost values they supply (EdgeFill).  Waits on mbarriers are bounded: on time-out the kernel records
 // an error code and returns.
 #include <cuda.h>
 
 #include "clbm_cell.cuh"
 
 namespace clbm {
+
+// Interior columns the TMA tile store writes: whole 16-byte chunks of a row
+// only.  Cells in the remaining n2 - tma_store_cols columns store themselves.
+template <typename S>
+__host__ __device__ __forceinline__ constexpr int tma_store_cols(int n2) {
+    return n2 - n2 % (16 / (int)sizeof(S));
+}
 
 // Shared-memory layout of one tile (elements of the storage type S).
 template <int Q, typename S>
@@ -40,7 +49,8 @@ struct TileGeom {
     static constexpr int BUF = off(Q);                            // elements per input buffer
     static constexpr int OUT = Q * TR * TJ;                       // elements of the output tile
     static constexpr int TABB = TR * Tab<Q>::S * 4;               // bytes of one table block
-    static constexpr int SMEM = 2 * BUF * (int)sizeof(S) + OUT * (int)sizeof(S) + 2 * TABB + 64 + 128;
+    // two input buffers, two output tiles, two table blocks, barriers, alignment slack
+    static constexpr int SMEM = 2 * BUF * (int)sizeof(S) + 2 * OUT * (int)sizeof(S) + 2 * TABB + 64 + 128;
 };
 
 // Tensor maps of both state buffers: per buffer, the 8 box shapes of the loads
@@ -107,8 +117,9 @@ __device__ __forceinline__ void tma_store3(const CUtensorMap* map, int x, int y,
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ void bulk_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+// Wait until at most one committed bulk store still reads shared memory.
+__device__ __forceinline__ void bulk_wait_read1() {
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
 }
 
 __device__ __forceinline__ void bulk_wait_all() {
@@ -145,11 +156,12 @@ __global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
     using G = TileGeom<Q, S>;
     using T = Tab<Q>;
     constexpr int H = Lat<Q>::H;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // round up to 128 bytes by pointer arithmetic (keeps the shared address space)
+    unsigned char* const smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     unsigned char* const in_base = smem;
-    S* const sm_out = (S*)(smem + 2 * G::BUF * sizeof(S));
-    unsigned char* const tab_base = smem + 2 * G::BUF * sizeof(S) + G::OUT * sizeof(S);
+    S* const out_base = (S*)(smem + 2 * G::BUF * sizeof(S));
+    unsigned char* const tab_base = smem + 2 * G::BUF * sizeof(S) + 2 * G::OUT * sizeof(S);
     uint64_t* const bar = (uint64_t*)(tab_base + 2 * G::TABB);
     int* const s_abort_p = (int*)(bar + 2);
 #define s_abort (*s_abort_p)
@@ -189,19 +201,22 @@ __global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
         if (i < a.n1 && j < a.n2) {
             const C* tb = (const C*)sm_tab(buf) + r * T::S;
             const S* in = (const S*)sm_in(buf);
-            const float isc = a.inv_scale;
             Cell<Q, C> c;
             pull_cell<Q, C>(
                 [&](int al, int dr, int dc) -> C {
                     return C(Store<S>::lds(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) +
-                                               cc + G::col0(al) + dc,
-                                           isc));
+                                           cc + G::col0(al) + dc));
                 },
                 tb, k, c);
-            S* out = sm_out + r * G::TJ + cc;
+            S* out = out_base + (it & 1) * G::OUT + r * G::TJ + cc;
             collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
-                Store<S>::st(out + al * (G::TR * G::TJ), v, isc);
+                Store<S>::st(out + al * (G::TR * G::TJ), v);
             });
+            if (i < H || i >= a.n1 - H) {
+                const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo,
+                                        a.bc_hi, C(a.U0_lo), C(a.U0_hi), false};
+                ef.fill(i, j, out, G::TR * G::TJ, c.rho, c.Ut2);
+            }
             if (i < H) {
                 const int idx = i * a.n2 + j;
                 ((C*)a.wall_rho)[idx] = c.rho;
@@ -216,8 +231,29 @@ __global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
-            tma_store3(&maps.st[src ^ 1], j0, i0, 0, sm_out);
-            bulk_wait_read();
+            // store this tile; the output tile of the previous one must be read
+            // out before the next tile overwrites it (double-buffered)
+            tma_store3(&maps.st[src ^ 1], j0, i0, 0, out_base + (it & 1) * G::OUT);
+            bulk_wait_read1();
+        }
+        // Tiles at the periodic ends: the whole CTA copies, from the output
+        // tile, the periodic ghost columns its cells supply and the ragged
+        // tail the tile store leaves out (columns j < GC, and the last GC
+        // columns, which hold every column past the last whole 16-byte chunk).
+        if (j0 < GC || j0 + G::TJ > a.n2 - GC) {
+            const int n2v = tma_store_cols<S>(a.n2);
+            const int jend = j0 + G::TJ < a.n2 ? j0 + G::TJ : a.n2;
+            const S* ob = out_base + (it & 1) * G::OUT;
+            for (int e = tid; e < Q * G::TR * 2 * GC; e += G::NT) {
+                const int x = e % (2 * GC), rr = (e / (2 * GC)) % G::TR, al = e / (2 * GC * G::TR);
+                const int jj = x < GC ? x : a.n2 - 2 * GC + x;
+                const int ii = i0 + rr;
+                if (jj < j0 || jj >= jend || ii >= a.n1) continue;
+                const C v = C(Store<S>::lds(ob + al * (G::TR * G::TJ) + rr * G::TJ + (jj - j0)));
+                S* rowp = (S*)a.dst + al * a.plane + (long long)(ii + H) * a.ld;
+                if (jj >= n2v) Store<S>::st(rowp + jj + GC, v);
+                store_wrap<S, C>(rowp, jj, a.n2, v);
+            }
         }
         __syncthreads();
     }
@@ -298,9 +334,13 @@ static int encode_maps(EncodeFn enc, TmaMaps* m, void* bufA, void* bufB, int n1,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return -1;
         }
-        // interior view for the tile store: origin at (row H, column GC)
+        // interior view for the tile store: origin at (row H, column GC), rows
+        // cut at the last whole 16-byte chunk (a partial chunk would be
+        // written whole, into the ghost columns)
         char* ib = (char*)bases[b] + ((size_t)H * ld + GC) * es;
-        cuuint64_t idims[3] = {(cuuint64_t)n2, (cuuint64_t)n1, (cuuint64_t)Q};
+        const int n2v = tma_store_cols<S>(n2);
+        if (n2v < 1) return -1;
+        cuuint64_t idims[3] = {(cuuint64_t)n2v, (cuuint64_t)n1, (cuuint64_t)Q};
         cuuint32_t obox[3] = {(cuuint32_t)G::TJ, (cuuint32_t)G::TR, (cuuint32_t)Q};
         if (enc(&m->st[b], dt, 3, ib, idims, strides, obox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

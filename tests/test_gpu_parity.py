@@ -204,6 +204,40 @@ def test_fp32_tma_ragged_tiles_random_state(Q):
                 tol_u=1e-5, kernel=2)
 
 
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (2, 3e-3), (3, 3e-2)])
+@pytest.mark.parametrize("n2", [45, 61, 130])
+def test_tma_and_per_cell_kernels_agree_on_ragged_rows(prec, tol, n2):
+    """Row lengths whose end is not on a 16-byte boundary: after a
+    j-dependent random start both kernels give the same state, ghost columns
+    included, since every later pull reads them."""
+    n1 = 13
+    c = Case(21, n1, n2, O.PLANAR, I.uniform_edges(n1), bc=(1, 1), tau=0.9, U0=(0.02, -0.01))
+    st = c.oracle().state()
+    st = st * (1.0 + I.smooth_field(st.shape, seed=5, amplitude=1e-2))
+    a, b = c.gpu(prec, 1), c.gpu(prec, 2)
+    a.set_state(st)
+    b.set_state(st)
+    a.step(60)
+    b.step(60)
+    sa, sb = a.state(), b.state()
+    dev = st - c.oracle().state()
+    assert np.abs(sa - sb).max() <= tol * np.abs(dev).max()
+    assert vel_err(b.moments(), a.moments()) <= tol
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_rows_shorter_than_a_tma_chunk_use_the_per_cell_kernel(prec):
+    """n2 = 3 (less than 16 bytes per row): the TMA kernel is refused, the
+    automatic choice runs the per-cell kernel and matches the oracle."""
+    c = _clbm()
+    n1, n2 = 10, 3
+    case = Case(21, n1, n2, O.PLANAR, I.uniform_edges(n1), bc=(1, 0), tau=0.9, U0=(0.02, 0.0))
+    with pytest.raises(c.ClbmError):
+        case.gpu(prec, 2)
+    if prec == 1:
+        compare_run(case, 1, 300, tol_u=1e-5)
+
+
 def test_fp32_kernels_agree():
     """Both FP32 kernels run the same arithmetic; they differ by rounding only."""
     c = polar_case(21, n1=40, n2=200)
