@@ -356,10 +356,17 @@ def run_serving(n, verbose=False):
     for r in serve.poisson_requests(n, rate, **kw):
         srv.submit(r)
     batched = srv.run()
-    _, serial = serve.serve_serial(serve.poisson_requests(n, rate, **kw), precision="fp32", chunk=100)
+    reqs = serve.poisson_requests(n, rate, **kw)
+    done_serial, serial = serve.serve_serial(reqs, precision="fp32", chunk=100)
+    st_b = {d["rid"]: d["status"] for d in srv.done}
+    differ = [{"rid": r.rid, "case": r.case, "lattice": r.lattice, "n1": r.n1, "n2": r.n2,
+               "batched": st_b[r.rid], "serial": d["status"]}
+              for r, d in zip(sorted(reqs, key=lambda q: q.arrival), done_serial)
+              if st_b[r.rid] != d["status"]]
     out = {"requests": n, "arrival_rate_per_s": rate,
-           "ladder": "n1 8..32, n2 8..64 log-uniform; tol 1e-8; cap 150000 steps",
-           "batched": batched, "serial": serial,
+           "ladder": "n1 8..32, n2 8..64 log-uniform (circular: n2 = round(2 pi n1)); tol 1e-8; "
+                     "cap 150000 steps",
+           "batched": batched, "serial": serial, "status_differs": differ,
            "speedup_solves_per_s": batched["solves_per_s"] / serial["solves_per_s"],
            "speedup_converged_per_s": (batched["converged_per_s"] / serial["converged_per_s"]
                                        if serial["converged_per_s"] > 0 else None)}
