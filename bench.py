@@ -229,7 +229,7 @@ def config_of(wl, args):
     return {"workload": wl, "lattice": "D2Q%d" % Q, "n1": n1, "n2": n2, "geometry":
             "annulus R2/R1=%g, radial CR=%g" % (R2 / R1, CR), "tau": tau, "u_wall": uw,
             "storage": prec, "chunk": args.chunk,
-            "kernel": {0: "auto", 1: "per-cell", 2: "tma-tiles"}[args.kernel],
+            "kernel": {0: "auto", 1: "per-cell", 2: "tma-tiles", 3: "tma-pipeline"}[args.kernel],
             "l2": "inputs larger than L2 (state %d MB)" % (2 * Q * n1 * n2 * STORAGE_BYTES[prec] >> 20),
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -245,14 +245,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", type=int, default=0,
-                    help="0 automatic, 1 one thread per cell, 2 TMA-staged tiles")
+                    help="0 automatic, 1 one thread per cell, 2 TMA-staged tiles, "
+                         "3 TMA-staged warp-specialised pipeline")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving comparison (continuous batching vs serial solves)")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="only the batched form against per-lattice launches (512 lattices)")
+    ap.add_argument("--batch-lattices", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     if args.serve:
         print(json.dumps(run_serving(args.serve_requests, verbose=True)))
         return
@@ -371,6 +377,77 @@ def run_serving(n, verbose=False):
            "speedup_converged_per_s": (batched["converged_per_s"] / serial["converged_per_s"]
                                        if serial["converged_per_s"] > 0 else None)}
     return out
+
+
+def batch_requests(n, seed=20230105):
+    """The batched configuration: n lattices, case uniform over the four
+    flows, D2Q21, tau uniform in [0.55, 1], speed 0.01.  Planar lattices draw
+    n1 in 32..1024 and n2 in 32..2048; circular ones draw n2 in 32..2048 and
+    take n1 = round(n2 / (2 pi)) (near-square cells at the inner wall, as the
+    paper's polar grids)."""
+    from paper_2301_01868_gb300 import serve
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        case = serve.CASES[rng.integers(4)]
+        n1 = int(rng.integers(32, 1025))
+        n2 = int(rng.integers(32, 2049))
+        if case.startswith("circular"):
+            n1 = max(8, int(round(n2 / (2.0 * math.pi))))
+        out.append(serve.Request(case=case, lattice=21, n1=n1, n2=n2, tau=float(rng.uniform(0.55, 1.0)),
+                                 speed=0.01, rid=k))
+    return out
+
+
+def run_batch(args):
+    """--batch: the batched form against per-lattice launches on the same
+    lattices (MLUPS over all lattices, K timed steps each, after warm-up;
+    the batch's tile variant from its autotuner)."""
+    import torch
+    from paper_2301_01868_gb300 import clbm, serve
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    reqs = batch_requests(args.batch_lattices)
+    t0 = time.perf_counter()
+    grids = [serve.build_grid(r, clbm.FP32, stream) for r in reqs]
+    setup_s = time.perf_counter() - t0
+    cells = sum(r.n1 * r.n2 for r in reqs)
+    ws = sum(clbm.workspace_bytes(21, clbm.FP32, r.n1, r.n2) for r in reqs)
+    b = clbm.Batch(grids)
+    best, ms = b.tune(steps=2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    l0 = b.launch_count()
+    ev0.record(stream)
+    b.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_b = ev0.elapsed_time(ev1)
+    l_b = b.launch_count() - l0
+    b.close()
+    for g in grids:
+        g.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for g in grids:
+        g.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_l = ev0.elapsed_time(ev1)
+    for g in grids:
+        g.close()
+    out = {"metric": "batched MLUPS (all lattices)", "unit": "MLUPS", "lattices": len(reqs),
+           "cells": cells, "workspace_bytes": ws, "steps": args.steps, "warmup": args.warmup,
+           "setup_s": setup_s, "tuned_variant": int(best), "variant_ms_per_step": list(map(float, ms)),
+           "batched": {"value": cells * args.steps / (t_b * 1e-3) / 1e6, "ms": t_b, "launches": l_b},
+           "per_lattice": {"value": cells * args.steps / (t_l * 1e-3) / 1e6, "ms": t_l,
+                           "launches": len(reqs) * args.steps},
+           "config": {"workload": "batched_512_d2q21_fp32", "lattice": "D2Q21", "storage": "fp32",
+                      "shapes": "planar n1 32..1024 x n2 32..2048; circular n2 32..2048, "
+                                "n1 = n2 / 2 pi", "tau": "U[0.55, 1]"},
+           "data": "synthetic"}
+    print(json.dumps(out))
 
 
 def run_e2e(g, args, torch, stream, world, dist, cells, Q):

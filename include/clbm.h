@@ -160,10 +160,12 @@ clbm_status clbm_set_stream(clbm_handle h, void* stream);
 clbm_status clbm_set_profiling(clbm_handle h, int on);
 clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
 
-/* Kernel of the bulk update: 0 automatic (TMA-staged tiles where available),
- * 1 one thread per cell with direct loads, 2 TMA-staged tiles (FP32 / FP16 /
- * BF16 storage; the implicit-force passes always use variant 1).  Both run
- * the same arithmetic. */
+/* Kernel of the bulk update: 0 automatic (variant 3 where available, else 1),
+ * 1 one thread per cell with direct loads, 2 TMA-staged tiles with a shared
+ * output tile, 3 TMA-staged tiles in a warp-specialised pipeline (2 and 3:
+ * FP32 / FP16 / BF16 storage and rows of at least 16 bytes; the
+ * implicit-force passes always use variant 1).  All run the same arithmetic.
+ * CLBM_EINVAL for a variant the grid cannot use. */
 clbm_status clbm_set_kernel(clbm_handle h, int variant);
 
 /* Number of kernel launches this grid has issued since creation. */
@@ -201,7 +203,9 @@ typedef struct clbm_batch* clbm_batch_handle;
 clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle* out);
 /* Advance every grid of the batch n time steps.  Asynchronous. */
 clbm_status clbm_batch_step(clbm_batch_handle b, long long n);
-/* clbm_residual for every grid in one pass: res[n], cons[n][6].  Synchronises. */
+/* clbm_residual for every grid in one pass: res[n], cons[n][6].  Synchronises.
+ * Every entry is filled; res[k] is NaN for a grid with a non-finite or
+ * non-positive density, and the call then returns CLBM_EUNSTABLE. */
 clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons);
 /* Update tile of the batched kernel: 0 = 128 x 1 cells, 1 = 256 x 1 cells
  * (2 per thread), 2 = 32 x 4 cells, 3 = 64 x 1 cells. */

@@ -283,11 +283,14 @@ class Batch:
         _check(lib().clbm_batch_step(self._h, int(n)))
 
     def residual(self):
-        """(res[n], cons[n, 6]) for every grid, as clbm_residual gives them."""
+        """(res[n], cons[n, 6]) for every grid, as clbm_residual gives them;
+        res[k] is NaN for a grid that went unstable (the others stay valid)."""
         n = len(self.grids)
         res = np.empty(n)
         cons = np.empty((n, 6))
-        _check(lib().clbm_batch_residual(self._h, res.ctypes.data, cons.ctypes.data))
+        st = lib().clbm_batch_residual(self._h, res.ctypes.data, cons.ctypes.data)
+        if st != 4:
+            _check(st)
         return res, cons
 
     def set_variant(self, v):

@@ -512,7 +512,7 @@ clbm_status clbm_step(clbm_handle g, long long n) {
         }
         if (use_tma(g)) {
             const int src = g->stA == g->phys[0] ? 0 : 1;
-            if (launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->stream) != 0)
+            if (launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->variant != 2, g->stream) != 0)
                 return fail(CLBM_ECUDA, "TMA-staged update could not be launched");
         } else {
             launch_step(g->Q, g->prec, a, g->stream);
@@ -707,8 +707,8 @@ clbm_status clbm_kernel_time(clbm_handle g, double* ms, long long* launches) {
 
 clbm_status clbm_set_kernel(clbm_handle g, int variant) {
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
-    if (variant < 0 || variant > 2) return fail(CLBM_EINVAL, "variant must be 0, 1 or 2");
-    if (variant == 2 && !g->tma)
+    if (variant < 0 || variant > 3) return fail(CLBM_EINVAL, "variant must be 0, 1, 2 or 3");
+    if (variant >= 2 && !g->tma)
         return fail(CLBM_EINVAL, "the TMA-staged update needs 16/32-bit storage on sm_90 or newer");
     g->variant = variant;
     return CLBM_OK;
@@ -751,8 +751,8 @@ struct clbm_batch {
     int niter;
     int4* d_bnd;
     int nbnd;
-    int4* d_mom;
-    int nmom;
+    int4* d_mom;                     // diagnostics items: lagged-force lattices first
+    int nmom, nmom_lag;
     int2* d_range;
     double* d_partial;
     double* d_out;
@@ -927,10 +927,6 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
             wb.push_back(make_int4(k, 1, j, 0));
         }
         for (int t = 0; t < g->n1 * b->Q; t += 128 / (2 * GC)) wb.push_back(make_int4(k, 2, t, 0));
-        const int r0 = (int)wm.size();
-        for (int i = 0; i < g->n1; ++i)
-            for (int j = 0; j < g->n2; j += 128) wm.push_back(make_int4(k, i, j, 0));
-        range.push_back(make_int2(r0, (int)wm.size()));
         if (g->cs.force_iterations > 0) {
             for (int i = 0; i < g->n1; i += tr0)
                 for (int j = 0; j < g->n2; j += tj0) wi.push_back(make_int4(k, i, j, 0));
@@ -941,6 +937,19 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
             batch_tile_shape(v, &tj, &tr);
             for (int i = 0; i < g->n1; i += tr)
                 for (int j = 0; j < g->n2; j += tj) ws[v].push_back(make_int4(k, i, j, 0));
+        }
+    }
+    // diagnostics items, lattice by lattice: lagged-force lattices first
+    range.resize(n);
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) b->nmom_lag = (int)wm.size();
+        for (int k = 0; k < n; ++k) {
+            clbm_grid* g = grids[k];
+            if ((g->cs.force_iterations > 0) != (pass == 1)) continue;
+            const int r0 = (int)wm.size();
+            for (int i = 0; i < g->n1; ++i)
+                for (int j = 0; j < g->n2; j += 128) wm.push_back(make_int4(k, i, j, 0));
+            range[k] = make_int2(r0, (int)wm.size());
         }
     }
     b->nbnd = (int)wb.size();
@@ -1030,10 +1039,12 @@ clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons) 
     st = refresh(b);
     if (st != CLBM_OK) return st;
     batch_ghosts(b);
-    launch_batch(b->Q, b->prec, 2, 0, b->d_grids, b->d_mom, b->nmom, b->phase, b->nblk, b->d_partial,
+    launch_batch(b->Q, b->prec, 2, 0, b->d_grids, b->d_mom, b->nmom_lag, b->phase, b->nblk, b->d_partial,
                  b->stream);
+    launch_batch(b->Q, b->prec, 4, 0, b->d_grids, b->d_mom + b->nmom_lag, b->nmom - b->nmom_lag, b->phase,
+                 b->nblk, b->d_partial + (size_t)b->nmom_lag * NRED, b->stream);
     launch_batch_reduce(b->d_partial, b->d_range, (int)b->g.size(), b->d_out, b->stream);
-    b->launches += 2;
+    b->launches += 2 + (b->nmom_lag > 0 && b->nmom > b->nmom_lag ? 1 : 0);
     CK(cudaGetLastError());
     std::vector<double> v(b->g.size() * NRED);
     CK(cudaMemcpyAsync(v.data(), b->d_out, v.size() * 8, cudaMemcpyDeviceToHost, b->stream));
@@ -1045,6 +1056,7 @@ clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons) 
         const long long dt = g->t - g->t_prev;
         double r = INFINITY;
         if (g->have_prev && dt > 0) r = x[1] > 0.0 ? sqrt(x[0]) / (dt * sqrt(x[1])) : (x[0] > 0 ? INFINITY : 0.0);
+        if (x[8] > 0.0 || !std::isfinite(x[2])) r = NAN;
         if (res) res[k] = r;
         if (cons)
             for (int q = 0; q < 6; ++q) cons[k * 6 + q] = x[2 + q];

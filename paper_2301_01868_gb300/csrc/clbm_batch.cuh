@@ -26,8 +26,9 @@ struct BatchGrid {
 constexpr int BATCH_VARIANTS = 4;
 
 // what: 0 boundary items, 1 update tiles (variant) of lagged-force lattices,
-// 2 diagnostics tiles, 3 update tiles (variant 0 shape) of lattices that
-// iterate the force.
+// 2 diagnostics tiles of lagged-force lattices, 3 update tiles (variant 0
+// shape) and 4 diagnostics tiles of lattices that iterate the force.  Work
+// item e writes partial[e] (diagnostics).
 void launch_batch(int Q, int prec, int what, int variant, const BatchGrid* grids, const int4* work,
                   int nwork, int parity, int nblk, double* partial, cudaStream_t s);
 void launch_batch_reduce(const double* partial, const int2* range, int ngrids, double* out,

@@ -197,6 +197,37 @@ __device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C
     }
 }
 
+// Per-cell terms of the residual and conservation sums (clbm_residual), added
+// to v: J |u(t) - u(t')|^2, J |u|^2 (physical u = Ut^k g_k), mass, momentum
+// sum c N' (2), kinetic energy J rho |u|^2 / 2, angular momentum
+// J rho (M1 Ut^1 + M2 Ut^2), largest |u|^2, and a flag for a non-finite or
+// non-positive density.  Each term is formed in the compute type (the
+// precision of the update) and summed in FP64; the mass adds the exact FP64
+// rest part J rho0 of the row.  prev holds Ut of the last call (FP64 storage).
+template <int Q, typename C>
+__device__ __forceinline__ void residual_terms(const Cell<Q, C>& c, const double* __restrict__ ge,
+                                               double rho0, double* prev1, double* prev2,
+                                               bool have_prev, double (&v)[NRED]) {
+    const C g11 = C(ge[Geo::G11]), g12 = C(ge[Geo::G12]), g22 = C(ge[Geo::G22]);
+    const C J = C(ge[Geo::J]);
+    const C u1 = c.Ut1, u2 = c.Ut2;
+    const C uu = g11 * u1 * u1 + C(2) * g12 * u1 * u2 + g22 * u2 * u2;
+    if (have_prev) {
+        const C e1 = u1 - C(*prev1), e2 = u2 - C(*prev2);
+        v[0] += double(J * (g11 * e1 * e1 + C(2) * g12 * e1 * e2 + g22 * e2 * e2));
+    }
+    *prev1 = double(u1);
+    *prev2 = double(u2);
+    v[1] += double(J * uu);
+    v[2] += ge[Geo::J] * rho0 + double(c.ls);
+    v[3] += double(c.ls1);
+    v[4] += double(c.ls2);
+    v[5] += double(C(0.5) * J * c.rho * uu);
+    v[6] += double(J * c.rho * (C(ge[Geo::M1]) * u1 + C(ge[Geo::M2]) * u2));
+    v[7] = fmax(v[7], double(uu));
+    v[8] += (c.rho > C(0) && isfinite(c.rho) && isfinite(uu)) ? 0.0 : 1.0;
+}
+
 // Reference N of direction a at 1-based row r (FP64 geometry table); rows
 // beyond a wall are the mirror image of the row inside, which flips c^1.
 template <int Q>

@@ -147,7 +147,7 @@ struct TmaMaps;
 int make_tma_maps(int Q, int prec, TmaMaps** out, void* bufA, void* bufB, int n1, int n2, int ld);
 void free_tma_maps(TmaMaps* m);
 int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
-                    cudaStream_t s);
+                    int pipelined, cudaStream_t s);
 
 // Set the thread-local message returned by clbm_last_error (clbm_api.cu).
 void set_last_error(const char* msg);

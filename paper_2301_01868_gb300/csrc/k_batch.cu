@@ -140,9 +140,10 @@ __global__ void __launch_bounds__(128) k_batch_boundary(const BatchGrid* __restr
 }
 
 // Diagnostics tiles (128 cells of one row): the per-lattice residual and
-// conservation sums of clbm_residual, one partial per work item.
-template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(128) k_batch_moments(const BatchGrid* __restrict__ grids,
+// conservation sums of clbm_residual, one partial per work item (the same
+// per-cell terms as k_residual).  ITER: lattices that iterate the force.
+template <int Q, typename S, typename C, bool ITER>
+__global__ void __launch_bounds__(128, ITER ? 2 : 4) k_batch_moments(const BatchGrid* __restrict__ grids,
                                                       const int4* __restrict__ work, int nwork,
                                                       int parity, double* __restrict__ partial) {
     using T = Tab<Q>;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(128) k_batch_moments(const BatchGrid* __restri
             const S* p = (const S*)g.phys[src] + off;
             Cell<Q, C> c;
             pull_cell<Q, C>(GlobalLoad<S>{p, g.plane, g.ld}, tb, kc, c);
-            if (g.iters > 0) {
+            if (ITER) {
                 C out[Q];
                 collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
                 for (int it = 0; it < g.iters; ++it) {
@@ -173,35 +174,9 @@ __global__ void __launch_bounds__(128) k_batch_moments(const BatchGrid* __restri
             } else {
                 collide_emit<Q, C>(tb, c, kc, [](int, C) {});
             }
-            const double* ge = g.geo + (size_t)i * Geo::stride(Q);
-            const double u1 = double(c.Ut1), u2 = double(c.Ut2), rho = double(c.rho);
-            const double J = ge[Geo::J];
-            const double uu = ge[Geo::G11] * u1 * u1 + 2.0 * ge[Geo::G12] * u1 * u2 + ge[Geo::G22] * u2 * u2;
             const size_t m = (size_t)i * g.n2 + j, nc = (size_t)g.n1 * g.n2;
-            double dd = 0.0;
-            if (g.have_prev) {
-                const double e1 = u1 - g.prev[m], e2 = u2 - g.prev[nc + m];
-                dd = ge[Geo::G11] * e1 * e1 + 2.0 * ge[Geo::G12] * e1 * e2 + ge[Geo::G22] * e2 * e2;
-            }
-            g.prev[m] = u1;
-            g.prev[nc + m] = u2;
-            double mass = 0.0, p1 = 0.0, p2 = 0.0;
-#pragma unroll
-            for (int al = 0; al < Q; ++al) {
-                const double Np = double(Store<S>::ld(p + al * g.plane)) + ge[Geo::ref(Q, al)];
-                mass += Np;
-                p1 += c1_of(al) * Np;
-                p2 += c2_of(al) * Np;
-            }
-            v[0] = J * dd;
-            v[1] = J * uu;
-            v[2] = mass;
-            v[3] = p1;
-            v[4] = p2;
-            v[5] = 0.5 * J * rho * uu;
-            v[6] = J * rho * (ge[Geo::M1] * u1 + ge[Geo::M2] * u2);
-            v[7] = sqrt(uu);
-            v[8] = (rho > 0.0 && isfinite(rho) && isfinite(uu)) ? 0.0 : 1.0;
+            residual_terms<Q, C>(c, g.geo + (size_t)i * Geo::stride(Q), g.k.rho0, g.prev + m,
+                                 g.prev + nc + m, g.have_prev != 0, v);
         }
 #pragma unroll
         for (int q = 0; q < NRED; ++q) {
@@ -218,7 +193,7 @@ __global__ void __launch_bounds__(128) k_batch_moments(const BatchGrid* __restri
             const int q = threadIdx.x;
             double x = sh[0][q];
             for (int ww = 1; ww < 4; ++ww) x = q == 7 ? fmax(x, sh[ww][q]) : x + sh[ww][q];
-            partial[(size_t)e * NRED + q] = x;
+            partial[(size_t)e * NRED + q] = q == 7 ? sqrt(x) : x;
         }
         __syncthreads();
     }
@@ -266,7 +241,8 @@ void run_all(int what, int v, const BatchGrid* grids, const int4* work, int nwor
     if (what == 0) k_batch_boundary<Q, S, C><<<nblk, 128, 0, s>>>(grids, work, nwork, parity);
     else if (what == 1) step_variant<Q, S, C>(v, grids, work, nwork, parity, nblk, s);
     else if (what == 3) k_batch_step<Q, S, C, 0, true><<<nblk, Var<0>::NT, 0, s>>>(grids, work, nwork, parity);
-    else k_batch_moments<Q, S, C><<<nblk, 128, 0, s>>>(grids, work, nwork, parity, partial);
+    else if (what == 4) k_batch_moments<Q, S, C, true><<<nblk, 128, 0, s>>>(grids, work, nwork, parity, partial);
+    else k_batch_moments<Q, S, C, false><<<nblk, 128, 0, s>>>(grids, work, nwork, parity, partial);
 }
 
 }  // namespace

@@ -11,12 +11,15 @@ constexpr int RB = 128;  // threads per block of the diagnostics kernels
 
 // Persistent blocks of the residual reduction: enough to fill the GPU, never
 // more than there are (row, 128-column) items.
+// One block per (row, 128-column) item up to 65536 blocks: enough loads in
+// flight to stream the state (fewer, longer-lived blocks left the diagnostics
+// latency-bound).
 int residual_blocks(int n1, int n2) {
     const int items = n1 * ((n2 + RB - 1) / RB);
-    return items < 1216 ? items : 1216;
+    return items < 65536 ? items : 65536;
 }
 
-template <int Q, typename S, typename C>
+template <int Q, typename S, typename C, bool ITER>
 __device__ __forceinline__ void cell_moments(const MomArgs& a, int iters, int i, int j,
                                              Cell<Q, C>& c) {
     using T = Tab<Q>;
@@ -25,7 +28,7 @@ __device__ __forceinline__ void cell_moments(const MomArgs& a, int iters, int i,
     const Consts<C> kc = Consts<C>::make(a.k);
     const long long off = (long long)(i + H) * a.ld + j + GC;
     pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld}, tb, kc, c);
-    if (iters > 0) {
+    if (ITER) {
         C out[Q];
         collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });
         for (int it = 0; it < iters; ++it) {
@@ -38,13 +41,13 @@ __device__ __forceinline__ void cell_moments(const MomArgs& a, int iters, int i,
 }
 
 // Field output of the moments: one thread per cell.
-template <int Q, typename S, typename C>
+template <int Q, typename S, typename C, bool ITER>
 __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= a.n2) return;
     Cell<Q, C> c;
-    cell_moments<Q, S, C>(a, iters, i, j, c);
+    cell_moments<Q, S, C, ITER>(a, iters, i, j, c);
     const size_t m = (size_t)i * a.n2 + j;
     if (a.rho) a.rho[m] = double(c.rho);
     if (a.U1) a.U1[m] = double(c.U1);
@@ -55,13 +58,13 @@ __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters) {
     if (a.F2) a.F2[m] = double(c.F2);
 }
 
-// Residual and conservation sums: persistent blocks stride over (row, 128-column)
-// items; each thread accumulates its cells in FP64 in a fixed order, then a
+// Residual and conservation sums: blocks stride over (row, 128-column) items; each thread accumulates its cells in FP64 in a fixed order, then a
 // warp-shuffle and block reduction in a fixed tree writes one partial per
 // block, so repeated runs give identical bits.  The rest parts of the totals
 // are exact per row: sum_a ref_a(i) = J rho0 and sum_a c_a ref_a(i) = 0.
-template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(RB) k_residual(const MomArgs a, int iters) {
+// The largest |u| is tracked as the largest |u|^2 and rooted once per block.
+template <int Q, typename S, typename C, bool ITER>
+__global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, int iters) {
     const int bx = (a.n2 + RB - 1) / RB;
     const int items = a.n1 * bx;
     const size_t nc = (size_t)a.n1 * a.n2;
@@ -72,26 +75,10 @@ __global__ void __launch_bounds__(RB) k_residual(const MomArgs a, int iters) {
         const int i = it / bx, j = (it % bx) * RB + threadIdx.x;
         if (j >= a.n2) continue;
         Cell<Q, C> c;
-        cell_moments<Q, S, C>(a, iters, i, j, c);
-        const double* g = a.geo + (size_t)i * Geo::stride(Q);
+        cell_moments<Q, S, C, ITER>(a, iters, i, j, c);
         const size_t m = (size_t)i * a.n2 + j;
-        const double u1 = double(c.Ut1), u2 = double(c.Ut2), rho = double(c.rho);
-        const double J = g[Geo::J];
-        const double uu = g[Geo::G11] * u1 * u1 + 2.0 * g[Geo::G12] * u1 * u2 + g[Geo::G22] * u2 * u2;
-        if (a.have_prev) {
-            const double e1 = u1 - a.ut_prev[m], e2 = u2 - a.ut_prev[nc + m];
-            v[0] += J * (g[Geo::G11] * e1 * e1 + 2.0 * g[Geo::G12] * e1 * e2 + g[Geo::G22] * e2 * e2);
-        }
-        a.ut_prev[m] = u1;
-        a.ut_prev[nc + m] = u2;
-        v[1] += J * uu;
-        v[2] += J * a.k.rho0 + double(c.ls);
-        v[3] += double(c.ls1);
-        v[4] += double(c.ls2);
-        v[5] += 0.5 * J * rho * uu;
-        v[6] += J * rho * (g[Geo::M1] * u1 + g[Geo::M2] * u2);
-        v[7] = fmax(v[7], sqrt(uu));
-        v[8] += (rho > 0.0 && isfinite(rho) && isfinite(uu)) ? 0.0 : 1.0;
+        residual_terms<Q, C>(c, a.geo + (size_t)i * Geo::stride(Q), a.k.rho0, a.ut_prev + m,
+                             a.ut_prev + nc + m, a.have_prev != 0, v);
     }
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
@@ -112,7 +99,7 @@ __global__ void __launch_bounds__(RB) k_residual(const MomArgs a, int iters) {
         const int k = threadIdx.x;
         double x = sh[0][k];
         for (int q = 1; q < RB / 32; ++q) x = (k == 7) ? fmax(x, sh[q][k]) : x + sh[q][k];
-        a.partial[(size_t)blockIdx.x * NRED + k] = x;
+        a.partial[(size_t)blockIdx.x * NRED + k] = k == 7 ? sqrt(x) : x;
     }
 }
 
@@ -233,10 +220,12 @@ __global__ void __launch_bounds__(256) k_row_mean(const double* __restrict__ f, 
 template <int Q, typename S, typename C>
 void run_moments(const MomArgs& a, int iters, int reduce, cudaStream_t s) {
     if (reduce) {
-        k_residual<Q, S, C><<<residual_blocks(a.n1, a.n2), RB, 0, s>>>(a, iters);
+        if (iters > 0) k_residual<Q, S, C, true><<<residual_blocks(a.n1, a.n2), RB, 0, s>>>(a, iters);
+        else k_residual<Q, S, C, false><<<residual_blocks(a.n1, a.n2), RB, 0, s>>>(a, iters);
     } else {
         dim3 b(RB), g((a.n2 + RB - 1) / RB, a.n1);
-        k_moments<Q, S, C><<<g, b, 0, s>>>(a, iters);
+        if (iters > 0) k_moments<Q, S, C, true><<<g, b, 0, s>>>(a, iters);
+        else k_moments<Q, S, C, false><<<g, b, 0, s>>>(a, iters);
     }
 }
 

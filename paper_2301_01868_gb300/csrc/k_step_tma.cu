@@ -53,6 +53,22 @@ struct TileGeom {
     static constexpr int SMEM = 2 * BUF * (int)sizeof(S) + 2 * OUT * (int)sizeof(S) + 2 * TABB + 64 + 128;
 };
 
+// Warp-specialised pipeline over the same tiles: STAGES input stages (boxes
+// and table rows), one producer warp issuing TMA loads, TR x TJ / 32 consumer
+// warps that each update 32 cells of a tile row and store them straight to
+// global memory (128-byte row segments).  Full / empty mbarriers per stage
+// replace every CTA-wide barrier of the tile loop.
+template <int Q, typename S>
+struct PipeGeom {
+    using G = TileGeom<Q, S>;
+    static constexpr int STAGES = 3;
+    static constexpr int CONSUMERS = G::NT / 32;
+    static constexpr int NTHREADS = G::NT + 32;
+    static constexpr int IN_BYTES = (G::BUF * (int)sizeof(S) + 127) / 128 * 128;
+    static constexpr int STAGE_BYTES = IN_BYTES + (G::TABB + 127) / 128 * 128;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16 + 128;
+};
+
 // Tensor maps of both state buffers: per buffer, the 8 box shapes of the loads
 // (|c1| = 0..3, c2 zero / nonzero) and the interior map of the tile store.
 struct TmaMaps {
@@ -74,6 +90,10 @@ __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Bounded wait for phase `parity` of the barrier; false on time-out.
@@ -270,7 +290,130 @@ __global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
 #undef s_abort
 }
 
+// The pipelined update (PipeGeom).  Tile k of a CTA uses stage k mod STAGES;
+// the producer re-fills a stage once all consumer warps have released it.
+// Waits are bounded: on time-out the kernel records an error code, the other
+// warps give up at their next wait, and the producer lets its loads in flight
+// land before the CTA exits.
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+    k_fused_ws(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
+    using G = TileGeom<Q, S>;
+    using P = PipeGeom<Q, S>;
+    using T = Tab<Q>;
+    constexpr int H = Lat<Q>::H;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* const smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t* const full = (uint64_t*)(smem + P::STAGES * P::STAGE_BYTES);
+    uint64_t* const empty = full + P::STAGES;
+    volatile int* const s_abort = (volatile int*)(empty + P::STAGES);
+    auto stage_in = [&](int st) { return smem + st * P::STAGE_BYTES; };
+    auto stage_tab = [&](int st) { return smem + st * P::STAGE_BYTES + P::IN_BYTES; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_j = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * tiles_j;
+    if (tid == 0) {
+        for (int st = 0; st < P::STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], P::CONSUMERS);
+        }
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == P::CONSUMERS) {  // producer
+        if (lane == 0) {
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int st = it % P::STAGES;
+                if (it >= P::STAGES && !mbar_wait(&empty[st], (it / P::STAGES - 1) & 1)) {
+                    *s_abort = 1;
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                if (*s_abort) break;
+                issue_tile<Q, S, C>(maps, src, tile, tiles_j, a, stage_in(st), stage_tab(st), &full[st]);
+            }
+            // the loads of the last issued tiles must land before the CTA exits
+            for (int t = it > P::STAGES ? it - P::STAGES : 0; t < it; ++t)
+                mbar_wait(&full[t % P::STAGES], (t / P::STAGES) & 1);
+        }
+        return;
+    }
+
+    const int r = tid / G::TJ, cc = tid % G::TJ;
+    const Consts<C> k = Consts<C>::make(a.k);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int st = it % P::STAGES;
+        if (!mbar_wait(&full[st], (it / P::STAGES) & 1)) {
+            *s_abort = 1;
+            atomicExch(a.err, 1);
+            break;
+        }
+        if (*s_abort) break;
+        const int i0 = (tile / tiles_j) * G::TR, j0 = (tile % tiles_j) * G::TJ;
+        const int i = i0 + r, j = j0 + cc;
+        if (i < a.n1 && j < a.n2) {
+            const C* tb = (const C*)stage_tab(st) + r * T::S;
+            const S* in = (const S*)stage_in(st);
+            Cell<Q, C> c;
+            pull_cell<Q, C>(
+                [&](int al, int dr, int dc) -> C {
+                    return C(Store<S>::lds(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) +
+                                           cc + G::col0(al) + dc));
+                },
+                tb, k, c);
+            S* dst = (S*)a.dst + (long long)(i + H) * a.ld + j + GC;
+            const int dw = wrap_offset(j, a.n2);
+            collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
+                Store<S>::st(dst + al * a.plane, v);
+                if (dw != 0) Store<S>::st(dst + al * a.plane + dw, v);
+            });
+            if (EdgeFill<Q, S>::needed(i, a.n1, a.n2)) {
+                const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo,
+                                        a.bc_hi, C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC};
+                ef.fill(i, j, dst, a.plane, c.rho, c.Ut2);
+            }
+            if (i < H) {
+                const int idx = i * a.n2 + j;
+                ((C*)a.wall_rho)[idx] = c.rho;
+                ((C*)a.wall_ut2)[idx] = c.Ut2;
+            }
+            if (i >= a.n1 - H) {
+                const int idx = (H + (a.n1 - 1 - i)) * a.n2 + j;
+                ((C*)a.wall_rho)[idx] = c.rho;
+                ((C*)a.wall_ut2)[idx] = c.Ut2;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+    }
+}
+
 }  // namespace
+
+template <int Q, typename S>
+static int run_ws(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cudaStream_t s) {
+    using G = TileGeom<Q, S>;
+    using P = PipeGeom<Q, S>;
+    using C = typename Store<S>::C;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_fused_ws<Q, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 P::SMEM) != cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    const int tiles = ((a.n1 + G::TR - 1) / G::TR) * ((a.n2 + G::TJ - 1) / G::TJ);
+    const int grid = tiles < nsm ? tiles : nsm;
+    k_fused_ws<Q, S, C><<<grid, P::NTHREADS, P::SMEM, s>>>(maps, a, src);
+    return 0;
+}
 
 template <int Q, typename S>
 static int run_tma(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cudaStream_t s) {
@@ -292,19 +435,21 @@ static int run_tma(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cud
 }
 
 int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
-                    cudaStream_t s) {
+                    int pipelined, cudaStream_t s) {
     if (Q == 9) {
         switch (prec) {
-            case 1: return run_tma<9, float>(maps, a, src, nsm, s);
-            case 2: return run_tma<9, __half>(maps, a, src, nsm, s);
-            case 3: return run_tma<9, __nv_bfloat16>(maps, a, src, nsm, s);
+            case 1: return pipelined ? run_ws<9, float>(maps, a, src, nsm, s) : run_tma<9, float>(maps, a, src, nsm, s);
+            case 2: return pipelined ? run_ws<9, __half>(maps, a, src, nsm, s) : run_tma<9, __half>(maps, a, src, nsm, s);
+            case 3: return pipelined ? run_ws<9, __nv_bfloat16>(maps, a, src, nsm, s)
+                                     : run_tma<9, __nv_bfloat16>(maps, a, src, nsm, s);
             default: return -1;
         }
     }
     switch (prec) {
-        case 1: return run_tma<21, float>(maps, a, src, nsm, s);
-        case 2: return run_tma<21, __half>(maps, a, src, nsm, s);
-        case 3: return run_tma<21, __nv_bfloat16>(maps, a, src, nsm, s);
+        case 1: return pipelined ? run_ws<21, float>(maps, a, src, nsm, s) : run_tma<21, float>(maps, a, src, nsm, s);
+        case 2: return pipelined ? run_ws<21, __half>(maps, a, src, nsm, s) : run_tma<21, __half>(maps, a, src, nsm, s);
+        case 3: return pipelined ? run_ws<21, __nv_bfloat16>(maps, a, src, nsm, s)
+                                 : run_tma<21, __nv_bfloat16>(maps, a, src, nsm, s);
         default: return -1;
     }
 }

@@ -204,10 +204,7 @@ class Server:
                 for a in members:
                     a["steps"] += self.chunk
             for Q, (b, members) in list(self._batches.items()):
-                try:
-                    res, _ = b.residual()
-                except clbm.UnstableError:
-                    res = np.full(len(members), np.nan)
+                res, _ = b.residual()   # NaN marks a lattice that went unstable
                 for a, r in zip(members, res):
                     a["checks"] += 1
                     conv = a["checks"] > 1 and np.isfinite(r) and r <= a["req"].tol

@@ -143,3 +143,50 @@ def test_autotuner_picks_a_variant():
     b.step(10)
     assert grids[0].t == t0 + 10
     b.close()
+
+
+@pytest.mark.parametrize("Q,prec", [(9, 1), (21, 2)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_batch_matches_lattices_alone_more_storage(Q, prec, variant):
+    """D2Q9 with FP32 storage and D2Q21 with FP16 storage: the batch gives the
+    lattices' own results (the single-lattice path runs the per-cell kernel)."""
+    c = _clbm()
+    stream = torch.cuda.Stream()
+    alone = build(Q, prec, stream)
+    mixed = build(Q, prec, stream)
+    for g in alone:
+        g.set_kernel(1)
+        g.step(300)
+    b = c.Batch(mixed)
+    b.set_variant(variant)
+    b.step(300)
+    for ga, gm in zip(alone, mixed):
+        sa, sm = ga.state(), gm.state()
+        dev = np.abs(sa - sa.mean(axis=(1, 2), keepdims=True)).max()
+        assert np.abs(sa - sm).max() <= (1e-6 if prec == 1 else 2e-3) * max(dev, 1e-12)
+    b.close()
+
+
+def test_batch_residual_isolates_an_unstable_lattice():
+    """One lattice with a non-finite density: its residual is NaN, every other
+    lattice's residual is still returned and matches its own."""
+    c = _clbm()
+    stream = torch.cuda.Stream()
+    grids = build(21, 0, stream)
+    ref = build(21, 0, stream)
+    st = grids[2].state()
+    st[:, 3, 5] = np.nan
+    grids[2].set_state(st)
+    b = c.Batch(grids)
+    b.residual()
+    b.step(20)
+    for g in ref:
+        g.residual()
+        g.step(20)
+    res, _ = b.residual()
+    assert np.isnan(res[2])
+    for k, g in enumerate(ref):
+        if k != 2:
+            r, _ = g.residual()
+            assert abs(res[k] - r) <= 1e-12 * abs(r)
+    b.close()
