@@ -73,8 +73,8 @@ def peaks():
 def traffic_for(workload, kernel):
     """Per-launch DRAM bytes of the timed update kernel from the committed ncu
     summary, only if it was taken on the current kernel source (kernel 1: the
-    per-cell kernel; otherwise the TMA-staged one, the automatic choice for
-    16/32-bit storage)."""
+    per-cell kernel; 0 and 3: the pipelined TMA kernel, the automatic choice
+    for 16/32-bit storage; 2: not captured)."""
     p = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
     if not os.path.exists(p):
         return None
@@ -82,6 +82,8 @@ def traffic_for(workload, kernel):
         d = json.load(f)
     e = d.get(workload)
     if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    if kernel == 2:
         return None
     return e.get("bytes_per_launch_per_cell_kernel" if kernel == 1 else "bytes_per_launch")
 

@@ -2,8 +2,9 @@
 
 This module holds no arithmetic of the lattice Boltzmann method itself: it
 only builds the wall-normal cell edges of the paper's grids (App. C linear
-contraction, a geometric stretch, polar radii), picks the azimuthal size of
-the circular cases, and draws seeded random fields.  Both the CUDA library's
+contraction, a geometric stretch, polar radii), the node positions of
+general (non-separable) grids, picks the azimuthal size of the circular
+cases, and draws seeded random fields.  Both the CUDA library's
 callers and the oracle take their grids and random perturbations from here.
 """
 import math
@@ -60,6 +61,56 @@ def geometric_stretch_edges(N, ratio, length, origin=0.0):
     e = np.concatenate([[0.0], np.cumsum(full)])
     e[-1] = length
     return origin + e
+
+
+GHOST = 4  # node layers beyond each wall and each periodic end in a node array
+
+
+def _node_q(n):
+    """Node coordinates q = k - 1/2 for k = -3 .. n + 4 (1-based node index)."""
+    return np.arange(1 - GHOST, n + GHOST + 1, dtype=np.float64) - 0.5
+
+
+def mapped_nodes(fun, n1, n2, ghosts="mirror"):
+    """Node positions of a general grid, shape (n1 + 8, n2 + 8, 2): nodes
+    i = -3 .. n1 + 4 (wall-normal) by j = -3 .. n2 + 4 (periodic) at
+    x = fun(q1, q2), q = (i - 1/2, j - 1/2).  fun takes arrays and returns
+    (x, y); it must give the periodic images itself (fun(q1, q2 + n2) = fun(q1,
+    q2) shifted by the period).  Rows beyond a wall: ghosts="extend" evaluates
+    fun there too; ghosts="mirror" reflects the first four rows inside through
+    the wall, which must be a straight line (the wall node positions fun(0, q2)
+    and fun(n1, q2) each lie on one line)."""
+    q1, q2 = np.meshgrid(_node_q(n1), _node_q(n2), indexing="ij")
+    x, y = fun(q1, q2)
+    P = np.stack([np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64)], axis=-1)
+    if ghosts == "extend":
+        return np.ascontiguousarray(P)
+    if ghosts != "mirror":
+        raise ValueError("ghosts must be 'mirror' or 'extend'")
+    for lo in (True, False):
+        qw = 0.0 if lo else float(n1)
+        w = np.stack(fun(np.full(n2 + 2 * GHOST, qw), _node_q(n2)), axis=-1)
+        a, b = w[0], w[-1]
+        t = (b - a) / np.linalg.norm(b - a)          # wall direction
+        nrm = np.array([-t[1], t[0]])
+        for k in range(1, GHOST + 1):
+            gi = GHOST - k if lo else GHOST + n1 + k - 1          # ghost row index
+            mi = GHOST + k - 1 if lo else GHOST + n1 - k          # mirrored interior row
+            d = P[mi] - a
+            P[gi] = P[mi] - 2.0 * (d @ nrm)[:, None] * nrm[None, :]
+    return np.ascontiguousarray(P)
+
+
+def sheared_channel(n1, n2, h=1.0, L2=1.0, shear=0.3):
+    """Affine map with parallelogram cells: x = q1 h, y = q2 L2 + shear q1 h."""
+    return lambda q1, q2: (q1 * h, q2 * L2 + shear * q1 * h)
+
+
+def wavy_channel(n1, n2, h=1.0, L2=1.0, amp=0.2):
+    """Non-separable map between straight walls x = 0 and x = n1 h:
+    x = h (q1 + amp sin(pi q1 / n1) sin(2 pi q2 / n2)), y = q2 L2."""
+    return lambda q1, q2: (h * (q1 + amp * np.sin(np.pi * q1 / n1) * np.sin(2.0 * np.pi * q2 / n2)),
+                           q2 * L2)
 
 
 def polar_edges(R1, R2, Nr, CR=0.0):
