@@ -61,7 +61,9 @@ typedef enum {
 /* Geometry of the coordinate map x(q) (Sec. 2, App. C, App. D). */
 typedef enum {
     CLBM_GEOM_PLANAR = 0,  /* x = (x^1_i, (j - 1/2) step2), x^1_i edge midpoints */
-    CLBM_GEOM_POLAR = 1    /* x = r_i (cos th_j, sin th_j), th_j = (j - 1/2) 2 pi / n2 */
+    CLBM_GEOM_POLAR = 1,   /* x = r_i (cos th_j, sin th_j), th_j = (j - 1/2) 2 pi / n2 */
+    CLBM_GEOM_GENERAL = 2  /* node positions given (nodes); Sec. 2 in full generality:
+                              metric, volume and Theta of every cell, per-cell tables */
 } clbm_geom_kind;
 
 /* Wall conditions of App. B (direction q^2 is always periodic). */
@@ -77,15 +79,23 @@ typedef struct {
     int kind;               /* clbm_geom_kind */
     const double* edges1;   /* host, n1+1 increasing wall-normal edges x'_0..x'_n1
                                (radii for POLAR, all > 0); nodes sit at midpoints,
-                               walls at edges1[0] and edges1[n1] */
+                               walls at edges1[0] and edges1[n1]; unused by GENERAL */
     double step2;           /* PLANAR: physical step along q^2 (> 0) */
     double dx;              /* Delta x of the tangent vectors (Sec. 2); <= 0 picks
-                               the average wall-normal step (edges1[n1]-edges1[0])/n1 */
+                               the average wall-normal step (edges1[n1]-edges1[0])/n1;
+                               GENERAL needs dx > 0 */
     int bc_lo, bc_hi;       /* clbm_wall_bc of the walls at edges1[0] / edges1[n1] */
     int device;             /* CUDA device ordinal */
     void* stream;           /* cudaStream_t for all work of this grid (NULL: legacy default) */
     void* workspace;        /* optional caller-owned device memory (NULL: library allocates) */
     size_t workspace_bytes; /* size of workspace */
+    const double* nodes;    /* GENERAL only, host: positions (x, y) of the nodes
+                               i = -3..n1+4 (wall-normal) by j = -3..n2+4 (periodic),
+                               row-major [(n1+8)][(n2+8)][2], node (i, j) at
+                               q = (i - 1/2, j - 1/2); the rows beyond the walls
+                               are the ghost nodes of App. B (e.g. mirror images
+                               through straight walls), the columns beyond the ends
+                               the periodic images.  Read during create only. */
 } clbm_grid_desc;
 
 typedef struct {

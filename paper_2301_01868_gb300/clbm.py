@@ -16,7 +16,7 @@ _LIB_PATH = os.path.join(_HERE, "libclbm.so")
 
 D2Q9, D2Q21 = 9, 21
 FP64, FP32, FP32_F16STORE, FP32_BF16STORE = 0, 1, 2, 3
-PLANAR, POLAR = 0, 1
+PLANAR, POLAR, GENERAL = 0, 1, 2
 NOSLIP, MOVING = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP32_F16STORE, "bf16": FP32_BF16STORE}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "EBUSY"}
@@ -36,7 +36,8 @@ class _Desc(C.Structure):
     _fields_ = [("lattice", C.c_int), ("precision", C.c_int), ("n1", C.c_int), ("n2", C.c_int),
                 ("kind", C.c_int), ("edges1", C.POINTER(C.c_double)), ("step2", C.c_double),
                 ("dx", C.c_double), ("bc_lo", C.c_int), ("bc_hi", C.c_int), ("device", C.c_int),
-                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+                ("nodes", C.POINTER(C.c_double))]
 
 
 class _Case(C.Structure):
@@ -113,19 +114,29 @@ def _is_device(x):
     return x is not None and not isinstance(x, np.ndarray) and x.is_cuda
 
 
-def _desc(lattice, precision, n1, n2, kind, edges, step2, dx, bc_lo, bc_hi, device, stream):
+def _desc(lattice, precision, n1, n2, kind, edges, step2, dx, bc_lo, bc_hi, device, stream, nodes=None):
+    dp = C.POINTER(C.c_double)
+    if kind == GENERAL:
+        P = np.ascontiguousarray(nodes, dtype=np.float64)
+        if P.shape != (n1 + 8, n2 + 8, 2):
+            raise ValueError("nodes must be (n1+8, n2+8, 2)")
+        d = _Desc(lattice, precision, n1, n2, kind, None, float(step2), float(dx), bc_lo, bc_hi,
+                  device, stream, None, 0, P.ctypes.data_as(dp))
+        return d, P
     e = np.ascontiguousarray(edges, dtype=np.float64)
     if e.shape != (n1 + 1,):
         raise ValueError("edges must have n1+1 entries")
-    d = _Desc(lattice, precision, n1, n2, kind, e.ctypes.data_as(C.POINTER(C.c_double)),
-              float(step2), float(dx), bc_lo, bc_hi, device, stream, None, 0)
+    d = _Desc(lattice, precision, n1, n2, kind, e.ctypes.data_as(dp), float(step2), float(dx), bc_lo,
+              bc_hi, device, stream, None, 0, None)
     return d, e
 
 
-def workspace_bytes(lattice, precision, n1, n2):
-    """Device bytes a grid of this size needs."""
+def workspace_bytes(lattice, precision, n1, n2, kind=PLANAR):
+    """Device bytes a grid of this size needs (general grids hold per-cell
+    geometry and tables)."""
     e = np.arange(n1 + 1, dtype=np.float64) + 1.0
-    d, _ = _desc(lattice, precision, n1, n2, PLANAR, e, 1.0, 0.0, 0, 0, 0, None)
+    nodes = np.zeros((n1 + 8, n2 + 8, 2)) if kind == GENERAL else None
+    d, _ = _desc(lattice, precision, n1, n2, kind, e, 1.0, 1.0, 0, 0, 0, None, nodes)
     out = C.c_size_t()
     _check(lib().clbm_workspace_bytes(C.byref(d), C.byref(out)))
     return out.value
@@ -134,15 +145,18 @@ def workspace_bytes(lattice, precision, n1, n2):
 class Grid:
     """A lattice advanced on one GPU by the fused curvilinear LBM update.
 
-    edges  : n1+1 wall-normal cell edges (radii for POLAR).
+    edges  : n1+1 wall-normal cell edges (radii for POLAR); None for GENERAL.
     step2  : q^2 step of PLANAR grids.
+    nodes  : GENERAL grids: node positions (n1+8, n2+8, 2) of nodes i = -3..n1+4,
+             j = -3..n2+4 at q = (i - 1/2, j - 1/2), ghosts and periodic images
+             included (clbm_inputs.mapped_nodes builds them); dx > 0 required.
     precision : FP64, FP32, FP32_F16STORE or FP32_BF16STORE (or "fp64", ...).
     The device workspace is a torch uint8 tensor; work goes on torch's
     current stream of `device` unless `stream` (a torch.cuda.Stream) is given.
     """
 
     def __init__(self, lattice, n1, n2, edges, kind=PLANAR, step2=1.0, precision=FP64, dx=0.0,
-                 bc_lo=NOSLIP, bc_hi=NOSLIP, device=0, stream=None):
+                 bc_lo=NOSLIP, bc_hi=NOSLIP, device=0, stream=None, nodes=None):
         import torch
 
         if isinstance(precision, str):
@@ -153,7 +167,8 @@ class Grid:
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         d, self._edges = _desc(self.Q, self.precision, self.n1, self.n2, self.kind, edges, step2, dx,
-                               int(bc_lo), int(bc_hi), self.device.index, self.stream.cuda_stream)
+                               int(bc_lo), int(bc_hi), self.device.index, self.stream.cuda_stream,
+                               nodes)
         nb = C.c_size_t()
         _check(lib().clbm_workspace_bytes(C.byref(d), C.byref(nb)))
         self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)

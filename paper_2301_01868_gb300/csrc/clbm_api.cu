@@ -67,6 +67,8 @@ struct clbm_grid {
     std::vector<double> edges;
     double step2;
     double* stage;          // lazily allocated FP64 staging buffer for host transfers
+    int ncol;               // geometry columns: 1 (planar, polar) or n2 (general)
+    std::vector<double> nodes;  // node positions of a general grid (for the no-flow clone)
     void* phys[2];          // the two state buffers (stA / stB alternate over them)
     TmaMaps* tma;           // tensor maps of the TMA-staged update (16/32-bit storage)
     int nsm;                // SM count of the device
@@ -83,20 +85,26 @@ clbm_status layout_of(const clbm_grid_desc* d, Layout* L, int* ld_out, int* h_ou
     if (d->n1 < 4 || d->n2 < 1) return fail(CLBM_EINVAL, "need n1 >= 4 and n2 >= 1");
     if ((long long)d->n1 * d->n2 > (1LL << 31) / 32)
         return fail(CLBM_EINVAL, "grid too large for 32-bit cell indexing");
+    if (d->kind < CLBM_GEOM_PLANAR || d->kind > CLBM_GEOM_GENERAL)
+        return fail(CLBM_EINVAL, "kind must be PLANAR, POLAR or GENERAL");
     const int Q = d->lattice, h = Q == 9 ? 1 : 3;
     const int ld = (d->n2 + 2 * GC + 31) / 32 * 32;
     const size_t sb = storage_bytes(d->precision), cb = compute_bytes(d->precision);
-    const int TS = Q == 9 ? Tab<9>::S : Tab<21>::S;
+    // general grids carry per-cell geometry and tables, the others one row each
+    const int ncol = d->kind == CLBM_GEOM_GENERAL ? d->n2 : 1;
+    const size_t tab_entries = ncol > 1 ? (size_t)(Q == 9 ? CellTabLayout<9>::S : CellTabLayout<21>::S) *
+                                              d->n1 * d->n2
+                                        : (size_t)(Q == 9 ? Tab<9>::S : Tab<21>::S) * d->n1;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     L->stA = take((size_t)Q * (d->n1 + 2 * h) * ld * sb);
     L->stB = take((size_t)Q * (d->n1 + 2 * h) * ld * sb);
-    L->tab = take((size_t)d->n1 * TS * cb);
-    L->geo = take((size_t)d->n1 * Geo::stride(Q) * 8);
+    L->tab = take(tab_entries * cb);
+    L->geo = take((size_t)d->n1 * ncol * Geo::stride(Q) * 8);
     L->wall_r = take((size_t)2 * h * d->n2 * cb);
     L->wall_u = take((size_t)2 * h * d->n2 * cb);
-    L->ghost = take((size_t)2 * h * Q * 2 * 8);
-    L->pos = take((size_t)(d->n1 + 8) * 9 * 2 * 8);
+    L->ghost = take((size_t)2 * h * Q * 2 * ncol * 8);
+    L->pos = take((size_t)(d->n1 + 8) * (ncol + 8) * 2 * 8);
     L->partial = take((size_t)moments_blocks(d->n1, d->n2) * NRED * 8);
     L->red = take(16 * 8);
     L->prev = take((size_t)2 * d->n1 * d->n2 * 8);
@@ -155,6 +163,7 @@ StepArgs step_args(const clbm_grid* g, const void* src, void* dst) {
     a.U0_hi = g->cs.u_wall_hi;
     a.bc_lo = g->bc_lo;
     a.bc_hi = g->bc_hi;
+    a.ncol = g->ncol;
     a.iters = g->cs.force_iterations;
     a.err = g->err;
     return a;
@@ -193,6 +202,7 @@ MomArgs mom_args(const clbm_grid* g) {
     m.rho0 = g->cs.rho0;
     m.g1 = g->cs.g_ext[0];
     m.g2 = g->cs.g_ext[1];
+    m.ncol = g->ncol;
     m.ut_prev = g->prev;
     m.partial = g->partial;
     return m;
@@ -230,8 +240,8 @@ void fill_ghosts(clbm_grid* g) {
 }
 
 clbm_status rebuild_tables(clbm_grid* g) {
-    launch_reference(g->Q, g->geo, g->n1, g->cs.rho0, g->stream);
-    launch_tables(g->Q, g->prec, g->geo, g->tab, g->ghost, g->n1, g->cs.tau, g->bc_lo, g->bc_hi,
+    launch_reference(g->Q, g->geo, g->n1 * g->ncol, g->cs.rho0, g->stream);
+    launch_tables(g->Q, g->prec, g->geo, g->tab, g->ghost, g->n1, g->n2, g->ncol, g->bc_lo, g->bc_hi,
                   g->stream);
     g->launches += 3;
     CK(cudaGetLastError());
@@ -274,22 +284,32 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
     int ld, h;
     clbm_status st = layout_of(d, &L, &ld, &h);
     if (st != CLBM_OK) return st;
-    if (d->kind != CLBM_GEOM_PLANAR && d->kind != CLBM_GEOM_POLAR)
-        return fail(CLBM_EINVAL, "kind must be PLANAR or POLAR");
     if ((d->bc_lo != 0 && d->bc_lo != 1) || (d->bc_hi != 0 && d->bc_hi != 1))
         return fail(CLBM_EINVAL, "bad wall condition");
-    if (!d->edges1) return fail(CLBM_EINVAL, "edges1 is NULL");
-    std::vector<double> e(d->edges1, d->edges1 + d->n1 + 1);
-    for (int k = 0; k < d->n1; ++k)
-        if (!(e[k + 1] > e[k]) || !std::isfinite(e[k + 1]))
-            return fail(CLBM_EINVAL, "edges1 must be finite and strictly increasing");
-    if (d->kind == CLBM_GEOM_PLANAR && !(d->step2 > 0.0))
-        return fail(CLBM_EINVAL, "step2 must be > 0");
-    const double dx = d->dx > 0.0 ? d->dx : (e[d->n1] - e[0]) / d->n1;
-    // node positions of rows -3..n1+4, columns -3..5 (1-based)
-    std::vector<double> pos((size_t)(d->n1 + 8) * 9 * 2);
+    const bool general = d->kind == CLBM_GEOM_GENERAL;
+    const int ncol = general ? d->n2 : 1;
+    std::vector<double> e, pos;
+    double dx = d->dx;
+    if (general) {
+        if (!d->nodes) return fail(CLBM_EINVAL, "GENERAL needs nodes");
+        if (!(d->dx > 0.0)) return fail(CLBM_EINVAL, "GENERAL needs dx > 0");
+        pos.assign(d->nodes, d->nodes + (size_t)(d->n1 + 8) * (d->n2 + 8) * 2);
+        for (double v : pos)
+            if (!std::isfinite(v)) return fail(CLBM_EINVAL, "node positions must be finite");
+    } else {
+        if (!d->edges1) return fail(CLBM_EINVAL, "edges1 is NULL");
+        e.assign(d->edges1, d->edges1 + d->n1 + 1);
+        for (int k = 0; k < d->n1; ++k)
+            if (!(e[k + 1] > e[k]) || !std::isfinite(e[k + 1]))
+                return fail(CLBM_EINVAL, "edges1 must be finite and strictly increasing");
+        if (d->kind == CLBM_GEOM_PLANAR && !(d->step2 > 0.0))
+            return fail(CLBM_EINVAL, "step2 must be > 0");
+        if (!(dx > 0.0)) dx = (e[d->n1] - e[0]) / d->n1;
+        // node positions of rows -3..n1+4, columns -3..5 (1-based)
+        pos.resize((size_t)(d->n1 + 8) * 9 * 2);
+    }
     const double pi = 3.14159265358979323846;
-    for (int i = -3; i <= d->n1 + 4; ++i) {
+    for (int i = -3; !general && i <= d->n1 + 4; ++i) {
         const double s = node_coord(e, d->n1, i);
         if (d->kind == CLBM_GEOM_POLAR && !(s > 0.0))
             return fail(CLBM_EINVAL, "mirrored ghost radius %g <= 0 at row %d: the annulus is "
@@ -323,6 +343,8 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
     g->L = L;
     g->edges = e;
     g->step2 = d->step2;
+    g->ncol = ncol;
+    if (general) g->nodes = pos;
     cudaError_t ce = cudaSetDevice(d->device);
     if (ce != cudaSuccess) {
         delete g;
@@ -364,7 +386,7 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(g->pos, pos.data(), pos.size() * 8, cudaMemcpyHostToDevice, g->stream);
     if (ce == cudaSuccess) {
-        launch_geometry(g->Q, g->pos, g->n1, dx, d->kind == CLBM_GEOM_POLAR, g->geo, g->stream);
+        launch_geometry(g->Q, g->pos, g->n1, ncol, dx, d->kind != CLBM_GEOM_PLANAR, g->geo, g->stream);
         g->launches++;
         ce = cudaGetLastError();
     }
@@ -373,7 +395,7 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
         clbm_destroy(g);
         return fail(CLBM_ECUDA, "geometry precompute: %s", cudaGetErrorString(ce));
     }
-    if (g->prec != CLBM_FP64) {
+    if (g->prec != CLBM_FP64 && !general) {
         int major = 0;
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, d->device);
         if (major >= 9 && make_tma_maps(g->Q, g->prec, &g->tma, g->phys[0], g->phys[1], g->n1, g->n2,
@@ -381,16 +403,17 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
             g->tma = nullptr;
     }
     // every cell volume must be positive
-    std::vector<double> geo((size_t)g->n1 * Geo::stride(g->Q));
+    std::vector<double> geo((size_t)g->n1 * ncol * Geo::stride(g->Q));
     ce = cudaMemcpy(geo.data(), g->geo, geo.size() * 8, cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) {
         clbm_destroy(g);
         return fail(CLBM_ECUDA, "geometry readback: %s", cudaGetErrorString(ce));
     }
-    for (int r = 0; r < g->n1; ++r)
-        if (!(geo[(size_t)r * Geo::stride(g->Q) + Geo::J] > 0.0)) {
+    for (size_t r = 0; r < (size_t)g->n1 * ncol; ++r)
+        if (!(geo[r * Geo::stride(g->Q) + Geo::J] > 0.0)) {
             clbm_destroy(g);
-            return fail(CLBM_EINVAL, "cell volume J <= 0 at row %d", r + 1);
+            return fail(CLBM_EINVAL, "cell volume J <= 0 at row %d, column %d", (int)(r / ncol) + 1,
+                        (int)(r % ncol) + 1);
         }
     *out = g;
     return CLBM_OK;
@@ -406,7 +429,7 @@ clbm_status clbm_set_case(clbm_handle g, const clbm_case* c) {
     g->have_case = true;
     st = rebuild_tables(g);
     if (st != CLBM_OK) return st;
-    launch_state_from_fp64(g->Q, g->prec, nullptr, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
+    launch_state_from_fp64(g->Q, g->prec, nullptr, g->geo, g->stA, g->n1, g->n2, g->ld, g->h, g->ncol,
                            g->stream);
     launch_wall_init(g->prec, g->wall_r, g->wall_u, nullptr, nullptr, g->n1, g->n2, g->h,
                      c->rho0, g->stream);
@@ -446,7 +469,7 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
                 du = extra + nc;
             }
         }
-        launch_state_from_fp64(g->Q, g->prec, dN, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
+        launch_state_from_fp64(g->Q, g->prec, dN, g->geo, g->stA, g->n1, g->n2, g->ld, g->h, g->ncol,
                                g->stream);
         launch_wall_init(g->prec, g->wall_r, g->wall_u, dr, du, g->n1, g->n2, g->h, g->cs.rho0,
                          g->stream);
@@ -455,7 +478,7 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
         CK(cudaStreamSynchronize(g->stream));
         cudaFree(extra);
     } else {
-        launch_state_from_fp64(g->Q, g->prec, dN, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
+        launch_state_from_fp64(g->Q, g->prec, dN, g->geo, g->stA, g->n1, g->n2, g->ld, g->h, g->ncol,
                                g->stream);
         launch_wall_init(g->prec, g->wall_r, g->wall_u, dr, du, g->n1, g->n2, g->h, g->cs.rho0,
                          g->stream);
@@ -478,7 +501,7 @@ clbm_status clbm_get_state(clbm_handle g, double* Np, int dst_is_device) {
         st = staging(g, &dN);
         if (st != CLBM_OK) return st;
     }
-    launch_state_to_fp64(g->Q, g->prec, g->stA, g->geo, dN, g->n1, g->n2, g->ld, g->h,
+    launch_state_to_fp64(g->Q, g->prec, g->stA, g->geo, dN, g->n1, g->n2, g->ld, g->h, g->ncol,
                          g->stream);
     g->launches++;
     CK(cudaGetLastError());
@@ -614,7 +637,8 @@ clbm_status clbm_no_flow_adjust(clbm_handle g, long long nsteps, double* rho_nf)
     d.n1 = g->n1;
     d.n2 = g->n2;
     d.kind = g->kind;
-    d.edges1 = g->edges.data();
+    d.edges1 = g->edges.empty() ? nullptr : g->edges.data();
+    d.nodes = g->nodes.empty() ? nullptr : g->nodes.data();
     d.step2 = g->step2;
     d.dx = g->dx;
     d.bc_lo = g->bc_lo;
@@ -638,18 +662,24 @@ clbm_status clbm_no_flow_adjust(clbm_handle g, long long nsteps, double* rho_nf)
     if (st == CLBM_OK) st = clbm_moments(nf, rho, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1);
     if (st == CLBM_OK) st = clbm_get_state(nf, Np, 1);
     if (st == CLBM_OK) {
-        launch_row_mean(rho, g->n1, g->n2, rowm, g->stream);
-        // Eq. 23: J <- J rho_nf / rho0, then references and tables anew
-        launch_scale_volume(g->Q, g->geo, rowm, g->n1, g->cs.rho0, g->stream);
-        g->launches += 2;
+        // Eq. 23: J <- J rho_nf / rho0 (the row mean of rho_nf where one
+        // geometry row serves the whole row), then references and tables anew
+        if (g->ncol == 1) {
+            launch_row_mean(rho, g->n1, g->n2, rowm, g->stream);
+            g->launches++;
+        }
+        launch_scale_volume(g->Q, g->geo, g->ncol == 1 ? rowm : rho, g->n1 * g->ncol, g->cs.rho0,
+                            g->stream);
+        g->launches++;
         st = rebuild_tables(g);
     }
     if (st == CLBM_OK) {
         // keep the no-flow state; its last-collision densities scale by rho0/rho_nf
-        launch_state_from_fp64(g->Q, g->prec, Np, g->geo, g->stA, g->n1, g->n2, g->ld, g->h,
+        launch_state_from_fp64(g->Q, g->prec, Np, g->geo, g->stA, g->n1, g->n2, g->ld, g->h, g->ncol,
                                g->stream);
         launch_wall_copy(g->prec, g->wall_r, g->wall_u, (const double*)nf->wall_r,
-                         (const double*)nf->wall_u, rowm, g->n1, g->n2, g->h, g->cs.rho0, g->stream);
+                         (const double*)nf->wall_u, g->ncol == 1 ? rowm : rho, g->n1, g->n2, g->h,
+                         g->cs.rho0, g->ncol, g->stream);
         g->launches += 2;
         if (cudaGetLastError() != cudaSuccess) st = fail(CLBM_ECUDA, "no-flow state transfer failed");
     }
@@ -896,6 +926,8 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
     for (int k = 0; k < n; ++k) {
         if (!grids[k]) return fail(CLBM_EINVAL, "grid %d is NULL", k);
         if (!grids[k]->have_case) return fail(CLBM_EINVAL, "grid %d has no case", k);
+        if (grids[k]->ncol != 1)
+            return fail(CLBM_EINVAL, "grid %d is a general grid: batches take planar and polar grids", k);
         if (grids[k]->Q != grids[0]->Q || grids[k]->prec != grids[0]->prec ||
             grids[k]->device != grids[0]->device || grids[k]->stream != grids[0]->stream)
             return fail(CLBM_EINVAL, "grids of a batch share lattice, precision, device and stream");

@@ -37,18 +37,88 @@ struct Cell {
     C ls, ls1, ls2;                           // sums of the lagged sigma: 1, c^1, c^2 weighted
 };
 
+// Coefficient tables as the update reads them.  s(k): header value k of
+// Tab<Q> (INVJ .. M2); pa(q), pd(q): Christoffel contractions and pull
+// offsets of pair q; pb(q): (P0_a, E11, E22, E12); p0(q): P0_a alone.
+//
+// RowTab: one Tab<Q> block per row (planar and polar grids), read as
+// aligned vectors (global or shared memory).
+template <int Q, typename C>
+struct RowTab {
+    // the pull offset vanishes for directions with c^1 = 0 (same row)
+    static constexpr bool ALL_OFFSETS = false;
+    const C* p;
+    __device__ __forceinline__ C s(int k) const { return p[k]; }
+    __device__ __forceinline__ V4<C> pa(int q) const { return ld4(p + Tab<Q>::pa(q)); }
+    __device__ __forceinline__ V4<C> pb(int q) const { return ld4(p + Tab<Q>::pb(q)); }
+    __device__ __forceinline__ C p0(int q) const { return p[Tab<Q>::pb(q)]; }
+    __device__ __forceinline__ V4<C> pd(int q) const { return ld4(p + Tab<Q>::pd(q)); }
+};
+
+// Rest polynomial of Eq. 19 at U = Ut = 0 in the compute type:
+// 1 + [c.(g - 1).c / T0 - tr(g - 1)] / 2 for direction a.
+template <int Q, typename C>
+__device__ __forceinline__ C rest_poly_c(int a, C gi11, C gi12, C gi22) {
+    const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
+    const C q = c1 * c1 * (gi11 - C(1)) + C(2) * c1 * c2 * gi12 + c2 * c2 * (gi22 - C(1));
+    return C(1) + C(0.5) * (q * C(1.0 / Lat<Q>::T0) - (gi11 - C(1)) - (gi22 - C(1)));
+}
+
+// CellTab: per-cell tables of general grids, one plane of n1 n2 values per
+// entry (CellTabLayout), so a warp's loads are coalesced.  The dPi weights
+// and P0 are formed from the metric and the contractions instead of stored.
+template <int Q, typename C>
+struct CellTab {
+    using L = CellTabLayout<Q>;
+    // every direction pulls from a cell with its own reference
+    static constexpr bool ALL_OFFSETS = true;
+    const C* p;             // entry 0 of this cell
+    size_t st;              // plane stride (cells)
+    __device__ __forceinline__ C s(int k) const { return p[(size_t)k * st]; }
+    __device__ __forceinline__ V4<C> pa(int q) const {
+        return {p[(size_t)L::pa(q) * st], p[(size_t)(L::pa(q) + 1) * st], p[(size_t)(L::pa(q) + 2) * st],
+                p[(size_t)(L::pa(q) + 3) * st]};
+    }
+    __device__ __forceinline__ V4<C> pd(int q) const {
+        return {p[(size_t)L::pd(q) * st], p[(size_t)(L::pd(q) + 1) * st], C(0), C(0)};
+    }
+    __device__ __forceinline__ C p0(int q) const {
+        return rest_poly_c<Q, C>(Lat<Q>::plus(q), s(Tab<Q>::G11), s(Tab<Q>::G12), s(Tab<Q>::G22));
+    }
+    __device__ __forceinline__ V4<C> pb(int q) const {
+        const int a = Lat<Q>::plus(q);
+        const C w = C(Lat<Q>::w(a)), c1 = C(c1_of(a)), c2 = C(c2_of(a));
+        const V4<C> A = pa(q);
+        const C D1 = A.x + A.z, D2 = A.y + A.w;
+        return {p0(q), C(2) * w * c1 * D1, C(2) * w * c2 * D2, w * (c1 * D2 + c2 * D1)};
+    }
+};
+
+// The table of cell (i, j): RowTab for planar / polar grids (GEN = false),
+// CellTab for general grids.
+template <int Q, typename C, bool GEN> struct TabOf;
+template <int Q, typename C> struct TabOf<Q, C, false> {
+    __device__ static __forceinline__ RowTab<Q, C> at(const void* tab, int i, int, int, int) {
+        return {(const C*)tab + (size_t)i * Tab<Q>::S};
+    }
+};
+template <int Q, typename C> struct TabOf<Q, C, true> {
+    __device__ static __forceinline__ CellTab<Q, C> at(const void* tab, int i, int j, int n1, int n2) {
+        return {(const C*)tab + (size_t)i * n2 + j, (size_t)n1 * n2};
+    }
+};
+
 // Advection (Eq. 12) with the lagged read of N'(q, t-1), moments (Eqs. 7, 8,
 // 10) and the lagged inertial force (Eq. 15 with N'(q, t-1)):
 //   F^k = -1/(2J) sum_b a^k_b [N'_b(q, t-1) + N_{opp b}(q, t)] + rho g^k.
 // ld(alpha, dr, dc) returns the stored value of population alpha at the cell
 // offset by (dr, dc) rows / columns; dr and dc are compile-time after unrolling.
-template <int Q, typename C, typename LD>
-__device__ __forceinline__ void pull_cell(LD&& ld, const C* __restrict__ tb, const Consts<C>& k,
-                                          Cell<Q, C>& c) {
+template <int Q, typename C, typename LD, typename TB>
+__device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>& k, Cell<Q, C>& c) {
     using L = Lat<Q>;
     using T = Tab<Q>;
-    C Sd = tb[T::D0], S1 = tb[T::M1], S2 = tb[T::M2];
-    C f1 = tb[T::F01], f2 = tb[T::F02];
+    C Sd = tb.s(T::D0), S1 = tb.s(T::M1), S2 = tb.s(T::M2);
+    C f1 = tb.s(T::F01), f2 = tb.s(T::F02);
     c.d[0] = ld(0, 0, 0);
     Sd += c.d[0];
     c.ls = c.d[0];
@@ -58,7 +128,7 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const C* __restrict__ tb, con
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const int c1 = c1_of(a), c2 = c2_of(a);
-        const V4<C> A = ld4(tb + T::pa(q));
+        const V4<C> A = tb.pa(q);
         // pulled: N_a(q) from q - c_a, N_b(q) from q + c_a; lagged: own values
         const C pa = ld(a, -c1, -c2);
         const C pb = ld(b, c1, c2);
@@ -74,8 +144,8 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const C* __restrict__ tb, con
         c.ls += la + lb;
         if (c1 != 0) c.ls1 += C(c1) * (la - lb);
         if (c2 != 0) c.ls2 += C(c2) * (la - lb);
-        if (c1 != 0) {
-            const V4<C> D = ld4(tb + T::pd(q));
+        if (c1 != 0 || TB::ALL_OFFSETS) {
+            const V4<C> D = tb.pd(q);
             c.d[a] = pa + D.x;
             c.d[b] = pb + D.y;
         } else {
@@ -83,7 +153,7 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const C* __restrict__ tb, con
             c.d[b] = pb;
         }
     }
-    const C invJ = tb[T::INVJ];
+    const C invJ = tb.s(T::INVJ);
     c.drho = Sd * invJ;
     c.rho = k.rho0 + c.drho;
     c.irho = C(1) / c.rho;
@@ -107,21 +177,21 @@ struct GlobalLoad {
 
 // The force of Eq. 15 re-evaluated with the newest N'(q, t) (own-row
 // deviations out[]) for one fixed-point pass of the implicit relation.
-template <int Q, typename C>
-__device__ __forceinline__ void force_again(const C* __restrict__ tb, const C (&out)[Q],
-                                            const Consts<C>& k, Cell<Q, C>& c) {
+template <int Q, typename C, typename TB>
+__device__ __forceinline__ void force_again(const TB& tb, const C (&out)[Q], const Consts<C>& k,
+                                            Cell<Q, C>& c) {
     using T = Tab<Q>;
     using L = Lat<Q>;
-    C f1 = tb[T::FI1], f2 = tb[T::FI2];
+    C f1 = tb.s(T::FI1), f2 = tb.s(T::FI2);
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
-        const V4<C> A = ld4(tb + T::pa(q));
+        const V4<C> A = tb.pa(q);
         const C ta = out[a] + c.d[b], tbv = out[b] + c.d[a];
         f1 += A.x * ta + A.z * tbv;
         f2 += A.y * ta + A.w * tbv;
     }
-    const C invJ = tb[T::INVJ];
+    const C invJ = tb.s(T::INVJ);
     c.F1 = -C(0.5) * invJ * f1 + c.rho * k.g1;
     c.F2 = -C(0.5) * invJ * f2 + c.rho * k.g2;
 }
@@ -129,9 +199,9 @@ __device__ __forceinline__ void force_again(const C* __restrict__ tb, const C (&
 // Ut (Eq. 18), equilibrium coefficients (Eq. 19), odd parts, the momentum-flux
 // correction (Eq. 16, symmetric part), source (Eq. 17) and BGK (Eqs. 6, 11).
 // emit(alpha, value) receives every new post-collision deviation.
-template <int Q, typename C, typename Emit>
-__device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C>& c,
-                                             const Consts<C>& k, Emit&& emit) {
+template <int Q, typename C, typename TB, typename Emit>
+__device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const Consts<C>& k,
+                                             Emit&& emit) {
     using L = Lat<Q>;
     using T = Tab<Q>;
     constexpr C T0 = C(L::T0);
@@ -143,7 +213,7 @@ __device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C
     const C Ut2 = U2 + C(0.5) * c.F2 * c.irho;
     c.Ut1 = Ut1;
     c.Ut2 = Ut2;
-    const C gi11 = tb[T::G11], gi12 = tb[T::G12], gi22 = tb[T::G22];
+    const C gi11 = tb.s(T::G11), gi12 = tb.s(T::G12), gi22 = tb.s(T::G22);
     // Third-order Hermite coefficients C^{ijk} of Eq. 19 (symmetric).
     const C C111 = T0 * (C(3) * gi11 * Ut1 - C(3) * U1) + Ut1 * Ut1 * Ut1;
     const C C112 = T0 * (gi11 * Ut2 + C(2) * gi12 * Ut1 - U2) + Ut1 * Ut1 * Ut2;
@@ -166,7 +236,7 @@ __device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C
         const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
         O[q] = K11 * c1 + K12 * c2 + K111 * (c1 * c1 * c1) + K112 * (c1 * c1 * c2) +
                K122 * (c1 * c2 * c2) + K222 * (c2 * c2 * c2);
-        const V4<C> B = ld4(tb + T::pb(q));
+        const V4<C> B = tb.pb(q);
         S11 += B.y * O[q];
         S22 += B.z * O[q];
         S12 += B.w * O[q];
@@ -176,7 +246,7 @@ __device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C
     S22 *= pr;
     S12 *= pr;
     const C trS = S11 + S22;
-    const C J = tb[T::J];
+    const C J = tb.s(T::J);
     const C omt = k.omt;
     const C drt = c.drho * k.tau_inv, rt = c.rho * k.tau_inv;
     const C Fa = c.F1 * iT0, Fb = c.F2 * iT0;
@@ -184,12 +254,12 @@ __device__ __forceinline__ void collide_emit(const C* __restrict__ tb, Cell<Q, C
     const C Ea = rt * dK11 + S11 * (iT0 * iT0);
     const C Eb = rt * dK12 + C(2) * S12 * (iT0 * iT0);
     const C Ec = rt * dK22 + S22 * (iT0 * iT0);
-    emit(0, c.d[0] * omt + J * C(L::w(0)) * (drt * tb[T::P00] + base));
+    emit(0, c.d[0] * omt + J * C(L::w(0)) * (drt * tb.s(T::P00) + base));
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
-        const C X = drt * tb[T::pb(q)] + base + Ea * (c1 * c1) + Eb * (c1 * c2) + Ec * (c2 * c2);
+        const C X = drt * tb.p0(q) + base + Ea * (c1 * c1) + Eb * (c1 * c2) + Ec * (c2 * c2);
         const C Y = rt * O[q] + Fa * c1 + Fb * c2;
         const C Jw = J * C(L::w(a));
         emit(a, c.d[a] * omt + Jw * (X + Y));
@@ -228,14 +298,15 @@ __device__ __forceinline__ void residual_terms(const Cell<Q, C>& c, const double
     v[8] += (c.rho > C(0) && isfinite(c.rho) && isfinite(uu)) ? 0.0 : 1.0;
 }
 
-// Reference N of direction a at 1-based row r (FP64 geometry table); rows
-// beyond a wall are the mirror image of the row inside, which flips c^1.
+// Reference N of direction a at 1-based row r and geometry column jc (FP64
+// geometry table of ncol columns); rows beyond a wall are the mirror image
+// of the row inside, which flips c^1.
 template <int Q>
-__device__ __forceinline__ double ref_at(const double* geo, int n1, int a, int r) {
+__device__ __forceinline__ double ref_at(const double* geo, int n1, int ncol, int a, int r, int jc) {
     int m = r, b = a;
     if (r < 1) { m = 1 - r; b = hat_of(a); }
     else if (r > n1) { m = 2 * n1 + 1 - r; b = hat_of(a); }
-    return geo[(size_t)(m - 1) * Geo::stride(Q) + Geo::ref(Q, b)];
+    return geo[((size_t)(m - 1) * ncol + jc) * Geo::stride(Q) + Geo::ref(Q, b)];
 }
 
 // The periodic copies of interior column j (0..n2-1) in the ghost columns
@@ -296,6 +367,7 @@ struct EdgeFill {
     int ld, n1, n2, bc_lo, bc_hi;
     C U0_lo, U0_hi;
     bool own_wrap;
+    int gcols;               // ghost-table columns: 1 (planar, polar) or n2 (general)
 
     __device__ static __forceinline__ bool needed(int i, int n1, int n2) {
         return i < Lat<Q>::H || i >= n1 - Lat<Q>::H || n2 < 2 * GC;
@@ -311,7 +383,7 @@ struct EdgeFill {
                 const int k = i + 1;
                 const int a = bc_lo == 0 ? opp_of(b) : hat_of(b);
                 if (c1_of(a) >= k) {
-                    const double* gt = ghost + 2 * ((k - 1) * Q + a);
+                    const double* gt = ghost + 2 * (((k - 1) * Q + a) * gcols + (gcols > 1 ? j : 0));
                     store_periodic<S, C>(st + a * plane + (long long)(H - k) * ld, j, n2,
                                          ghost_value<C>(v, gt, rho, U0_lo, ut2));
                 }
@@ -320,7 +392,7 @@ struct EdgeFill {
                 const int k = n1 - i;
                 const int a = bc_hi == 0 ? opp_of(b) : hat_of(b);
                 if (c1_of(a) <= -k) {
-                    const double* gt = ghost + 2 * ((H + k - 1) * Q + a);
+                    const double* gt = ghost + 2 * (((H + k - 1) * Q + a) * gcols + (gcols > 1 ? j : 0));
                     store_periodic<S, C>(st + a * plane + (long long)(n1 + H + k - 1) * ld, j, n2,
                                          ghost_value<C>(v, gt, rho, U0_hi, ut2));
                 }

@@ -91,6 +91,7 @@ struct StepArgs {
     long long plane;        // elements per population plane = (n1+2h)*ld
     double tau, rho0, g1, g2, U0_lo, U0_hi;
     int bc_lo, bc_hi;
+    int ncol;               // geometry / ghost-table columns: 1 (planar, polar) or n2 (general)
     int iters;              // extra passes of the implicit force
     int* err;               // device error word (bounded waits that gave up)
 };
@@ -104,6 +105,7 @@ struct MomArgs {
     int n1, n2, ld, h;
     long long plane;
     double tau, rho0, g1, g2;
+    int ncol;               // 1 (planar, polar) or n2 (general grids: per-cell tables)
     // outputs (device, [n1][n2] FP64, may be null)
     double *rho, *U1, *U2, *Ut1, *Ut2, *F1, *F2;
     // residual mode
@@ -115,30 +117,35 @@ struct MomArgs {
 constexpr int NRED = 10;  // reduced quantities per block
 
 // Launchers (defined in the .cu files); all asynchronous on `stream`.
-void launch_geometry(int Q, const double* pos, int n1, double dx, int polar,
+// Geometry of n1 rows x ncol columns (ncol = 1: one column serves the row;
+// ncol = n2: general grids), reference states of `count` geometry entries,
+// and the coefficient + ghost tables (row tables, or per-cell tables when
+// ncol > 1).
+void launch_geometry(int Q, const double* pos, int n1, int ncol, double dx, int moments,
                      double* geo, cudaStream_t stream);
-void launch_reference(int Q, double* geo, int n1, double rho0, cudaStream_t stream);
-void launch_tables(int Q, int prec, const double* geo, void* tab, double* ghost, int n1,
-                   double tau, int bc_lo, int bc_hi, cudaStream_t stream);
+void launch_reference(int Q, double* geo, int count, double rho0, cudaStream_t stream);
+void launch_tables(int Q, int prec, const double* geo, void* tab, double* ghost, int n1, int n2,
+                   int ncol, int bc_lo, int bc_hi, cudaStream_t stream);
 void launch_boundary(int Q, int prec, const StepArgs& a, void* state, cudaStream_t stream);
 void launch_step(int Q, int prec, const StepArgs& a, cudaStream_t stream);
 void launch_moments(int Q, int prec, const MomArgs& a, int iters, int reduce,
                     cudaStream_t stream);
 int moments_blocks(int n1, int n2);
 void launch_reduce_final(const double* partial, int nblocks, double* out, cudaStream_t stream);
+// ncol: geometry columns, 1 (planar, polar) or n2 (general grids).
 void launch_state_from_fp64(int Q, int prec, const double* Np, const double* geo, void* state,
-                            int n1, int n2, int ld, int h, cudaStream_t stream);
+                            int n1, int n2, int ld, int h, int ncol, cudaStream_t stream);
 void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo, double* Np,
-                          int n1, int n2, int ld, int h, cudaStream_t stream);
+                          int n1, int n2, int ld, int h, int ncol, cudaStream_t stream);
+// rho_nf: no-flow density per row (ncol = 1) or per cell (ncol = n2).
 void launch_wall_copy(int prec, void* wall_rho, void* wall_ut2, const double* src_rho,
-                      const double* src_ut2, const double* rho_nf_row, int n1, int n2, int h,
-                      double rho0, cudaStream_t stream);
+                      const double* src_ut2, const double* rho_nf, int n1, int n2, int h,
+                      double rho0, int ncol, cudaStream_t stream);
 void launch_wall_init(int prec, void* wall_rho, void* wall_ut2, const double* rho,
                       const double* ut2, int n1, int n2, int h, double rho0, cudaStream_t stream);
-void launch_scale_volume(int Q, double* geo, const double* rho_nf_row, int n1, double rho0,
+// Eq. 23 on `count` geometry entries (rows, or cells of a general grid).
+void launch_scale_volume(int Q, double* geo, const double* rho_nf, int count, double rho0,
                          cudaStream_t stream);
-void launch_rescale_wall(int prec, void* wall_rho, const double* rho_nf_row, int n1, int n2,
-                         int h, double rho0, cudaStream_t stream);
 void launch_row_mean(const double* field, int n1, int n2, double* out, cudaStream_t stream);
 
 // TMA-staged fused update (k_step_tma.cu): tensor maps of the two state

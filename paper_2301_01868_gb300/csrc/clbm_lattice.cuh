@@ -94,6 +94,18 @@ template <int Q> struct Tab {
     __host__ __device__ static constexpr int pd(int p) { return PB + 12 * p + 8; }
 };
 
+// Per-cell table of a general grid, one plane of n1 n2 values per entry:
+// the Tab<Q> header values INVJ .. M2 at the same indices, then per pair the
+// contractions (a^1_a, a^2_a, a^1_b, a^2_b) and the pull offsets
+// (Delta_a, Delta_b); P0 and the dPi weights are formed when read.
+template <int Q>
+struct CellTabLayout {
+    static constexpr int NS = Tab<Q>::M2 + 1;                   // header values
+    __host__ __device__ static constexpr int pa(int q) { return NS + 6 * q; }
+    __host__ __device__ static constexpr int pd(int q) { return NS + 6 * q + 4; }
+    static constexpr int S = NS + 6 * Lat<Q>::NP;               // entries per cell
+};
+
 // Four table values read with one vector load.
 template <typename C> struct V4 { C x, y, z, w; };
 __device__ __forceinline__ V4<float> ld4(const float* p) {

@@ -27,7 +27,7 @@ template <int Q, typename S, typename C, bool ITER>
 __device__ __forceinline__ void batch_cell(const BatchGrid& g, int src, int i, int j) {
     using T = Tab<Q>;
     constexpr int H = Lat<Q>::H;
-    const C* __restrict__ tb = (const C*)g.tab + (size_t)i * T::S;
+    const RowTab<Q, C> tb{(const C*)g.tab + (size_t)i * T::S};
     const Consts<C> k = Consts<C>::make(g.k);
     const long long off = (long long)(i + H) * g.ld + j + GC;
     Cell<Q, C> c;
@@ -52,7 +52,7 @@ __device__ __forceinline__ void batch_cell(const BatchGrid& g, int src, int i, i
     }
     if (EdgeFill<Q, S>::needed(i, g.n1, g.n2)) {
         const EdgeFill<Q, S> ef{(S*)g.phys[src ^ 1], g.ghost, g.plane, g.ld, g.n1, g.n2, g.bc_lo,
-                                g.bc_hi, C(g.U0_lo), C(g.U0_hi), g.n2 < 2 * GC};
+                                g.bc_hi, C(g.U0_lo), C(g.U0_hi), g.n2 < 2 * GC, 1};
         ef.fill(i, j, dst, g.plane, c.rho, c.Ut2);
     }
     if (i < H) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_batch_moments(const Batch
 #pragma unroll
         for (int q = 0; q < NRED; ++q) v[q] = 0.0;
         if (j < g.n2) {
-            const C* tb = (const C*)g.tab + (size_t)i * T::S;
+            const RowTab<Q, C> tb{(const C*)g.tab + (size_t)i * T::S};
             const Consts<C> kc = Consts<C>::make(g.k);
             const long long off = (long long)(i + H) * g.ld + j + GC;
             const S* p = (const S*)g.phys[src] + off;

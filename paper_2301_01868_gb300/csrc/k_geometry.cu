@@ -1,22 +1,25 @@
 // k_geometry.cu -- geometry / metric / Christoffel precompute (Sec. 2,
-// Eqs. 1-5) and the per-row coefficient tables of the fused update.
+// Eqs. 1-5) and the coefficient tables of the fused update.
 //
 // Planar and polar grids are invariant under a shift along q^2 (translation,
 // rotation), so every quantity is evaluated once per row, at column 1, from
-// the node positions around it; a state that does not depend on j then stays
-// exactly independent of j under the update, as in the paper's runs.
+// the node positions around it (ncol = 1); a state that does not depend on j
+// then stays exactly independent of j under the update, as in the paper's
+// runs.  General grids evaluate every cell (ncol = n2) from the node
+// positions the caller supplies, ghosts included.
 #include "clbm_cell.cuh"
 
 namespace clbm {
 
 namespace {
 
-// Node positions (n1+8) x 9 columns: rows i = -3..n1+4, columns j = -3..5
+// Node positions (n1+8) x (ncol+8): rows i = -3..n1+4, columns j = -3..ncol+4
 // (1-based), x and y interleaved.
 struct Pos {
     const double* p;
+    int ncp;                // ncol + 8
     __device__ double2 at(int i, int j) const {
-        const double* q = p + (((size_t)(i + 3) * 9 + (size_t)(j + 3)) * 2);
+        const double* q = p + (((size_t)(i + 3) * ncp + (size_t)(j + 3)) * 2);
         return make_double2(q[0], q[1]);
     }
 };
@@ -31,18 +34,21 @@ __device__ double2 tangent(const Pos& P, int m, int i, int j, double dx) {
     return make_double2((dp.x - dm.x) / (2.0 * dx), (dp.y - dm.y) / (2.0 * dx));
 }
 
+// One thread per (row, geometry column); moments: the angular momentum
+// weights x cross g_k (about the origin) unless planar.
 template <int Q>
-__global__ void k_geometry(const double* __restrict__ pos, int n1, double dx, int polar,
+__global__ void k_geometry(const double* __restrict__ pos, int n1, int ncol, double dx, int moments,
                            double* __restrict__ geo) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jc = blockIdx.y;
     if (r >= n1) return;
-    const int i = r + 1;  // 1-based row
-    Pos P{pos};
-    double2 g1 = tangent(P, 0, i, 1, dx), g2 = tangent(P, 1, i, 1, dx);
+    const int i = r + 1, j = jc + 1;  // 1-based node
+    Pos P{pos, ncol + 8};
+    double2 g1 = tangent(P, 0, i, j, dx), g2 = tangent(P, 1, i, j, dx);
     double J = g1.x * g2.y - g1.y * g2.x;                       // Eq. 2, g_3 = z
     double2 G1 = make_double2(g2.y / J, -g2.x / J);             // Eq. 3
     double2 G2 = make_double2(-g1.y / J, g1.x / J);
-    double* o = geo + (size_t)r * Geo::stride(Q);
+    double* o = geo + ((size_t)r * ncol + jc) * Geo::stride(Q);
     o[Geo::J] = J;
     o[Geo::JGEO] = J;
     o[Geo::GI11] = G1.x * G1.x + G1.y * G1.y;
@@ -51,9 +57,9 @@ __global__ void k_geometry(const double* __restrict__ pos, int n1, double dx, in
     o[Geo::G11] = g1.x * g1.x + g1.y * g1.y;
     o[Geo::G12] = g1.x * g2.x + g1.y * g2.y;
     o[Geo::G22] = g2.x * g2.x + g2.y * g2.y;
-    double2 x = P.at(i, 1);
-    o[Geo::M1] = polar ? (x.x * g1.y - x.y * g1.x) : 0.0;
-    o[Geo::M2] = polar ? (x.x * g2.y - x.y * g2.x) : 0.0;
+    double2 x = P.at(i, j);
+    o[Geo::M1] = moments ? (x.x * g1.y - x.y * g1.x) : 0.0;
+    o[Geo::M2] = moments ? (x.x * g2.y - x.y * g2.x) : 0.0;
     o[Geo::G2N] = sqrt(o[Geo::G22]);
     o[Geo::R] = sqrt(x.x * x.x + x.y * x.y);
 #pragma unroll
@@ -63,8 +69,8 @@ __global__ void k_geometry(const double* __restrict__ pos, int n1, double dx, in
         if (a != 0) {
             // Eq. 5: Theta^k_m(q + c, q) = [g_m(q + c) - g_m(q)] . g^k(q),
             // contracted with c^m.
-            double2 h1 = tangent(P, 0, i + c1, 1 + c2, dx);
-            double2 h2 = tangent(P, 1, i + c1, 1 + c2, dx);
+            double2 h1 = tangent(P, 0, i + c1, j + c2, dx);
+            double2 h2 = tangent(P, 1, i + c1, j + c2, dx);
             double2 d1 = make_double2(h1.x - g1.x, h1.y - g1.y);
             double2 d2 = make_double2(h2.x - g2.x, h2.y - g2.y);
             double t11 = d1.x * G1.x + d1.y * G1.y, t12 = d2.x * G1.x + d2.y * G1.y;
@@ -88,9 +94,9 @@ __host__ __device__ double rest_poly(int a, double gi11, double gi12, double gi2
 }
 
 template <int Q>
-__global__ void k_reference(double* __restrict__ geo, int n1, double rho0) {
+__global__ void k_reference(double* __restrict__ geo, int count, double rho0) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n1) return;
+    if (r >= count) return;
     double* o = geo + (size_t)r * Geo::stride(Q);
 #pragma unroll
     for (int a = 0; a < Q; ++a)
@@ -119,7 +125,7 @@ __global__ void k_tables(const double* __restrict__ geo, C* __restrict__ tab, in
     double D0 = 0.0, M1 = 0.0, M2 = 0.0;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        dl[a] = ref_at<Q>(geo, n1, a, i - c1_of(a)) - g[Geo::ref(Q, a)];
+        dl[a] = ref_at<Q>(geo, n1, 1, a, i - c1_of(a), 0) - g[Geo::ref(Q, a)];
         D0 += dl[a];
         M1 += c1_of(a) * dl[a];
         M2 += c2_of(a) * dl[a];
@@ -166,57 +172,132 @@ __global__ void k_tables(const double* __restrict__ geo, C* __restrict__ tab, in
     }
 }
 
-// Ghost table [wall][k-1][alpha] x {offset, coefficient}: the stored ghost
-// value of direction a at depth k is sigma_b(m) + offset + coefficient * rho
-// (U0 - Ut^2) with b = a* (no-slip) or a-hat (moving wall) and m the mirrored
-// row; the offset converts between the two rows' references.
+// Per-cell tables of general grids (CellTabLayout, one plane per entry): the
+// header values and, per +/- pair, the contractions a^k and the pull offsets,
+// with Delta_a = ref_a(source cell) - ref_a(cell), the source cell being
+// (i - c1, j - c2) with j periodic and rows beyond a wall mirrored.
+template <int Q, typename C>
+__global__ void k_tables_cell(const double* __restrict__ geo, C* __restrict__ tab, int n1, int n2) {
+    using T = Tab<Q>;
+    using L = CellTabLayout<Q>;
+    const int jc = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (jc >= n2) return;
+    const int i = r + 1;
+    const size_t st = (size_t)n1 * n2, m = (size_t)r * n2 + jc;
+    const double* g = geo + m * Geo::stride(Q);
+    auto put = [&](int k, double v) { tab[(size_t)k * st + m] = C(v); };
+    const double J = g[Geo::J];
+    put(T::INVJ, 1.0 / J);
+    put(T::J, J);
+    put(T::G11, g[Geo::GI11]);
+    put(T::G12, g[Geo::GI12]);
+    put(T::G22, g[Geo::GI22]);
+    put(T::P00, rest_poly<Q>(0, g[Geo::GI11], g[Geo::GI12], g[Geo::GI22]));
+    double dl[Q];
+    double D0 = 0.0, M1 = 0.0, M2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        int js = (jc - c2_of(a)) % n2;
+        if (js < 0) js += n2;
+        dl[a] = ref_at<Q>(geo, n1, n2, a, i - c1_of(a), js) - g[Geo::ref(Q, a)];
+        D0 += dl[a];
+        M1 += c1_of(a) * dl[a];
+        M2 += c2_of(a) * dl[a];
+    }
+    put(T::D0, D0);
+    put(T::M1, M1);
+    put(T::M2, M2);
+    double F01 = 0.0, F02 = 0.0, FI1 = 0.0, FI2 = 0.0;
+#pragma unroll
+    for (int b = 1; b < Q; ++b) {
+        const int ob = opp_of(b);
+        const double ab1 = g[Geo::a1(b)], ab2 = g[Geo::a2(b)];
+        const double own = g[Geo::ref(Q, b)];
+        const double in = g[Geo::ref(Q, ob)] + dl[ob];
+        F01 += ab1 * (own + in);
+        F02 += ab2 * (own + in);
+        FI1 += ab1 * (own + in - dl[ob]);
+        FI2 += ab2 * (own + in - dl[ob]);
+    }
+    put(T::F01, F01);
+    put(T::F02, F02);
+    put(T::FI1, FI1);
+    put(T::FI2, FI2);
+#pragma unroll
+    for (int p = 0; p < Lat<Q>::NP; ++p) {
+        const int a = Lat<Q>::plus(p), ab = opp_of(a);
+        put(L::pa(p) + 0, g[Geo::a1(a)]);
+        put(L::pa(p) + 1, g[Geo::a2(a)]);
+        put(L::pa(p) + 2, g[Geo::a1(ab)]);
+        put(L::pa(p) + 3, g[Geo::a2(ab)]);
+        put(L::pd(p) + 0, dl[a]);
+        put(L::pd(p) + 1, dl[ab]);
+    }
+}
+
+// Ghost table [wall][k-1][alpha][column] x {offset, coefficient} (one column
+// unless the grid is general): the stored ghost value of direction a at
+// depth k is sigma_b(m) + offset + coefficient * rho (U0 - Ut^2) with
+// b = a* (no-slip) or a-hat (moving wall) and m the mirrored row of the same
+// column; the offset converts between the two cells' references.
 template <int Q>
-__global__ void k_ghost(const double* __restrict__ geo, double* __restrict__ ghost, int n1,
+__global__ void k_ghost(const double* __restrict__ geo, double* __restrict__ ghost, int n1, int ncol,
                         int bc_lo, int bc_hi) {
     constexpr int H = Lat<Q>::H;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * H * Q) return;
-    const int wall = t / (H * Q), k = (t / Q) % H + 1, a = t % Q;
+    if (t >= 2 * H * Q * ncol) return;
+    const int jc = t % ncol, u = t / ncol;
+    const int wall = u / (H * Q), k = (u / Q) % H + 1, a = u % Q;
     const int bc = wall == 0 ? bc_lo : bc_hi;
     const int b = bc == 0 ? opp_of(a) : hat_of(a);
     const int gr = wall == 0 ? 1 - k : n1 + k;          // ghost row (1-based)
     const int m = wall == 0 ? k : n1 + 1 - k;           // mirrored fluid row
-    const double off = ref_at<Q>(geo, n1, b, m) - ref_at<Q>(geo, n1, a, gr);
+    const double off = ref_at<Q>(geo, n1, ncol, b, m, jc) - ref_at<Q>(geo, n1, ncol, a, gr, jc);
     double coef = 0.0;
     if (bc == 1)  // App. B moving wall, reading (2/T0) w J rho c^2 (U0^2 - Ut^2)
-        coef = 2.0 / Lat<Q>::T0 * Lat<Q>::w(b) * geo[(size_t)(m - 1) * Geo::stride(Q) + Geo::J] *
-               c2_of(b);
+        coef = 2.0 / Lat<Q>::T0 * Lat<Q>::w(b) *
+               geo[((size_t)(m - 1) * ncol + jc) * Geo::stride(Q) + Geo::J] * c2_of(b);
     ghost[2 * t] = off;
     ghost[2 * t + 1] = coef;
 }
 
 }  // namespace
 
-void launch_geometry(int Q, const double* pos, int n1, double dx, int polar, double* geo,
+void launch_geometry(int Q, const double* pos, int n1, int ncol, double dx, int moments, double* geo,
                      cudaStream_t s) {
-    dim3 b(128), g((n1 + 127) / 128);
-    if (Q == 9) k_geometry<9><<<g, b, 0, s>>>(pos, n1, dx, polar, geo);
-    else k_geometry<21><<<g, b, 0, s>>>(pos, n1, dx, polar, geo);
+    dim3 b(128), g((n1 + 127) / 128, ncol);
+    if (Q == 9) k_geometry<9><<<g, b, 0, s>>>(pos, n1, ncol, dx, moments, geo);
+    else k_geometry<21><<<g, b, 0, s>>>(pos, n1, ncol, dx, moments, geo);
 }
 
-void launch_reference(int Q, double* geo, int n1, double rho0, cudaStream_t s) {
-    dim3 b(128), g((n1 + 127) / 128);
-    if (Q == 9) k_reference<9><<<g, b, 0, s>>>(geo, n1, rho0);
-    else k_reference<21><<<g, b, 0, s>>>(geo, n1, rho0);
+void launch_reference(int Q, double* geo, int count, double rho0, cudaStream_t s) {
+    dim3 b(128), g((count + 127) / 128);
+    if (Q == 9) k_reference<9><<<g, b, 0, s>>>(geo, count, rho0);
+    else k_reference<21><<<g, b, 0, s>>>(geo, count, rho0);
 }
 
-void launch_tables(int Q, int prec, const double* geo, void* tab, double* ghost, int n1,
-                   double, int bc_lo, int bc_hi, cudaStream_t s) {
-    dim3 b(128), g((n1 + 127) / 128);
-    if (Q == 9) {
-        if (prec == 0) k_tables<9, double><<<g, b, 0, s>>>(geo, (double*)tab, n1);
-        else k_tables<9, float><<<g, b, 0, s>>>(geo, (float*)tab, n1);
-        k_ghost<9><<<1, 2 * 1 * 9, 0, s>>>(geo, ghost, n1, bc_lo, bc_hi);
+template <int Q>
+static void tables(int prec, const double* geo, void* tab, double* ghost, int n1, int n2, int ncol,
+                   int bc_lo, int bc_hi, cudaStream_t s) {
+    constexpr int H = Lat<Q>::H;
+    if (ncol > 1) {
+        dim3 b(128), g((n2 + 127) / 128, n1);
+        if (prec == 0) k_tables_cell<Q, double><<<g, b, 0, s>>>(geo, (double*)tab, n1, n2);
+        else k_tables_cell<Q, float><<<g, b, 0, s>>>(geo, (float*)tab, n1, n2);
     } else {
-        if (prec == 0) k_tables<21, double><<<g, b, 0, s>>>(geo, (double*)tab, n1);
-        else k_tables<21, float><<<g, b, 0, s>>>(geo, (float*)tab, n1);
-        k_ghost<21><<<1, 2 * 3 * 21, 0, s>>>(geo, ghost, n1, bc_lo, bc_hi);
+        dim3 b(128), g((n1 + 127) / 128);
+        if (prec == 0) k_tables<Q, double><<<g, b, 0, s>>>(geo, (double*)tab, n1);
+        else k_tables<Q, float><<<g, b, 0, s>>>(geo, (float*)tab, n1);
     }
+    const int nt = 2 * H * Q * ncol;
+    k_ghost<Q><<<(nt + 127) / 128, 128, 0, s>>>(geo, ghost, n1, ncol, bc_lo, bc_hi);
+}
+
+void launch_tables(int Q, int prec, const double* geo, void* tab, double* ghost, int n1, int n2,
+                   int ncol, int bc_lo, int bc_hi, cudaStream_t s) {
+    if (Q == 9) tables<9>(prec, geo, tab, ghost, n1, n2, ncol, bc_lo, bc_hi, s);
+    else tables<21>(prec, geo, tab, ghost, n1, n2, ncol, bc_lo, bc_hi, s);
 }
 
 }  // namespace clbm

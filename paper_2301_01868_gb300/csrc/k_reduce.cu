@@ -9,8 +9,6 @@ namespace {
 
 constexpr int RB = 128;  // threads per block of the diagnostics kernels
 
-// Persistent blocks of the residual reduction: enough to fill the GPU, never
-// more than there are (row, 128-column) items.
 // One block per (row, 128-column) item up to 65536 blocks: enough loads in
 // flight to stream the state (fewer, longer-lived blocks left the diagnostics
 // latency-bound).
@@ -19,12 +17,16 @@ int residual_blocks(int n1, int n2) {
     return items < 65536 ? items : 65536;
 }
 
-template <int Q, typename S, typename C, bool ITER>
+// Geometry row / cell of cell (i, j).
+__device__ __forceinline__ const double* geo_of(const double* geo, int Q, int ncol, int i, int j) {
+    return geo + ((size_t)i * ncol + (ncol > 1 ? j : 0)) * Geo::stride(Q);
+}
+
+template <int Q, typename S, typename C, bool ITER, bool GEN>
 __device__ __forceinline__ void cell_moments(const MomArgs& a, int iters, int i, int j,
                                              Cell<Q, C>& c) {
-    using T = Tab<Q>;
     constexpr int H = Lat<Q>::H;
-    const C* tb = (const C*)a.tab + (size_t)i * T::S;
+    const auto tb = TabOf<Q, C, GEN>::at(a.tab, i, j, a.n1, a.n2);
     const Consts<C> kc = Consts<C>::make(a.k);
     const long long off = (long long)(i + H) * a.ld + j + GC;
     pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld}, tb, kc, c);
@@ -41,13 +43,13 @@ __device__ __forceinline__ void cell_moments(const MomArgs& a, int iters, int i,
 }
 
 // Field output of the moments: one thread per cell.
-template <int Q, typename S, typename C, bool ITER>
+template <int Q, typename S, typename C, bool ITER, bool GEN>
 __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= a.n2) return;
     Cell<Q, C> c;
-    cell_moments<Q, S, C, ITER>(a, iters, i, j, c);
+    cell_moments<Q, S, C, ITER, GEN>(a, iters, i, j, c);
     const size_t m = (size_t)i * a.n2 + j;
     if (a.rho) a.rho[m] = double(c.rho);
     if (a.U1) a.U1[m] = double(c.U1);
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters) {
 // block, so repeated runs give identical bits.  The rest parts of the totals
 // are exact per row: sum_a ref_a(i) = J rho0 and sum_a c_a ref_a(i) = 0.
 // The largest |u| is tracked as the largest |u|^2 and rooted once per block.
-template <int Q, typename S, typename C, bool ITER>
+template <int Q, typename S, typename C, bool ITER, bool GEN>
 __global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, int iters) {
     const int bx = (a.n2 + RB - 1) / RB;
     const int items = a.n1 * bx;
@@ -75,9 +77,9 @@ __global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, 
         const int i = it / bx, j = (it % bx) * RB + threadIdx.x;
         if (j >= a.n2) continue;
         Cell<Q, C> c;
-        cell_moments<Q, S, C, ITER>(a, iters, i, j, c);
+        cell_moments<Q, S, C, ITER, GEN>(a, iters, i, j, c);
         const size_t m = (size_t)i * a.n2 + j;
-        residual_terms<Q, C>(c, a.geo + (size_t)i * Geo::stride(Q), a.k.rho0, a.ut_prev + m,
+        residual_terms<Q, C>(c, geo_of(a.geo, Q, a.ncol, i, j), a.k.rho0, a.ut_prev + m,
                              a.ut_prev + nc + m, a.have_prev != 0, v);
     }
 #pragma unroll
@@ -103,41 +105,41 @@ __global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_reduce_final(const double* __restrict__ partial,
-                                                      int nblocks, double* __restrict__ out) {
-    __shared__ double sh[256];
-    for (int k = 0; k < NRED; ++k) {
-        double x = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += 256) {
-            const double y = partial[(size_t)b * NRED + k];
-            x = (k == 7) ? fmax(x, y) : x + y;
-        }
-        sh[threadIdx.x] = x;
-        __syncthreads();
-        for (int st = 128; st > 0; st >>= 1) {
-            if (threadIdx.x < st)
-                sh[threadIdx.x] = (k == 7) ? fmax(sh[threadIdx.x], sh[threadIdx.x + st])
-                                           : sh[threadIdx.x] + sh[threadIdx.x + st];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[k] = sh[0];
+// Final reduction: block k reduces quantity k over all block partials, each
+// thread a fixed strided subset, then a fixed tree (repeatable bits).
+__global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict__ partial,
+                                                       int nblocks, double* __restrict__ out) {
+    __shared__ double sh[1024];
+    const int k = blockIdx.x;
+    double x = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 1024) {
+        const double y = partial[(size_t)b * NRED + k];
+        x = (k == 7) ? fmax(x, y) : x + y;
+    }
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int st = 512; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            sh[threadIdx.x] = (k == 7) ? fmax(sh[threadIdx.x], sh[threadIdx.x + st])
+                                       : sh[threadIdx.x] + sh[threadIdx.x + st];
         __syncthreads();
     }
+    if (threadIdx.x == 0) out[k] = sh[0];
 }
 
 template <int Q, typename S>
 __global__ void k_from_fp64(const double* __restrict__ Np, const double* __restrict__ geo,
-                            S* __restrict__ st, int n1, int n2, int ld, int h) {
+                            S* __restrict__ st, int n1, int n2, int ld, int h, int ncol) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= n2) return;
     const long long P = (long long)(n1 + 2 * h) * ld;
+    const double* ge = geo_of(geo, Q, ncol, i, j);
 #pragma unroll
     for (int al = 0; al < Q; ++al) {
-        // Np == nullptr: the rest state N' = J f^eq(rho0, 0) of this row.
-        const double Nv = Np ? Np[((size_t)al * n1 + i) * n2 + j]
-                             : geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
-        const double v = Nv - geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
+        // Np == nullptr: the rest state N' = J f^eq(rho0, 0) of this cell.
+        const double Nv = Np ? Np[((size_t)al * n1 + i) * n2 + j] : ge[Geo::ref(Q, al)];
+        const double v = Nv - ge[Geo::ref(Q, al)];
         using CT = typename Store<S>::C;
         store_periodic<S, CT>(st + al * P + (long long)(i + h) * ld, j, n2, CT(v));
     }
@@ -145,15 +147,16 @@ __global__ void k_from_fp64(const double* __restrict__ Np, const double* __restr
 
 template <int Q, typename S>
 __global__ void k_to_fp64(const S* __restrict__ st, const double* __restrict__ geo,
-                          double* __restrict__ Np, int n1, int n2, int ld, int h) {
+                          double* __restrict__ Np, int n1, int n2, int ld, int h, int ncol) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= n2) return;
     const long long P = (long long)(n1 + 2 * h) * ld;
+    const double* ge = geo_of(geo, Q, ncol, i, j);
 #pragma unroll
     for (int al = 0; al < Q; ++al) {
         const double s = double(Store<S>::ld(st + al * P + (long long)(i + h) * ld + j + GC));
-        Np[((size_t)al * n1 + i) * n2 + j] = s + geo[(size_t)i * Geo::stride(Q) + Geo::ref(Q, al)];
+        Np[((size_t)al * n1 + i) * n2 + j] = s + ge[Geo::ref(Q, al)];
     }
 }
 
@@ -173,33 +176,24 @@ __global__ void k_wall_init(C* __restrict__ wr, C* __restrict__ wu, const double
 template <typename C>
 __global__ void k_wall_copy(C* __restrict__ wr, C* __restrict__ wu, const double* __restrict__ sr,
                             const double* __restrict__ su, const double* __restrict__ rnf, int n1,
-                            int n2, int h, double rho0) {
+                            int n2, int h, double rho0, int ncol) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int wk = blockIdx.y;
     if (j >= n2) return;
     const int wall = wk / h, k = wk % h + 1;
     const int row = wall == 0 ? k - 1 : n1 - k;
     const size_t m = (size_t)wk * n2 + j;
-    wr[m] = C(sr[m] * (rnf ? rho0 / rnf[row] : 1.0));
+    wr[m] = C(sr[m] * (rnf ? rho0 / rnf[(size_t)row * ncol + (ncol > 1 ? j : 0)] : 1.0));
     wu[m] = C(su[m]);
 }
 
-template <typename C>
-__global__ void k_rescale_wall(C* __restrict__ wr, const double* __restrict__ rnf, int n1, int n2,
-                               int h, double rho0) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int wk = blockIdx.y;
-    if (j >= n2) return;
-    const int wall = wk / h, k = wk % h + 1;
-    const int row = wall == 0 ? k - 1 : n1 - k;
-    wr[(size_t)wk * n2 + j] = C(double(wr[(size_t)wk * n2 + j]) * rho0 / rnf[row]);
-}
-
+// Eq. 23, J <- J rho_nf / rho0, for every geometry entry (rows, or cells of a
+// general grid) with its no-flow density rnf.
 __global__ void k_scale_volume(double* __restrict__ geo, int stride, const double* __restrict__ rnf,
-                               int n1, double rho0) {
+                               int count, double rho0) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n1) return;
-    geo[(size_t)r * stride + Geo::J] *= rnf[r] / rho0;  // Eq. 23
+    if (r >= count) return;
+    geo[(size_t)r * stride + Geo::J] *= rnf[r] / rho0;
 }
 
 __global__ void __launch_bounds__(256) k_row_mean(const double* __restrict__ f, int n2,
@@ -217,16 +211,23 @@ __global__ void __launch_bounds__(256) k_row_mean(const double* __restrict__ f, 
     if (threadIdx.x == 0) out[i] = sh[0] / n2;
 }
 
-template <int Q, typename S, typename C>
-void run_moments(const MomArgs& a, int iters, int reduce, cudaStream_t s) {
+template <int Q, typename S, typename C, bool GEN>
+void run_moments_g(const MomArgs& a, int iters, int reduce, cudaStream_t s) {
     if (reduce) {
-        if (iters > 0) k_residual<Q, S, C, true><<<residual_blocks(a.n1, a.n2), RB, 0, s>>>(a, iters);
-        else k_residual<Q, S, C, false><<<residual_blocks(a.n1, a.n2), RB, 0, s>>>(a, iters);
+        const int nb = residual_blocks(a.n1, a.n2);
+        if (iters > 0) k_residual<Q, S, C, true, GEN><<<nb, RB, 0, s>>>(a, iters);
+        else k_residual<Q, S, C, false, GEN><<<nb, RB, 0, s>>>(a, iters);
     } else {
         dim3 b(RB), g((a.n2 + RB - 1) / RB, a.n1);
-        if (iters > 0) k_moments<Q, S, C, true><<<g, b, 0, s>>>(a, iters);
-        else k_moments<Q, S, C, false><<<g, b, 0, s>>>(a, iters);
+        if (iters > 0) k_moments<Q, S, C, true, GEN><<<g, b, 0, s>>>(a, iters);
+        else k_moments<Q, S, C, false, GEN><<<g, b, 0, s>>>(a, iters);
     }
+}
+
+template <int Q, typename S, typename C>
+void run_moments(const MomArgs& a, int iters, int reduce, cudaStream_t s) {
+    if (a.ncol > 1) run_moments_g<Q, S, C, true>(a, iters, reduce, s);
+    else run_moments_g<Q, S, C, false>(a, iters, reduce, s);
 }
 
 }  // namespace
@@ -252,43 +253,43 @@ void launch_moments(int Q, int prec, const MomArgs& a, int iters, int reduce, cu
 }
 
 void launch_reduce_final(const double* partial, int nblocks, double* out, cudaStream_t s) {
-    k_reduce_final<<<1, 256, 0, s>>>(partial, nblocks, out);
+    k_reduce_final<<<NRED, 1024, 0, s>>>(partial, nblocks, out);
 }
 
 template <int Q>
 static void from64(int prec, const double* Np, const double* geo, void* st, int n1, int n2, int ld,
-                   int h, cudaStream_t s) {
+                   int h, int ncol, cudaStream_t s) {
     dim3 b(128), g((n2 + 127) / 128, n1);
     switch (prec) {
-        case 0: k_from_fp64<Q, double><<<g, b, 0, s>>>(Np, geo, (double*)st, n1, n2, ld, h); break;
-        case 1: k_from_fp64<Q, float><<<g, b, 0, s>>>(Np, geo, (float*)st, n1, n2, ld, h); break;
-        case 2: k_from_fp64<Q, __half><<<g, b, 0, s>>>(Np, geo, (__half*)st, n1, n2, ld, h); break;
-        default: k_from_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>(Np, geo, (__nv_bfloat16*)st, n1, n2, ld, h); break;
+        case 0: k_from_fp64<Q, double><<<g, b, 0, s>>>(Np, geo, (double*)st, n1, n2, ld, h, ncol); break;
+        case 1: k_from_fp64<Q, float><<<g, b, 0, s>>>(Np, geo, (float*)st, n1, n2, ld, h, ncol); break;
+        case 2: k_from_fp64<Q, __half><<<g, b, 0, s>>>(Np, geo, (__half*)st, n1, n2, ld, h, ncol); break;
+        default: k_from_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>(Np, geo, (__nv_bfloat16*)st, n1, n2, ld, h, ncol); break;
     }
 }
 
 template <int Q>
 static void to64(int prec, const void* st, const double* geo, double* Np, int n1, int n2, int ld,
-                 int h, cudaStream_t s) {
+                 int h, int ncol, cudaStream_t s) {
     dim3 b(128), g((n2 + 127) / 128, n1);
     switch (prec) {
-        case 0: k_to_fp64<Q, double><<<g, b, 0, s>>>((const double*)st, geo, Np, n1, n2, ld, h); break;
-        case 1: k_to_fp64<Q, float><<<g, b, 0, s>>>((const float*)st, geo, Np, n1, n2, ld, h); break;
-        case 2: k_to_fp64<Q, __half><<<g, b, 0, s>>>((const __half*)st, geo, Np, n1, n2, ld, h); break;
-        default: k_to_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>((const __nv_bfloat16*)st, geo, Np, n1, n2, ld, h); break;
+        case 0: k_to_fp64<Q, double><<<g, b, 0, s>>>((const double*)st, geo, Np, n1, n2, ld, h, ncol); break;
+        case 1: k_to_fp64<Q, float><<<g, b, 0, s>>>((const float*)st, geo, Np, n1, n2, ld, h, ncol); break;
+        case 2: k_to_fp64<Q, __half><<<g, b, 0, s>>>((const __half*)st, geo, Np, n1, n2, ld, h, ncol); break;
+        default: k_to_fp64<Q, __nv_bfloat16><<<g, b, 0, s>>>((const __nv_bfloat16*)st, geo, Np, n1, n2, ld, h, ncol); break;
     }
 }
 
 void launch_state_from_fp64(int Q, int prec, const double* Np, const double* geo, void* state,
-                            int n1, int n2, int ld, int h, cudaStream_t s) {
-    if (Q == 9) from64<9>(prec, Np, geo, state, n1, n2, ld, h, s);
-    else from64<21>(prec, Np, geo, state, n1, n2, ld, h, s);
+                            int n1, int n2, int ld, int h, int ncol, cudaStream_t s) {
+    if (Q == 9) from64<9>(prec, Np, geo, state, n1, n2, ld, h, ncol, s);
+    else from64<21>(prec, Np, geo, state, n1, n2, ld, h, ncol, s);
 }
 
 void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo, double* Np,
-                          int n1, int n2, int ld, int h, cudaStream_t s) {
-    if (Q == 9) to64<9>(prec, state, geo, Np, n1, n2, ld, h, s);
-    else to64<21>(prec, state, geo, Np, n1, n2, ld, h, s);
+                          int n1, int n2, int ld, int h, int ncol, cudaStream_t s) {
+    if (Q == 9) to64<9>(prec, state, geo, Np, n1, n2, ld, h, ncol, s);
+    else to64<21>(prec, state, geo, Np, n1, n2, ld, h, ncol, s);
 }
 
 void launch_wall_init(int prec, void* wr, void* wu, const double* rho, const double* ut2, int n1,
@@ -298,22 +299,15 @@ void launch_wall_init(int prec, void* wr, void* wu, const double* rho, const dou
     else k_wall_init<float><<<g, b, 0, s>>>((float*)wr, (float*)wu, rho, ut2, n1, n2, h, rho0);
 }
 
-void launch_rescale_wall(int prec, void* wr, const double* rnf, int n1, int n2, int h, double rho0,
-                         cudaStream_t s) {
-    dim3 b(128), g((n2 + 127) / 128, 2 * h);
-    if (prec == 0) k_rescale_wall<double><<<g, b, 0, s>>>((double*)wr, rnf, n1, n2, h, rho0);
-    else k_rescale_wall<float><<<g, b, 0, s>>>((float*)wr, rnf, n1, n2, h, rho0);
-}
-
 void launch_wall_copy(int prec, void* wr, void* wu, const double* sr, const double* su,
-                      const double* rnf, int n1, int n2, int h, double rho0, cudaStream_t s) {
+                      const double* rnf, int n1, int n2, int h, double rho0, int ncol, cudaStream_t s) {
     dim3 b(128), g((n2 + 127) / 128, 2 * h);
-    if (prec == 0) k_wall_copy<double><<<g, b, 0, s>>>((double*)wr, (double*)wu, sr, su, rnf, n1, n2, h, rho0);
-    else k_wall_copy<float><<<g, b, 0, s>>>((float*)wr, (float*)wu, sr, su, rnf, n1, n2, h, rho0);
+    if (prec == 0) k_wall_copy<double><<<g, b, 0, s>>>((double*)wr, (double*)wu, sr, su, rnf, n1, n2, h, rho0, ncol);
+    else k_wall_copy<float><<<g, b, 0, s>>>((float*)wr, (float*)wu, sr, su, rnf, n1, n2, h, rho0, ncol);
 }
 
-void launch_scale_volume(int Q, double* geo, const double* rnf, int n1, double rho0, cudaStream_t s) {
-    k_scale_volume<<<(n1 + 127) / 128, 128, 0, s>>>(geo, Geo::stride(Q), rnf, n1, rho0);
+void launch_scale_volume(int Q, double* geo, const double* rnf, int count, double rho0, cudaStream_t s) {
+    k_scale_volume<<<(count + 127) / 128, 128, 0, s>>>(geo, Geo::stride(Q), rnf, count, rho0);
 }
 
 void launch_row_mean(const double* f, int n1, int n2, double* out, cudaStream_t s) {

@@ -18,15 +18,14 @@ namespace clbm {
 
 namespace {
 
-template <int Q, typename S, typename C, bool ITER>
-__global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs a) {
+template <int Q, typename S, typename C, bool ITER, bool GEN>
+__global__ void __launch_bounds__(128, ITER ? 2 : (GEN ? 3 : 4)) k_fused_step(const StepArgs a) {
     using L = Lat<Q>;
-    using T = Tab<Q>;
     constexpr int H = L::H;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= a.n2) return;
-    const C* __restrict__ tb = (const C*)a.tab + (size_t)i * T::S;
+    const auto tb = TabOf<Q, C, GEN>::at(a.tab, i, j, a.n1, a.n2);
     const Consts<C> k = Consts<C>::make(a.k);
     const int row = i + H;
     const long long off = (long long)row * a.ld + j + GC;
@@ -52,7 +51,7 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_fused_step(const StepArgs
     }
     if (EdgeFill<Q, S>::needed(i, a.n1, a.n2)) {
         const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo, a.bc_hi,
-                                C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC};
+                                C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC, a.ncol};
         ef.fill(i, j, dst, a.plane, c.rho, c.Ut2);
     }
     // Near-wall rows keep rho and Ut^2 for the moving-wall correction (App. B).
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(128) k_boundary(const StepArgs a, S* __restric
             const int c1 = c1_of(al);
             if (wall == 0 ? (c1 < k) : (c1 > -k)) continue;
             const int b = bc == 0 ? opp_of(al) : hat_of(al);
-            const double* gt = a.ghost + 2 * ((wall * H + (k - 1)) * Q + al);
+            const double* gt = a.ghost + 2 * (((wall * H + (k - 1)) * Q + al) * a.ncol + (a.ncol > 1 ? j : 0));
             const C x = C(Store<S>::ld(st + b * P + (long long)mr * a.ld + j + GC));
             store_periodic<S, C>(st + al * P + (long long)gr * a.ld, j, a.n2,
                                  ghost_value<C>(x, gt, wr, U0, wu));
@@ -120,8 +119,13 @@ __global__ void __launch_bounds__(128) k_boundary(const StepArgs a, S* __restric
 template <int Q, typename S, typename C>
 void run_step(const StepArgs& a, cudaStream_t s) {
     dim3 b(128), g((a.n2 + 127) / 128, a.n1);
-    if (a.iters > 0) k_fused_step<Q, S, C, true><<<g, b, 0, s>>>(a);
-    else k_fused_step<Q, S, C, false><<<g, b, 0, s>>>(a);
+    if (a.ncol > 1) {
+        if (a.iters > 0) k_fused_step<Q, S, C, true, true><<<g, b, 0, s>>>(a);
+        else k_fused_step<Q, S, C, false, true><<<g, b, 0, s>>>(a);
+    } else {
+        if (a.iters > 0) k_fused_step<Q, S, C, true, false><<<g, b, 0, s>>>(a);
+        else k_fused_step<Q, S, C, false, false><<<g, b, 0, s>>>(a);
+    }
 }
 
 template <int Q, typename S, typename C>

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
         const int i0 = (tile / tiles_j) * G::TR, j0 = (tile % tiles_j) * G::TJ;
         const int i = i0 + r, j = j0 + cc;
         if (i < a.n1 && j < a.n2) {
-            const C* tb = (const C*)sm_tab(buf) + r * T::S;
+            const RowTab<Q, C> tb{(const C*)sm_tab(buf) + r * T::S};
             const S* in = (const S*)sm_in(buf);
             Cell<Q, C> c;
             pull_cell<Q, C>(
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
             });
             if (i < H || i >= a.n1 - H) {
                 const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo,
-                                        a.bc_hi, C(a.U0_lo), C(a.U0_hi), false};
+                                        a.bc_hi, C(a.U0_lo), C(a.U0_hi), false, 1};
                 ef.fill(i, j, out, G::TR * G::TJ, c.rho, c.Ut2);
             }
             if (i < H) {
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
         const int i0 = (tile / tiles_j) * G::TR, j0 = (tile % tiles_j) * G::TJ;
         const int i = i0 + r, j = j0 + cc;
         if (i < a.n1 && j < a.n2) {
-            const C* tb = (const C*)stage_tab(st) + r * T::S;
+            const RowTab<Q, C> tb{(const C*)stage_tab(st) + r * T::S};
             const S* in = (const S*)stage_in(st);
             Cell<Q, C> c;
             pull_cell<Q, C>(
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
             });
             if (EdgeFill<Q, S>::needed(i, a.n1, a.n2)) {
                 const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo,
-                                        a.bc_hi, C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC};
+                                        a.bc_hi, C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC, 1};
                 ef.fill(i, j, dst, a.plane, c.rho, c.Ut2);
             }
             if (i < H) {
