@@ -43,6 +43,11 @@ WORKLOADS = {
     "circular_couette_d2q9_fp32_1024x4096": (9, "fp32", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
     "circular_couette_d2q21_fp32_128x512": (21, "fp32", 128, 512, 1.0, 2.0, 0.35, 0.8, 0.01),
 }
+# general (non-separable) grids: name -> (Q, precision, n1, n2, amplitude, tau, u_wall)
+GENERAL_WORKLOADS = {
+    "wavy_channel_d2q21_fp32_1024x4096": (21, "fp32", 1024, 4096, 0.15, 0.8, 0.01),
+}
+TABLE_VALUES_PER_CELL = {21: 73, 9: 37}   # per-cell table entries of general grids
 DEFAULT = "circular_couette_d2q21_fp32_1024x4096"
 METRIC = "D2Q21 curvilinear MLUPS and % HBM roofline; served solves/s, p99 latency"
 STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
@@ -164,6 +169,13 @@ def smi_index(local):
     return vis.split(",")[local].strip()
 
 
+def wavy(wl):
+    """Wavy channel between straight walls (general grid), low wall moving."""
+    Q, prec, n1, n2, amp, tau, uw = GENERAL_WORKLOADS[wl]
+    nodes = I.mapped_nodes(I.wavy_channel(n1, n2, amp=amp), n1, n2, "extend")
+    return Q, prec, n1, n2, nodes, tau, uw
+
+
 def annulus(wl):
     Q, prec, n1, n2, R1, R2, CR, tau, uw = WORKLOADS[wl]
     e = I.polar_edges(R1, R2, n1, CR)
@@ -227,9 +239,14 @@ def run_reference(args):
 
 
 def config_of(wl, args):
-    Q, prec, n1, n2, R1, R2, CR, tau, uw = WORKLOADS[wl]
-    return {"workload": wl, "lattice": "D2Q%d" % Q, "n1": n1, "n2": n2, "geometry":
-            "annulus R2/R1=%g, radial CR=%g" % (R2 / R1, CR), "tau": tau, "u_wall": uw,
+    if wl in GENERAL_WORKLOADS:
+        Q, prec, n1, n2, amp, tau, uw = GENERAL_WORKLOADS[wl]
+        geom = "wavy channel (general grid, per-cell tables), amplitude %g" % amp
+    else:
+        Q, prec, n1, n2, R1, R2, CR, tau, uw = WORKLOADS[wl]
+        geom = "annulus R2/R1=%g, radial CR=%g" % (R2 / R1, CR)
+    return {"workload": wl, "lattice": "D2Q%d" % Q, "n1": n1, "n2": n2, "geometry": geom,
+            "tau": tau, "u_wall": uw,
             "storage": prec, "chunk": args.chunk,
             "kernel": {0: "auto", 1: "per-cell", 2: "tma-tiles", 3: "tma-pipeline"}[args.kernel],
             "l2": "inputs larger than L2 (state %d MB)" % (2 * Q * n1 * n2 * STORAGE_BYTES[prec] >> 20),
@@ -243,7 +260,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=100, help="time steps per bench step")
     ap.add_argument("--impl", default="clbm", choices=["clbm", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(GENERAL_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", type=int, default=0,
@@ -283,10 +300,16 @@ def main():
         torch.cuda.synchronize()
 
     wl = args.workload
-    Q, prec, n1, n2, e, tau, U0 = annulus(wl)
     stream = torch.cuda.Stream()
-    g = clbm.Grid(Q, n1, n2, e, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING,
-                  bc_hi=clbm.NOSLIP, device=local, stream=stream)
+    general = wl in GENERAL_WORKLOADS
+    if general:
+        Q, prec, n1, n2, nodes, tau, U0 = wavy(wl)
+        g = clbm.Grid(Q, n1, n2, None, kind=clbm.GENERAL, nodes=nodes, dx=1.0, precision=prec,
+                      bc_lo=clbm.MOVING, bc_hi=clbm.NOSLIP, device=local, stream=stream)
+    else:
+        Q, prec, n1, n2, e, tau, U0 = annulus(wl)
+        g = clbm.Grid(Q, n1, n2, e, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING,
+                      bc_hi=clbm.NOSLIP, device=local, stream=stream)
     g.set_case(tau, 1.0, U0, 0.0)
     if args.kernel:
         g.set_kernel(args.kernel)
@@ -320,6 +343,8 @@ def main():
     value = whole_job_mlups(cells, args.chunk, args.steps, world, ms_max)
     sb = STORAGE_BYTES[prec]
     bytes_per_launch = 2 * Q * sb * cells
+    if general:   # the per-cell tables are read once per update as well
+        bytes_per_launch += TABLE_VALUES_PER_CELL[Q] * (8 if prec == "fp64" else 4) * cells
     achieved = bytes_per_launch / (kms / kl * 1e-3) / 1e9 if kl else None
     peak, peak_src = peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -339,7 +364,7 @@ def main():
            "data": "synthetic", "config": config_of(wl, args), "roofline": roof,
            "gpu_launches": launches, "clocks": ck, "e2e": e2e,
            "residual_last": last[0] if last else None}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not general:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0 and world == 1 and not args.no_serve:
         out["serving"] = run_serving(args.serve_requests)

@@ -218,13 +218,16 @@ clbm_status clbm_batch_step(clbm_batch_handle b, long long n);
  * non-positive density, and the call then returns CLBM_EUNSTABLE. */
 clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons);
 /* Update tile of the batched kernel: 0 = 128 x 1 cells, 1 = 256 x 1 cells
- * (2 per thread), 2 = 32 x 4 cells, 3 = 64 x 1 cells. */
+ * (2 per thread), 2 = 32 x 4 cells, 3 = 64 x 1 cells, one thread per cell;
+ * 4 = 64 x 8 tiles staged by TMA in a warp-specialised pipeline (needs
+ * FP32 / FP16 / BF16 storage and TMA maps on every grid, else CLBM_EINVAL). */
 clbm_status clbm_batch_set_variant(clbm_batch_handle b, int variant);
-/* Autotuner: times every variant for `steps` steps on this batch (advancing
- * every grid by 4 (steps + 1) steps), keeps the fastest and caches the choice
- * for batches of the same lattice, precision and shape class in this process.
- * best (may be NULL) receives the variant, ms_per_step[4] (may be NULL) the
- * timings.  Synchronises. */
+/* Autotuner: times every usable variant for `steps` steps on this batch
+ * (advancing every grid by steps + 1 steps per variant), keeps the fastest and
+ * caches the choice for batches of the same lattice, precision and shape
+ * class in this process.  best (may be NULL) receives the variant,
+ * ms_per_step[5] (may be NULL) the timings (-1 for a variant the batch
+ * cannot use).  Synchronises. */
 clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* ms_per_step);
 clbm_status clbm_batch_launch_count(clbm_batch_handle b, long long* launches);
 clbm_status clbm_batch_destroy(clbm_batch_handle b);

@@ -285,7 +285,7 @@ class Batch:
     one persistent launch per phase, two steps per CUDA graph.  The grids stay
     owned by the caller and must outlive the batch."""
 
-    VARIANTS = 4
+    VARIANTS = 5
 
     def __init__(self, grids):
         self.grids = list(grids)

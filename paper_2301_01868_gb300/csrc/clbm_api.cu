@@ -775,8 +775,10 @@ struct clbm_batch {
     int phase;                       // time steps taken through the batch, mod 2
     BatchGrid* d_grids;
     std::vector<BatchGrid> h_grids;
-    int4* d_step[BATCH_VARIANTS];    // update tiles of lagged-force lattices, per variant
-    int nstep[BATCH_VARIANTS];
+    int4* d_step[BATCH_ALL];         // update tiles of lagged-force lattices, per variant
+    int nstep[BATCH_ALL];
+    void* d_maps;                    // TMA load maps of every lattice (variant BATCH_WS)
+    bool ws_ok;                      // every lattice has TMA maps
     int4* d_iter;                    // update tiles of lattices that iterate the force
     int niter;
     int4* d_bnd;
@@ -860,8 +862,12 @@ void drop_graphs(clbm_batch* b) {
 // the ghost rows and columns of the buffer it writes).  Returns the number of
 // kernels launched.
 int batch_one(clbm_batch* b, int p) {
-    launch_batch(b->Q, b->prec, 1, b->variant, b->d_grids, b->d_step[b->variant], b->nstep[b->variant],
-                 p, b->nblk, nullptr, b->stream);
+    if (b->variant == BATCH_WS)
+        launch_batch_ws(b->Q, b->prec, b->d_grids, b->d_maps, b->d_step[BATCH_WS], b->nstep[BATCH_WS], p,
+                        b->g[0]->nsm, b->g[0]->err, b->stream);
+    else
+        launch_batch(b->Q, b->prec, 1, b->variant, b->d_grids, b->d_step[b->variant], b->nstep[b->variant],
+                     p, b->nblk, nullptr, b->stream);
     launch_batch(b->Q, b->prec, 3, 0, b->d_grids, b->d_iter, b->niter, p, b->nblk, nullptr, b->stream);
     return (b->nstep[b->variant] > 0) + (b->niter > 0);
 }
@@ -949,7 +955,9 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
     // work-lists
     std::vector<int4> wb, wm;
     std::vector<int2> range;
-    std::vector<int4> ws[BATCH_VARIANTS], wi;
+    std::vector<int4> ws[BATCH_ALL], wi;
+    b->ws_ok = true;
+    for (int k = 0; k < n; ++k) b->ws_ok = b->ws_ok && grids[k]->tma != nullptr;
     int tj0, tr0;
     batch_tile_shape(0, &tj0, &tr0);
     for (int k = 0; k < n; ++k) {
@@ -964,7 +972,8 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
                 for (int j = 0; j < g->n2; j += tj0) wi.push_back(make_int4(k, i, j, 0));
             continue;
         }
-        for (int v = 0; v < BATCH_VARIANTS; ++v) {
+        for (int v = 0; v < BATCH_ALL; ++v) {
+            if (v == BATCH_WS && !b->ws_ok) continue;
             int tj, tr;
             batch_tile_shape(v, &tj, &tr);
             for (int i = 0; i < g->n1; i += tr)
@@ -988,9 +997,16 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
     b->nmom = (int)wm.size();
     size_t bytes = n * sizeof(BatchGrid) + wb.size() * sizeof(int4) + wm.size() * sizeof(int4) +
                    range.size() * sizeof(int2) + wm.size() * NRED * 8 + (size_t)n * NRED * 8;
-    for (int v = 0; v < BATCH_VARIANTS; ++v) {
+    for (int v = 0; v < BATCH_ALL; ++v) {
         b->nstep[v] = (int)ws[v].size();
         bytes += ws[v].size() * sizeof(int4);
+    }
+    std::vector<unsigned char> maps;
+    if (b->ws_ok) {
+        const size_t mb = tma_load_maps(grids[0]->tma, nullptr);
+        maps.resize(mb * n);
+        for (int k = 0; k < n; ++k) tma_load_maps(grids[k]->tma, maps.data() + mb * k);
+        bytes += maps.size();
     }
     b->niter = (int)wi.size();
     bytes += wi.size() * sizeof(int4);
@@ -1001,8 +1017,9 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_range, range.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_partial, wm.size() * NRED * 8);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_out, (size_t)n * NRED * 8);
-    for (int v = 0; v < BATCH_VARIANTS && e == cudaSuccess; ++v)
+    for (int v = 0; v < BATCH_ALL && e == cudaSuccess; ++v)
         if (!ws[v].empty()) e = cudaMalloc((void**)&b->d_step[v], ws[v].size() * sizeof(int4));
+    if (e == cudaSuccess && !maps.empty()) e = cudaMalloc(&b->d_maps, maps.size());
     if (e == cudaSuccess && !wi.empty()) e = cudaMalloc((void**)&b->d_iter, wi.size() * sizeof(int4));
     if (e != cudaSuccess) {
         clbm_batch_destroy(b);
@@ -1012,7 +1029,9 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
     cudaMemcpyAsync(b->d_mom, wm.data(), wm.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
     cudaMemcpyAsync(b->d_range, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice,
                     b->stream);
-    for (int v = 0; v < BATCH_VARIANTS; ++v)
+    if (!maps.empty())
+        cudaMemcpyAsync(b->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice, b->stream);
+    for (int v = 0; v < BATCH_ALL; ++v)
         if (!ws[v].empty())
             cudaMemcpyAsync(b->d_step[v], ws[v].data(), ws[v].size() * sizeof(int4), cudaMemcpyHostToDevice,
                             b->stream);
@@ -1101,13 +1120,17 @@ clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons) 
         st = upload_desc(b);
         if (st != CLBM_OK) return st;
     }
+    st = check_err(b->g[0]);  // bounded waits of the pipelined variant
+    if (st != CLBM_OK) return st;
     if (unstable) return fail(CLBM_EUNSTABLE, "a lattice of the batch has a non-finite or non-positive density");
     return CLBM_OK;
 }
 
 clbm_status clbm_batch_set_variant(clbm_batch_handle b, int variant) {
     if (!b) return fail(CLBM_EINVAL, "batch is NULL");
-    if (variant < 0 || variant >= BATCH_VARIANTS) return fail(CLBM_EINVAL, "variant out of range");
+    if (variant < 0 || variant > BATCH_WS) return fail(CLBM_EINVAL, "variant out of range");
+    if (variant == BATCH_WS && !b->ws_ok)
+        return fail(CLBM_EINVAL, "the pipelined TMA variant needs 16/32-bit storage and TMA maps on every grid");
     if (variant != b->variant) drop_graphs(b);
     b->variant = variant;
     return CLBM_OK;
@@ -1126,7 +1149,11 @@ clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* m
     st = refresh(b);
     if (st != CLBM_OK) return st;
     batch_ghosts(b);
-    for (int v = 0; v < BATCH_VARIANTS; ++v) {
+    for (int v = 0; v < BATCH_ALL; ++v) {
+        if (v == BATCH_WS && !b->ws_ok) {
+            if (ms_per_step) ms_per_step[v] = -1.0;
+            continue;
+        }
         b->variant = v;
         b->launches += batch_one(b, b->phase);  // warm-up step
         batch_advance(b, 1);
@@ -1178,7 +1205,8 @@ clbm_status clbm_batch_destroy(clbm_batch_handle b) {
     cudaFree(b->d_range);
     cudaFree(b->d_partial);
     cudaFree(b->d_out);
-    for (int v = 0; v < BATCH_VARIANTS; ++v) cudaFree(b->d_step[v]);
+    for (int v = 0; v < BATCH_ALL; ++v) cudaFree(b->d_step[v]);
+    cudaFree(b->d_maps);
     cudaFree(b->d_iter);
     delete b;
     return CLBM_OK;

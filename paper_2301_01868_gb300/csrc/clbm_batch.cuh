@@ -36,4 +36,13 @@ void launch_batch_reduce(const double* partial, const int2* range, int ngrids, d
 // Update tile (columns x rows) of a variant.
 void batch_tile_shape(int variant, int* tj, int* tr);
 
+// Variant BATCH_WS: the pipelined TMA update over 8 x 64 tiles of every
+// lattice (k_step_tma.cu).  maps: per lattice the 2 x 8 load maps of its two
+// state buffers (device memory, tma_load_maps layout); err: device error word
+// of bounded waits.  Returns nonzero if it could not be launched.
+constexpr int BATCH_WS = BATCH_VARIANTS;
+constexpr int BATCH_ALL = BATCH_VARIANTS + 1;
+int launch_batch_ws(int Q, int prec, const BatchGrid* grids, const void* maps, const int4* work, int nwork,
+                    int parity, int nsm, int* err, cudaStream_t s);
+
 }  // namespace clbm

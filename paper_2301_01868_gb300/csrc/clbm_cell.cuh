@@ -267,36 +267,100 @@ __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const 
     }
 }
 
-// Per-cell terms of the residual and conservation sums (clbm_residual), added
-// to v: J |u(t) - u(t')|^2, J |u|^2 (physical u = Ut^k g_k), mass, momentum
-// sum c N' (2), kinetic energy J rho |u|^2 / 2, angular momentum
-// J rho (M1 Ut^1 + M2 Ut^2), largest |u|^2, and a flag for a non-finite or
-// non-positive density.  Each term is formed in the compute type (the
-// precision of the update) and summed in FP64; the mass adds the exact FP64
-// rest part J rho0 of the row.  prev holds Ut of the last call (FP64 storage).
+// Per-cell terms of the residual and conservation sums (clbm_residual):
+// J |u(t) - u(t')|^2, J |u|^2 (physical u = Ut^k g_k), the deviation part of
+// the mass and the momentum sum c N' (2), kinetic energy J rho |u|^2 / 2,
+// angular momentum J rho (M1 Ut^1 + M2 Ut^2), |u|^2, and a flag for a
+// non-finite or non-positive density; rest = J rho0, the exact FP64 rest
+// part of the mass.  Terms are formed in the compute type (the precision of
+// the update).  prev holds Ut of the last call (FP64 storage).
+template <typename C>
+struct CellTerms {
+    C dd, uu_j, ls, ls1, ls2, ke, am, uu;
+    bool bad;
+    double rest;
+};
+
 template <int Q, typename C>
-__device__ __forceinline__ void residual_terms(const Cell<Q, C>& c, const double* __restrict__ ge,
-                                               double rho0, double* prev1, double* prev2,
-                                               bool have_prev, double (&v)[NRED]) {
+__device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, const double* __restrict__ ge,
+                                                       double rho0, double* prev1, double* prev2,
+                                                       bool have_prev) {
     const C g11 = C(ge[Geo::G11]), g12 = C(ge[Geo::G12]), g22 = C(ge[Geo::G22]);
     const C J = C(ge[Geo::J]);
     const C u1 = c.Ut1, u2 = c.Ut2;
-    const C uu = g11 * u1 * u1 + C(2) * g12 * u1 * u2 + g22 * u2 * u2;
+    CellTerms<C> t;
+    t.uu = g11 * u1 * u1 + C(2) * g12 * u1 * u2 + g22 * u2 * u2;
+    t.dd = C(0);
     if (have_prev) {
         const C e1 = u1 - C(*prev1), e2 = u2 - C(*prev2);
-        v[0] += double(J * (g11 * e1 * e1 + C(2) * g12 * e1 * e2 + g22 * e2 * e2));
+        t.dd = J * (g11 * e1 * e1 + C(2) * g12 * e1 * e2 + g22 * e2 * e2);
     }
     *prev1 = double(u1);
     *prev2 = double(u2);
-    v[1] += double(J * uu);
-    v[2] += ge[Geo::J] * rho0 + double(c.ls);
-    v[3] += double(c.ls1);
-    v[4] += double(c.ls2);
-    v[5] += double(C(0.5) * J * c.rho * uu);
-    v[6] += double(J * c.rho * (C(ge[Geo::M1]) * u1 + C(ge[Geo::M2]) * u2));
-    v[7] = fmax(v[7], double(uu));
-    v[8] += (c.rho > C(0) && isfinite(c.rho) && isfinite(uu)) ? 0.0 : 1.0;
+    t.uu_j = J * t.uu;
+    t.ls = c.ls;
+    t.ls1 = c.ls1;
+    t.ls2 = c.ls2;
+    t.ke = C(0.5) * J * c.rho * t.uu;
+    t.am = J * c.rho * (C(ge[Geo::M1]) * u1 + C(ge[Geo::M2]) * u2);
+    t.bad = !(c.rho > C(0) && isfinite(c.rho) && isfinite(t.uu));
+    t.rest = ge[Geo::J] * rho0;
+    return t;
 }
+
+// A thread's running sums of CellTerms, reduced in FP64 afterwards (slots of
+// NRED: 0 dd, 1 |u|^2, 2 mass, 3-4 momentum, 5 kinetic energy, 6 angular
+// momentum, 7 largest |u|^2, 8 unstable cells).  FP64 compute sums in FP64;
+// FP32 compute sums with Kahan compensation in FP32 (the FP64 pipe is far
+// slower) and keeps the rest part of the mass in FP64.
+template <typename C> struct ResAcc;
+template <> struct ResAcc<double> {
+    double v[NRED] = {};
+    __device__ __forceinline__ void add(const CellTerms<double>& t) {
+        v[0] += t.dd;
+        v[1] += t.uu_j;
+        v[2] += t.rest + t.ls;
+        v[3] += t.ls1;
+        v[4] += t.ls2;
+        v[5] += t.ke;
+        v[6] += t.am;
+        v[7] = fmax(v[7], t.uu);
+        v[8] += t.bad ? 1.0 : 0.0;
+    }
+    __device__ __forceinline__ void out(double (&o)[NRED]) const {
+        for (int k = 0; k < NRED; ++k) o[k] = v[k];
+    }
+};
+template <> struct ResAcc<float> {
+    float s[7] = {}, e[7] = {};
+    float umax = 0.f, bad = 0.f;
+    double rest = 0.0;
+    __device__ __forceinline__ void kahan(int k, float x) {
+        const float y = x - e[k];
+        const float t = s[k] + y;
+        e[k] = (t - s[k]) - y;
+        s[k] = t;
+    }
+    __device__ __forceinline__ void add(const CellTerms<float>& t) {
+        kahan(0, t.dd);
+        kahan(1, t.uu_j);
+        kahan(2, t.ls);
+        kahan(3, t.ls1);
+        kahan(4, t.ls2);
+        kahan(5, t.ke);
+        kahan(6, t.am);
+        umax = fmaxf(umax, t.uu);
+        bad += t.bad ? 1.f : 0.f;
+        rest += t.rest;
+    }
+    __device__ __forceinline__ void out(double (&o)[NRED]) const {
+        for (int k = 0; k < 7; ++k) o[k] = double(s[k]) - double(e[k]);
+        o[2] += rest;
+        o[7] = umax;
+        o[8] = bad;
+        o[9] = 0.0;
+    }
+};
 
 // Reference N of direction a at 1-based row r and geometry column jc (FP64
 // geometry table of ncol columns); rows beyond a wall are the mirror image

@@ -153,6 +153,9 @@ void launch_row_mean(const double* field, int n1, int n2, double* out, cudaStrea
 struct TmaMaps;
 int make_tma_maps(int Q, int prec, TmaMaps** out, void* bufA, void* bufB, int n1, int n2, int ld);
 void free_tma_maps(TmaMaps* m);
+// Copy the 2 x 8 load maps of both buffers to out (host); returns their bytes
+// (out may be NULL to ask the size).
+size_t tma_load_maps(const TmaMaps* m, void* out);
 int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
                     int pipelined, cudaStream_t s);
 

@@ -175,8 +175,10 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_batch_moments(const Batch
                 collide_emit<Q, C>(tb, c, kc, [](int, C) {});
             }
             const size_t m = (size_t)i * g.n2 + j, nc = (size_t)g.n1 * g.n2;
-            residual_terms<Q, C>(c, g.geo + (size_t)i * Geo::stride(Q), g.k.rho0, g.prev + m,
-                                 g.prev + nc + m, g.have_prev != 0, v);
+            ResAcc<C> acc;
+            acc.add(residual_terms<Q, C>(c, g.geo + (size_t)i * Geo::stride(Q), g.k.rho0, g.prev + m,
+                                         g.prev + nc + m, g.have_prev != 0));
+            acc.out(v);
         }
 #pragma unroll
         for (int q = 0; q < NRED; ++q) {
@@ -252,7 +254,8 @@ void batch_tile_shape(int variant, int* tj, int* tr) {
         case 0: *tj = Var<0>::TJ; *tr = Var<0>::TR; break;
         case 1: *tj = Var<1>::TJ; *tr = Var<1>::TR; break;
         case 2: *tj = Var<2>::TJ; *tr = Var<2>::TR; break;
-        default: *tj = Var<3>::TJ; *tr = Var<3>::TR; break;
+        case 3: *tj = Var<3>::TJ; *tr = Var<3>::TR; break;
+        default: *tj = 64; *tr = 8; break;  // BATCH_WS: the TMA tile of k_step_tma.cu
     }
 }
 

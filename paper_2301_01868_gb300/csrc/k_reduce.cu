@@ -9,9 +9,9 @@ namespace {
 
 constexpr int RB = 128;  // threads per block of the diagnostics kernels
 
-// One block per (row, 128-column) item up to 65536 blocks: enough loads in
-// flight to stream the state (fewer, longer-lived blocks left the diagnostics
-// latency-bound).
+// Blocks of the residual reduction: one per (row, 128-column) item, up to
+// 65536 (each then takes a few items); the final reduction runs one block per
+// quantity over all block partials.
 int residual_blocks(int n1, int n2) {
     const int items = n1 * ((n2 + RB - 1) / RB);
     return items < 65536 ? items : 65536;
@@ -60,28 +60,30 @@ __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters) {
     if (a.F2) a.F2[m] = double(c.F2);
 }
 
-// Residual and conservation sums: blocks stride over (row, 128-column) items; each thread accumulates its cells in FP64 in a fixed order, then a
-// warp-shuffle and block reduction in a fixed tree writes one partial per
-// block, so repeated runs give identical bits.  The rest parts of the totals
-// are exact per row: sum_a ref_a(i) = J rho0 and sum_a c_a ref_a(i) = 0.
-// The largest |u| is tracked as the largest |u|^2 and rooted once per block.
+// Residual and conservation sums: blocks stride over (row, 128-column)
+// items; each thread accumulates its cells in a fixed order
+// (ResAcc), then a warp-shuffle and block reduction in FP64 in a fixed tree
+// writes one partial per block, so repeated runs give identical bits.  The
+// rest parts of the totals are exact per row: sum_a ref_a(i) = J rho0 and
+// sum_a c_a ref_a(i) = 0.  The largest |u| is tracked as the largest |u|^2
+// and rooted once per block.
 template <int Q, typename S, typename C, bool ITER, bool GEN>
 __global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, int iters) {
     const int bx = (a.n2 + RB - 1) / RB;
     const int items = a.n1 * bx;
     const size_t nc = (size_t)a.n1 * a.n2;
-    double v[NRED];
-#pragma unroll
-    for (int k = 0; k < NRED; ++k) v[k] = 0.0;
+    ResAcc<C> acc;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int i = it / bx, j = (it % bx) * RB + threadIdx.x;
         if (j >= a.n2) continue;
         Cell<Q, C> c;
         cell_moments<Q, S, C, ITER, GEN>(a, iters, i, j, c);
         const size_t m = (size_t)i * a.n2 + j;
-        residual_terms<Q, C>(c, geo_of(a.geo, Q, a.ncol, i, j), a.k.rho0, a.ut_prev + m,
-                             a.ut_prev + nc + m, a.have_prev != 0, v);
+        acc.add(residual_terms<Q, C>(c, geo_of(a.geo, Q, a.ncol, i, j), a.k.rho0, a.ut_prev + m,
+                                     a.ut_prev + nc + m, a.have_prev != 0));
     }
+    double v[NRED];
+    acc.out(v);
 #pragma unroll
     for (int k = 0; k < NRED; ++k) {
         double x = v[k];

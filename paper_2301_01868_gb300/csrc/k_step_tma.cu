@@ -15,6 +15,9 @@
 // an error code and returns.
 #include <cuda.h>
 
+#include <cstring>
+
+#include "clbm_batch.cuh"
 #include "clbm_cell.cuh"
 
 namespace clbm {
@@ -290,18 +293,89 @@ __global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
 #undef s_abort
 }
 
-// The pipelined update (PipeGeom).  Tile k of a CTA uses stage k mod STAGES;
-// the producer re-fills a stage once all consumer warps have released it.
-// Waits are bounded: on time-out the kernel records an error code, the other
-// warps give up at their next wait, and the producer lets its loads in flight
-// land before the CTA exits.
+// What a consumer needs of the lattice a tile belongs to.
+template <typename S>
+struct WsLattice {
+    S* dst;                 // state buffer written (row 0, column 0)
+    const double* ghost;
+    void* wall_rho;
+    void* wall_ut2;
+    long long plane;
+    int ld, n1, n2, bc_lo, bc_hi;
+    double U0_lo, U0_hi;
+};
+
+// One consumer thread's cell (i0 + r, j0 + cc) of a tile staged in shared
+// memory: pull, collide, store straight to global memory (plus the periodic
+// copy and, next to a wall, the ghost values it supplies), wall moments.
 template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
-    k_fused_ws(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
+__device__ __forceinline__ void ws_update_cell(const WsLattice<S>& L, const Consts<C>& k, const S* in,
+                                               const C* tab_rows, int i0, int j0, int r, int cc) {
     using G = TileGeom<Q, S>;
-    using P = PipeGeom<Q, S>;
     using T = Tab<Q>;
     constexpr int H = Lat<Q>::H;
+    const int i = i0 + r, j = j0 + cc;
+    if (i >= L.n1 || j >= L.n2) return;
+    const RowTab<Q, C> tb{tab_rows + r * T::S};
+    Cell<Q, C> c;
+    pull_cell<Q, C>(
+        [&](int al, int dr, int dc) -> C {
+            return C(Store<S>::lds(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) + cc +
+                                   G::col0(al) + dc));
+        },
+        tb, k, c);
+    S* dst = L.dst + (long long)(i + H) * L.ld + j + GC;
+    const int dw = wrap_offset(j, L.n2);
+    collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
+        Store<S>::st(dst + al * L.plane, v);
+        if (dw != 0) Store<S>::st(dst + al * L.plane + dw, v);
+    });
+    if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
+        const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
+                                C(L.U0_lo), C(L.U0_hi), L.n2 < 2 * GC, 1};
+        ef.fill(i, j, dst, L.plane, c.rho, c.Ut2);
+    }
+    if (i < H) {
+        const int idx = i * L.n2 + j;
+        ((C*)L.wall_rho)[idx] = c.rho;
+        ((C*)L.wall_ut2)[idx] = c.Ut2;
+    }
+    if (i >= L.n1 - H) {
+        const int idx = (H + (L.n1 - 1 - i)) * L.n2 + j;
+        ((C*)L.wall_rho)[idx] = c.rho;
+        ((C*)L.wall_ut2)[idx] = c.Ut2;
+    }
+}
+
+// Issue the TMA boxes of tile (i0, j0) from the 8 load maps of the source
+// buffer, plus the tile's table rows, on barrier bar.
+template <int Q, typename S, typename C>
+__device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0, int n1, const C* tab,
+                                         unsigned char* sm_in, unsigned char* sm_tab, uint64_t* bar) {
+    using G = TileGeom<Q, S>;
+    constexpr int H = Lat<Q>::H;
+    const int nrows = n1 - i0 < G::TR ? n1 - i0 : G::TR;
+    uint32_t bytes = (uint32_t)nrows * Tab<Q>::S * 4;
+#pragma unroll
+    for (int al = 0; al < Q; ++al) bytes += G::rows(al) * G::width(al) * (int)sizeof(S);
+    mbar_expect(bar, bytes);
+    S* in = (S*)sm_in;
+#pragma unroll
+    for (int al = 0; al < Q; ++al)
+        tma_load3(in + G::off(al), &ld8[G::shape(al)], j0 + GC - G::col0(al), i0 + H - G::row0(al), al, bar);
+    bulk_load(sm_tab, tab + (size_t)i0 * Tab<Q>::S, (uint32_t)nrows * Tab<Q>::S * 4, bar);
+}
+
+// The pipelined loop shared by the single-lattice and the batched kernels:
+// tile t of this CTA is tile_of(blockIdx.x + t gridDim.x); tile_of fills
+// (load maps, table, lattice, i0, j0) of a tile index.  The producer warp
+// re-fills a stage once all consumer warps released it; waits are bounded
+// and a time-out records an error, stops the other warps at their next
+// wait, and lets the loads in flight land before the CTA exits.
+template <int Q, typename S, typename C, typename TileOf>
+__device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_of) {
+    using G = TileGeom<Q, S>;
+    using P = PipeGeom<Q, S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* const smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     uint64_t* const full = (uint64_t*)(smem + P::STAGES * P::STAGE_BYTES);
@@ -311,8 +385,6 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     auto stage_tab = [&](int st) { return smem + st * P::STAGE_BYTES + P::IN_BYTES; };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles_j = (a.n2 + G::TJ - 1) / G::TJ;
-    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * tiles_j;
     if (tid == 0) {
         for (int st = 0; st < P::STAGES; ++st) {
             mbar_init(&full[st], 1);
@@ -330,11 +402,13 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
                 const int st = it % P::STAGES;
                 if (it >= P::STAGES && !mbar_wait(&empty[st], (it / P::STAGES - 1) & 1)) {
                     *s_abort = 1;
-                    atomicExch(a.err, 1);
+                    atomicExch(err, 1);
                     break;
                 }
                 if (*s_abort) break;
-                issue_tile<Q, S, C>(maps, src, tile, tiles_j, a, stage_in(st), stage_tab(st), &full[st]);
+                const auto t = tile_of(tile);
+                ws_issue<Q, S, C>(t.ld8, t.i0, t.j0, t.lat.n1, t.tab, stage_in(st), stage_tab(st),
+                                  &full[st]);
             }
             // the loads of the last issued tiles must land before the CTA exits
             for (int t = it > P::STAGES ? it - P::STAGES : 0; t < it; ++t)
@@ -344,53 +418,70 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     }
 
     const int r = tid / G::TJ, cc = tid % G::TJ;
-    const Consts<C> k = Consts<C>::make(a.k);
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int st = it % P::STAGES;
         if (!mbar_wait(&full[st], (it / P::STAGES) & 1)) {
             *s_abort = 1;
-            atomicExch(a.err, 1);
+            atomicExch(err, 1);
             break;
         }
         if (*s_abort) break;
-        const int i0 = (tile / tiles_j) * G::TR, j0 = (tile % tiles_j) * G::TJ;
-        const int i = i0 + r, j = j0 + cc;
-        if (i < a.n1 && j < a.n2) {
-            const RowTab<Q, C> tb{(const C*)stage_tab(st) + r * T::S};
-            const S* in = (const S*)stage_in(st);
-            Cell<Q, C> c;
-            pull_cell<Q, C>(
-                [&](int al, int dr, int dc) -> C {
-                    return C(Store<S>::lds(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) +
-                                           cc + G::col0(al) + dc));
-                },
-                tb, k, c);
-            S* dst = (S*)a.dst + (long long)(i + H) * a.ld + j + GC;
-            const int dw = wrap_offset(j, a.n2);
-            collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
-                Store<S>::st(dst + al * a.plane, v);
-                if (dw != 0) Store<S>::st(dst + al * a.plane + dw, v);
-            });
-            if (EdgeFill<Q, S>::needed(i, a.n1, a.n2)) {
-                const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo,
-                                        a.bc_hi, C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC, 1};
-                ef.fill(i, j, dst, a.plane, c.rho, c.Ut2);
-            }
-            if (i < H) {
-                const int idx = i * a.n2 + j;
-                ((C*)a.wall_rho)[idx] = c.rho;
-                ((C*)a.wall_ut2)[idx] = c.Ut2;
-            }
-            if (i >= a.n1 - H) {
-                const int idx = (H + (a.n1 - 1 - i)) * a.n2 + j;
-                ((C*)a.wall_rho)[idx] = c.rho;
-                ((C*)a.wall_ut2)[idx] = c.Ut2;
-            }
-        }
+        const auto t = tile_of(tile);
+        ws_update_cell<Q, S, C>(t.lat, t.k, (const S*)stage_in(st), (const C*)stage_tab(st), t.i0, t.j0,
+                                r, cc);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
     }
+}
+
+template <int Q, typename S, typename C>
+struct WsTile {
+    const CUtensorMap* ld8;
+    const C* tab;
+    WsLattice<S> lat;
+    Consts<C> k;
+    int i0, j0;
+};
+
+// The pipelined update of one lattice (PipeGeom): tile k of a CTA uses stage
+// k mod STAGES.
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+    k_fused_ws(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
+    using G = TileGeom<Q, S>;
+    const int tiles_j = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * tiles_j;
+    const WsLattice<S> lat{(S*)a.dst, a.ghost, a.wall_rho, a.wall_ut2, a.plane, a.ld, a.n1, a.n2,
+                           a.bc_lo, a.bc_hi, a.U0_lo, a.U0_hi};
+    const Consts<C> k = Consts<C>::make(a.k);
+    ws_pipeline<Q, S, C>(ntiles, a.err, [&](int tile) {
+        return WsTile<Q, S, C>{maps.ld[src], (const C*)a.tab, lat, k, (tile / tiles_j) * G::TR,
+                               (tile % tiles_j) * G::TJ};
+    });
+}
+
+// The pipelined update of a batch: work item e = (lattice, i0, j0) over all
+// lattices' 8 x 64 tiles; maps holds each lattice's 2 x 8 load maps in global
+// memory (written before the launch; acquired for the tensor-map proxy
+// before use).
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+    k_batch_ws(const BatchGrid* __restrict__ grids, const CUtensorMap* __restrict__ maps,
+               const int4* __restrict__ work, int nwork, int parity, int* err) {
+    ws_pipeline<Q, S, C>(nwork, err, [&](int e) {
+        const int4 w = work[e];
+        const BatchGrid& g = grids[w.x];
+        const int src = g.parity ^ parity;
+        const CUtensorMap* ld8 = maps + ((size_t)w.x * 2 + src) * 8;
+        if ((threadIdx.x & 31) == 0 && threadIdx.x / 32 == PipeGeom<Q, S>::CONSUMERS)
+            for (int q = 0; q < 8; ++q)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ld8 + q)
+                             : "memory");
+        const WsLattice<S> lat{(S*)g.phys[src ^ 1], g.ghost, g.wall_rho, g.wall_ut2, g.plane, g.ld,
+                               g.n1, g.n2, g.bc_lo, g.bc_hi, g.U0_lo, g.U0_hi};
+        return WsTile<Q, S, C>{ld8, (const C*)g.tab, lat, Consts<C>::make(g.k), w.y, w.z};
+    });
 }
 
 }  // namespace
@@ -413,6 +504,51 @@ static int run_ws(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cuda
     const int grid = tiles < nsm ? tiles : nsm;
     k_fused_ws<Q, S, C><<<grid, P::NTHREADS, P::SMEM, s>>>(maps, a, src);
     return 0;
+}
+
+template <int Q, typename S>
+static int run_batch_ws(const BatchGrid* grids, const void* maps, const int4* work, int nwork, int parity,
+                        int nsm, int* err, cudaStream_t s) {
+    using P = PipeGeom<Q, S>;
+    using C = typename Store<S>::C;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_batch_ws<Q, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 P::SMEM) != cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    const int grid = nwork < nsm ? nwork : nsm;
+    k_batch_ws<Q, S, C><<<grid, P::NTHREADS, P::SMEM, s>>>(grids, (const CUtensorMap*)maps, work, nwork,
+                                                          parity, err);
+    return 0;
+}
+
+int launch_batch_ws(int Q, int prec, const BatchGrid* grids, const void* maps, const int4* work, int nwork,
+                    int parity, int nsm, int* err, cudaStream_t s) {
+    if (nwork <= 0) return 0;
+    if (Q == 9) {
+        switch (prec) {
+            case 1: return run_batch_ws<9, float>(grids, maps, work, nwork, parity, nsm, err, s);
+            case 2: return run_batch_ws<9, __half>(grids, maps, work, nwork, parity, nsm, err, s);
+            case 3: return run_batch_ws<9, __nv_bfloat16>(grids, maps, work, nwork, parity, nsm, err, s);
+            default: return -1;
+        }
+    }
+    switch (prec) {
+        case 1: return run_batch_ws<21, float>(grids, maps, work, nwork, parity, nsm, err, s);
+        case 2: return run_batch_ws<21, __half>(grids, maps, work, nwork, parity, nsm, err, s);
+        case 3: return run_batch_ws<21, __nv_bfloat16>(grids, maps, work, nwork, parity, nsm, err, s);
+        default: return -1;
+    }
+}
+
+size_t tma_load_maps(const TmaMaps* m, void* out) {
+    const size_t bytes = sizeof(m->ld);
+    if (out) memcpy(out, m->ld, bytes);
+    return bytes;
 }
 
 template <int Q, typename S>
