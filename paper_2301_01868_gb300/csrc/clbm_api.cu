@@ -68,6 +68,7 @@ struct clbm_grid {
     double step2;
     double* stage;          // lazily allocated FP64 staging buffer for host transfers
     int ncol;               // geometry columns: 1 (planar, polar) or n2 (general)
+    double rest_mass;       // rho0 times the total volume (the rest part of the mass)
     std::vector<double> nodes;  // node positions of a general grid (for the no-flow clone)
     void* phys[2];          // the two state buffers (stA / stB alternate over them)
     TmaMaps* tma;           // tensor maps of the TMA-staged update (16/32-bit storage)
@@ -243,8 +244,12 @@ clbm_status rebuild_tables(clbm_grid* g) {
     launch_reference(g->Q, g->geo, g->n1 * g->ncol, g->cs.rho0, g->stream);
     launch_tables(g->Q, g->prec, g->geo, g->tab, g->ghost, g->n1, g->n2, g->ncol, g->bc_lo, g->bc_hi,
                   g->stream);
-    g->launches += 3;
+    launch_rest_mass(g->Q, g->geo, g->n1 * g->ncol, g->ncol == 1 ? g->n2 : 1, g->cs.rho0, g->red + NRED,
+                     g->stream);
+    g->launches += 4;
     CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&g->rest_mass, g->red + NRED, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
     return CLBM_OK;
 }
 
@@ -613,6 +618,7 @@ clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
     double r = INFINITY;
     if (g->have_prev && dt > 0) r = v[1] > 0.0 ? sqrt(v[0]) / (dt * sqrt(v[1])) : (v[0] > 0 ? INFINITY : 0.0);
     if (res) *res = r;
+    v[2] += g->rest_mass;
     if (cons)
         for (int k = 0; k < 6; ++k) cons[k] = v[2 + k];
     g->have_prev = true;
@@ -1110,7 +1116,7 @@ clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons) 
         if (x[8] > 0.0 || !std::isfinite(x[2])) r = NAN;
         if (res) res[k] = r;
         if (cons)
-            for (int q = 0; q < 6; ++q) cons[k * 6 + q] = x[2 + q];
+            for (int q = 0; q < 6; ++q) cons[k * 6 + q] = x[2 + q] + (q == 0 ? g->rest_mass : 0.0);
         if (!g->have_prev) changed = true;
         g->have_prev = true;
         g->t_prev = g->t;

@@ -74,17 +74,21 @@ struct CellTab {
     static constexpr bool ALL_OFFSETS = true;
     const C* p;             // entry 0 of this cell
     size_t st;              // plane stride (cells)
-    __device__ __forceinline__ C s(int k) const { return p[(size_t)k * st]; }
+    C gi11, gi12, gi22;     // inverse metric of the cell (read once)
+    __device__ __forceinline__ CellTab(const C* p_, size_t st_) : p(p_), st(st_) {
+        gi11 = ld(Tab<Q>::G11);
+        gi12 = ld(Tab<Q>::G12);
+        gi22 = ld(Tab<Q>::G22);
+    }
+    __device__ __forceinline__ C ld(int k) const { return __ldg(p + (size_t)k * st); }
+    __device__ __forceinline__ C s(int k) const {
+        return k == Tab<Q>::G11 ? gi11 : k == Tab<Q>::G12 ? gi12 : k == Tab<Q>::G22 ? gi22 : ld(k);
+    }
     __device__ __forceinline__ V4<C> pa(int q) const {
-        return {p[(size_t)L::pa(q) * st], p[(size_t)(L::pa(q) + 1) * st], p[(size_t)(L::pa(q) + 2) * st],
-                p[(size_t)(L::pa(q) + 3) * st]};
+        return {ld(L::pa(q)), ld(L::pa(q) + 1), ld(L::pa(q) + 2), ld(L::pa(q) + 3)};
     }
-    __device__ __forceinline__ V4<C> pd(int q) const {
-        return {p[(size_t)L::pd(q) * st], p[(size_t)(L::pd(q) + 1) * st], C(0), C(0)};
-    }
-    __device__ __forceinline__ C p0(int q) const {
-        return rest_poly_c<Q, C>(Lat<Q>::plus(q), s(Tab<Q>::G11), s(Tab<Q>::G12), s(Tab<Q>::G22));
-    }
+    __device__ __forceinline__ V4<C> pd(int q) const { return {ld(L::pd(q)), ld(L::pd(q) + 1), C(0), C(0)}; }
+    __device__ __forceinline__ C p0(int q) const { return rest_poly_c<Q, C>(Lat<Q>::plus(q), gi11, gi12, gi22); }
     __device__ __forceinline__ V4<C> pb(int q) const {
         const int a = Lat<Q>::plus(q);
         const C w = C(Lat<Q>::w(a)), c1 = C(c1_of(a)), c2 = C(c2_of(a));
@@ -104,7 +108,7 @@ template <int Q, typename C> struct TabOf<Q, C, false> {
 };
 template <int Q, typename C> struct TabOf<Q, C, true> {
     __device__ static __forceinline__ CellTab<Q, C> at(const void* tab, int i, int j, int n1, int n2) {
-        return {(const C*)tab + (size_t)i * n2 + j, (size_t)n1 * n2};
+        return CellTab<Q, C>((const C*)tab + (size_t)i * n2 + j, (size_t)n1 * n2);
     }
 };
 
@@ -269,42 +273,41 @@ __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const 
 
 // Per-cell terms of the residual and conservation sums (clbm_residual):
 // J |u(t) - u(t')|^2, J |u|^2 (physical u = Ut^k g_k), the deviation part of
-// the mass and the momentum sum c N' (2), kinetic energy J rho |u|^2 / 2,
+// the mass (the rest part, rho0 times the total volume, is added on the
+// host) and the momentum sum c N' (2), kinetic energy J rho |u|^2 / 2,
 // angular momentum J rho (M1 Ut^1 + M2 Ut^2), |u|^2, and a flag for a
-// non-finite or non-positive density; rest = J rho0, the exact FP64 rest
-// part of the mass.  Terms are formed in the compute type (the precision of
-// the update).  prev holds Ut of the last call (FP64 storage).
+// non-finite or non-positive density.  Everything is formed in the compute
+// type from the coefficient table (no FP64 work per cell in FP32 compute).
+// prev holds Ut of the last call in the compute type.
 template <typename C>
 struct CellTerms {
     C dd, uu_j, ls, ls1, ls2, ke, am, uu;
     bool bad;
-    double rest;
 };
 
-template <int Q, typename C>
-__device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, const double* __restrict__ ge,
-                                                       double rho0, double* prev1, double* prev2,
+template <int Q, typename C, typename TB>
+__device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, const TB& tb, C* prev1, C* prev2,
                                                        bool have_prev) {
-    const C g11 = C(ge[Geo::G11]), g12 = C(ge[Geo::G12]), g22 = C(ge[Geo::G22]);
-    const C J = C(ge[Geo::J]);
+    using T = Tab<Q>;
+    const C g11 = tb.s(T::C11), g12 = tb.s(T::C12), g22 = tb.s(T::C22);
+    const C J = tb.s(T::J);
     const C u1 = c.Ut1, u2 = c.Ut2;
     CellTerms<C> t;
     t.uu = g11 * u1 * u1 + C(2) * g12 * u1 * u2 + g22 * u2 * u2;
     t.dd = C(0);
     if (have_prev) {
-        const C e1 = u1 - C(*prev1), e2 = u2 - C(*prev2);
+        const C e1 = u1 - *prev1, e2 = u2 - *prev2;
         t.dd = J * (g11 * e1 * e1 + C(2) * g12 * e1 * e2 + g22 * e2 * e2);
     }
-    *prev1 = double(u1);
-    *prev2 = double(u2);
+    *prev1 = u1;
+    *prev2 = u2;
     t.uu_j = J * t.uu;
     t.ls = c.ls;
     t.ls1 = c.ls1;
     t.ls2 = c.ls2;
     t.ke = C(0.5) * J * c.rho * t.uu;
-    t.am = J * c.rho * (C(ge[Geo::M1]) * u1 + C(ge[Geo::M2]) * u2);
+    t.am = J * c.rho * (tb.s(T::AM1) * u1 + tb.s(T::AM2) * u2);
     t.bad = !(c.rho > C(0) && isfinite(c.rho) && isfinite(t.uu));
-    t.rest = ge[Geo::J] * rho0;
     return t;
 }
 
@@ -312,14 +315,14 @@ __device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, cons
 // NRED: 0 dd, 1 |u|^2, 2 mass, 3-4 momentum, 5 kinetic energy, 6 angular
 // momentum, 7 largest |u|^2, 8 unstable cells).  FP64 compute sums in FP64;
 // FP32 compute sums with Kahan compensation in FP32 (the FP64 pipe is far
-// slower) and keeps the rest part of the mass in FP64.
+// slower).
 template <typename C> struct ResAcc;
 template <> struct ResAcc<double> {
     double v[NRED] = {};
     __device__ __forceinline__ void add(const CellTerms<double>& t) {
         v[0] += t.dd;
         v[1] += t.uu_j;
-        v[2] += t.rest + t.ls;
+        v[2] += t.ls;
         v[3] += t.ls1;
         v[4] += t.ls2;
         v[5] += t.ke;
@@ -334,7 +337,6 @@ template <> struct ResAcc<double> {
 template <> struct ResAcc<float> {
     float s[7] = {}, e[7] = {};
     float umax = 0.f, bad = 0.f;
-    double rest = 0.0;
     __device__ __forceinline__ void kahan(int k, float x) {
         const float y = x - e[k];
         const float t = s[k] + y;
@@ -351,11 +353,9 @@ template <> struct ResAcc<float> {
         kahan(6, t.am);
         umax = fmaxf(umax, t.uu);
         bad += t.bad ? 1.f : 0.f;
-        rest += t.rest;
     }
     __device__ __forceinline__ void out(double (&o)[NRED]) const {
         for (int k = 0; k < 7; ++k) o[k] = double(s[k]) - double(e[k]);
-        o[2] += rest;
         o[7] = umax;
         o[8] = bad;
         o[9] = 0.0;

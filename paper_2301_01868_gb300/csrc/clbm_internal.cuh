@@ -143,6 +143,10 @@ void launch_wall_copy(int prec, void* wall_rho, void* wall_ut2, const double* sr
                       double rho0, int ncol, cudaStream_t stream);
 void launch_wall_init(int prec, void* wall_rho, void* wall_ut2, const double* rho,
                       const double* ut2, int n1, int n2, int h, double rho0, cudaStream_t stream);
+// rho0 times the total volume of `count` geometry entries of `mult` cells
+// each, written to *out (device).
+void launch_rest_mass(int Q, const double* geo, int count, int mult, double rho0, double* out,
+                      cudaStream_t stream);
 // Eq. 23 on `count` geometry entries (rows, or cells of a general grid).
 void launch_scale_volume(int Q, double* geo, const double* rho_nf, int count, double rho0,
                          cudaStream_t stream);

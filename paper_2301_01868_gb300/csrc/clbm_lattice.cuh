@@ -87,7 +87,9 @@ template <int Q> struct Tab {
     static constexpr int INVJ = 0, J = 1, G11 = 2, G12 = 3, G22 = 4;
     static constexpr int F01 = 5, F02 = 6, P00 = 7, FI1 = 8, FI2 = 9;
     static constexpr int D0 = 10, M1 = 11, M2 = 12;
-    static constexpr int PB = 16;
+    // diagnostics only: covariant metric g_ij and angular-momentum weights
+    static constexpr int C11 = 13, C12 = 14, C22 = 15, AM1 = 16, AM2 = 17;
+    static constexpr int PB = 20;
     static constexpr int S = PB + 12 * Lat<Q>::NP;              // stride (multiple of 4)
     __host__ __device__ static constexpr int pa(int p) { return PB + 12 * p; }
     __host__ __device__ static constexpr int pb(int p) { return PB + 12 * p + 4; }
@@ -95,12 +97,12 @@ template <int Q> struct Tab {
 };
 
 // Per-cell table of a general grid, one plane of n1 n2 values per entry:
-// the Tab<Q> header values INVJ .. M2 at the same indices, then per pair the
+// the Tab<Q> header values INVJ .. AM2 at the same indices, then per pair the
 // contractions (a^1_a, a^2_a, a^1_b, a^2_b) and the pull offsets
 // (Delta_a, Delta_b); P0 and the dPi weights are formed when read.
 template <int Q>
 struct CellTabLayout {
-    static constexpr int NS = Tab<Q>::M2 + 1;                   // header values
+    static constexpr int NS = Tab<Q>::AM2 + 1;                  // header values
     __host__ __device__ static constexpr int pa(int q) { return NS + 6 * q; }
     __host__ __device__ static constexpr int pd(int q) { return NS + 6 * q + 4; }
     static constexpr int S = NS + 6 * Lat<Q>::NP;               // entries per cell

@@ -175,9 +175,9 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_batch_moments(const Batch
                 collide_emit<Q, C>(tb, c, kc, [](int, C) {});
             }
             const size_t m = (size_t)i * g.n2 + j, nc = (size_t)g.n1 * g.n2;
+            C* prev = (C*)g.prev;
             ResAcc<C> acc;
-            acc.add(residual_terms<Q, C>(c, g.geo + (size_t)i * Geo::stride(Q), g.k.rho0, g.prev + m,
-                                         g.prev + nc + m, g.have_prev != 0));
+            acc.add(residual_terms<Q, C>(c, tb, prev + m, prev + nc + m, g.have_prev != 0));
             acc.out(v);
         }
 #pragma unroll

@@ -120,6 +120,11 @@ __global__ void k_tables(const double* __restrict__ geo, C* __restrict__ tab, in
     t[T::G12] = C(g[Geo::GI12]);
     t[T::G22] = C(g[Geo::GI22]);
     t[T::P00] = C(rest_poly<Q>(0, g[Geo::GI11], g[Geo::GI12], g[Geo::GI22]));
+    t[T::C11] = C(g[Geo::G11]);
+    t[T::C12] = C(g[Geo::G12]);
+    t[T::C22] = C(g[Geo::G22]);
+    t[T::AM1] = C(g[Geo::M1]);
+    t[T::AM2] = C(g[Geo::M2]);
     // Pull offsets and the rest-state sums (FP64, rounded once).
     double dl[Q];
     double D0 = 0.0, M1 = 0.0, M2 = 0.0;
@@ -194,6 +199,11 @@ __global__ void k_tables_cell(const double* __restrict__ geo, C* __restrict__ ta
     put(T::G12, g[Geo::GI12]);
     put(T::G22, g[Geo::GI22]);
     put(T::P00, rest_poly<Q>(0, g[Geo::GI11], g[Geo::GI12], g[Geo::GI22]));
+    put(T::C11, g[Geo::G11]);
+    put(T::C12, g[Geo::G12]);
+    put(T::C22, g[Geo::G22]);
+    put(T::AM1, g[Geo::M1]);
+    put(T::AM2, g[Geo::M2]);
     double dl[Q];
     double D0 = 0.0, M1 = 0.0, M2 = 0.0;
 #pragma unroll

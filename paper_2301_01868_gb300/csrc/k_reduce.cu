@@ -9,12 +9,13 @@ namespace {
 
 constexpr int RB = 128;  // threads per block of the diagnostics kernels
 
-// Blocks of the residual reduction: one per (row, 128-column) item, up to
-// 65536 (each then takes a few items); the final reduction runs one block per
-// quantity over all block partials.
+// Persistent blocks of the residual reduction: eight per SM of a GB300,
+// never more than there are (row, 128-column) items.  Each thread then sums
+// many cells before the warp and block reductions, whose shuffles would
+// otherwise cost as much as the cells themselves.
 int residual_blocks(int n1, int n2) {
     const int items = n1 * ((n2 + RB - 1) / RB);
-    return items < 65536 ? items : 65536;
+    return items < 1216 ? items : 1216;
 }
 
 // Geometry row / cell of cell (i, j).
@@ -60,8 +61,8 @@ __global__ void __launch_bounds__(RB) k_moments(const MomArgs a, int iters) {
     if (a.F2) a.F2[m] = double(c.F2);
 }
 
-// Residual and conservation sums: blocks stride over (row, 128-column)
-// items; each thread accumulates its cells in a fixed order
+// Residual and conservation sums: persistent blocks stride over (row,
+// 128-column) items; each thread accumulates its cells in a fixed order
 // (ResAcc), then a warp-shuffle and block reduction in FP64 in a fixed tree
 // writes one partial per block, so repeated runs give identical bits.  The
 // rest parts of the totals are exact per row: sum_a ref_a(i) = J rho0 and
@@ -79,8 +80,9 @@ __global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, 
         Cell<Q, C> c;
         cell_moments<Q, S, C, ITER, GEN>(a, iters, i, j, c);
         const size_t m = (size_t)i * a.n2 + j;
-        acc.add(residual_terms<Q, C>(c, geo_of(a.geo, Q, a.ncol, i, j), a.k.rho0, a.ut_prev + m,
-                                     a.ut_prev + nc + m, a.have_prev != 0));
+        C* prev = (C*)a.ut_prev;
+        acc.add(residual_terms<Q, C>(c, TabOf<Q, C, GEN>::at(a.tab, i, j, a.n1, a.n2), prev + m, prev + nc + m,
+                                     a.have_prev != 0));
     }
     double v[NRED];
     acc.out(v);
@@ -187,6 +189,22 @@ __global__ void k_wall_copy(C* __restrict__ wr, C* __restrict__ wu, const double
     const size_t m = (size_t)wk * n2 + j;
     wr[m] = C(sr[m] * (rnf ? rho0 / rnf[(size_t)row * ncol + (ncol > 1 ? j : 0)] : 1.0));
     wu[m] = C(su[m]);
+}
+
+// Rest part of the total mass, rho0 times the total volume: FP64, one block,
+// fixed order; each geometry entry covers `mult` cells (n2 for row geometry).
+__global__ void __launch_bounds__(256) k_rest_mass(const double* __restrict__ geo, int stride, int count,
+                                                   double mult, double rho0, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double x = 0.0;
+    for (int e = threadIdx.x; e < count; e += 256) x += geo[(size_t)e * stride + Geo::J];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] * mult * rho0;
 }
 
 // Eq. 23, J <- J rho_nf / rho0, for every geometry entry (rows, or cells of a
@@ -306,6 +324,11 @@ void launch_wall_copy(int prec, void* wr, void* wu, const double* sr, const doub
     dim3 b(128), g((n2 + 127) / 128, 2 * h);
     if (prec == 0) k_wall_copy<double><<<g, b, 0, s>>>((double*)wr, (double*)wu, sr, su, rnf, n1, n2, h, rho0, ncol);
     else k_wall_copy<float><<<g, b, 0, s>>>((float*)wr, (float*)wu, sr, su, rnf, n1, n2, h, rho0, ncol);
+}
+
+void launch_rest_mass(int Q, const double* geo, int count, int mult, double rho0, double* out,
+                      cudaStream_t s) {
+    k_rest_mass<<<1, 256, 0, s>>>(geo, Geo::stride(Q), count, double(mult), rho0, out);
 }
 
 void launch_scale_volume(int Q, double* geo, const double* rnf, int count, double rho0, cudaStream_t s) {

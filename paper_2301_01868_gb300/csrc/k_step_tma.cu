@@ -469,15 +469,18 @@ template <int Q, typename S, typename C>
 __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     k_batch_ws(const BatchGrid* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                const int4* __restrict__ work, int nwork, int parity, int* err) {
+    const CUtensorMap* fenced = nullptr;  // producer: maps acquired last
     ws_pipeline<Q, S, C>(nwork, err, [&](int e) {
         const int4 w = work[e];
         const BatchGrid& g = grids[w.x];
         const int src = g.parity ^ parity;
         const CUtensorMap* ld8 = maps + ((size_t)w.x * 2 + src) * 8;
-        if ((threadIdx.x & 31) == 0 && threadIdx.x / 32 == PipeGeom<Q, S>::CONSUMERS)
+        if (ld8 != fenced && (threadIdx.x & 31) == 0 && threadIdx.x / 32 == PipeGeom<Q, S>::CONSUMERS) {
             for (int q = 0; q < 8; ++q)
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ld8 + q)
                              : "memory");
+            fenced = ld8;
+        }
         const WsLattice<S> lat{(S*)g.phys[src ^ 1], g.ghost, g.wall_rho, g.wall_ut2, g.plane, g.ld,
                                g.n1, g.n2, g.bc_lo, g.bc_hi, g.U0_lo, g.U0_hi};
         return WsTile<Q, S, C>{ld8, (const C*)g.tab, lat, Consts<C>::make(g.k), w.y, w.z};
