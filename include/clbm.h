@@ -164,10 +164,12 @@ clbm_status clbm_time(clbm_handle h, long long* t);
 /* Change the stream the grid's work is issued on. */
 clbm_status clbm_set_stream(clbm_handle h, void* stream);
 
-/* When on, clbm_step records a CUDA event pair around every launch of the
- * fused update; clbm_kernel_time returns their summed duration (ms) and the
- * launch count since the last reset, and resets.  Synchronises. */
-clbm_status clbm_set_profiling(clbm_handle h, int on);
+/* period > 0: clbm_step records a CUDA event pair around every period-th
+ * launch of the fused update (1: every launch; a larger period keeps the
+ * events' own cost out of the timed stream); period 0 switches it off.
+ * clbm_kernel_time returns the recorded launches' summed duration (ms) and
+ * their count since the last reset, and resets.  Synchronises. */
+clbm_status clbm_set_profiling(clbm_handle h, int period);
 clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
 
 /* Kernel of the bulk update: 0 automatic (variant 3 where available, else 1),

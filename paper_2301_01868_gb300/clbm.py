@@ -260,8 +260,9 @@ class Grid:
         _check(lib().clbm_no_flow_adjust(self._h, int(nsteps), rho_nf.ctypes.data))
         return rho_nf
 
-    def set_profiling(self, on=True):
-        _check(lib().clbm_set_profiling(self._h, int(bool(on))))
+    def set_profiling(self, on=True, period=1):
+        """Time every period-th update launch with CUDA events (on=False: stop)."""
+        _check(lib().clbm_set_profiling(self._h, int(period) if on else 0))
 
     def kernel_time(self):
         """(ms, launches) of the fused update since profiling was switched on."""

@@ -62,6 +62,8 @@ struct clbm_grid {
     long long t, t_prev, launches;
     bool have_prev;
     bool profiling;
+    int prof_period;        // record every prof_period-th update launch
+    long long prof_count;   // update launches since profiling was switched on
     std::vector<cudaEvent_t> ev;
     size_t ev_used;
     std::vector<double> edges;
@@ -528,7 +530,8 @@ clbm_status clbm_step(clbm_handle g, long long n) {
     fill_ghosts(g);
     for (long long s = 0; s < n; ++s) {
         StepArgs a = step_args(g, g->stA, g->stB);
-        if (g->profiling) {
+        const bool timed = g->profiling && g->prof_count++ % g->prof_period == 0;
+        if (timed) {
             if (g->ev_used + 2 > g->ev.size()) {
                 for (int k = 0; k < 256; ++k) {
                     cudaEvent_t e;
@@ -545,7 +548,7 @@ clbm_status clbm_step(clbm_handle g, long long n) {
         } else {
             launch_step(g->Q, g->prec, a, g->stream);
         }
-        if (g->profiling) {
+        if (timed) {
             CK(cudaEventRecord(g->ev[g->ev_used + 1], g->stream));
             g->ev_used += 2;
         }
@@ -717,9 +720,12 @@ clbm_status clbm_set_stream(clbm_handle g, void* stream) {
     return CLBM_OK;
 }
 
-clbm_status clbm_set_profiling(clbm_handle g, int on) {
+clbm_status clbm_set_profiling(clbm_handle g, int period) {
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
-    g->profiling = on != 0;
+    if (period < 0) return fail(CLBM_EINVAL, "period < 0");
+    g->profiling = period > 0;
+    g->prof_period = period > 0 ? period : 1;
+    g->prof_count = 0;
     g->ev_used = 0;
     return CLBM_OK;
 }
