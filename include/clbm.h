@@ -130,8 +130,10 @@ clbm_status clbm_set_state(clbm_handle h, const double* Np, const double* rho_pr
  * Synchronises. */
 clbm_status clbm_get_state(clbm_handle h, double* Np, int dst_is_device);
 
-/* Advance n time steps (boundary fill, then the fused stream-collide-force
- * update, per step).  Asynchronous on the grid's stream. */
+/* Advance n time steps: one launch of the fused stream-collide-force update
+ * per step, which also writes the ghost rows (App. B) and periodic ghost
+ * columns of the buffer it fills; the ghosts are rebuilt once first when the
+ * state or case was set since.  Asynchronous on the grid's stream. */
 clbm_status clbm_step(clbm_handle h, long long n);
 
 /* Moments of the current state, i.e. of the post-advection populations
@@ -146,16 +148,21 @@ clbm_status clbm_moments(clbm_handle h, double* rho, double* U1, double* U2,
  * angular momentum).  res = ||u(t) - u(t')||_J / ((t - t') ||u(t)||_J) with
  * physical u = Ut^k g_k and t' the time of the previous call (+inf on the
  * first call).  cons = {sum N', sum c^1 N', sum c^2 N', kinetic energy
- * 1/2 sum J rho |u|^2, angular momentum sum J rho (x cross u) (POLAR, else 0),
- * max |u|}.  Returns CLBM_EUNSTABLE if a density is not finite and positive.
- * Synchronises. */
+ * 1/2 sum J rho |u|^2, angular momentum sum J rho (x cross u) about the
+ * origin (POLAR and GENERAL, else 0), max |u|}.  Per-cell terms are formed in
+ * the compute type and summed in FP64 (FP32 compute: a thread's cells with
+ * Kahan compensation in FP32 first).  Returns CLBM_EUNSTABLE if a density is
+ * not finite and positive, CLBM_ETIMEOUT if a bounded device wait of an
+ * earlier update gave up.  Synchronises. */
 clbm_status clbm_residual(clbm_handle h, double* res, double cons[6]);
 
 /* "No flow" adjustment (Sec. 3.1, Eq. 23): in FP64, run the grid from rest
- * with U0 = 0 and no body force for nsteps, then J <- J rho_nf / rho0 per
- * row, and leave the state at that no-flow solution (a fixed point of the
- * adjusted update).  rho_nf (host, may be NULL) receives the no-flow density
- * [n1][n2].  Requires a prior clbm_set_case.  Synchronises. */
+ * with U0 = 0 and no body force for nsteps, then J <- J rho_nf / rho0 (per
+ * row on planar and polar grids, where the no-flow state does not depend on
+ * j; per cell on general grids), and leave the state at that no-flow
+ * solution (a fixed point of the adjusted update).  rho_nf (host, may be
+ * NULL) receives the no-flow density [n1][n2].  Requires a prior
+ * clbm_set_case.  Synchronises. */
 clbm_status clbm_no_flow_adjust(clbm_handle h, long long nsteps, double* rho_nf);
 
 /* Time step counter t. */
