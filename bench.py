@@ -480,16 +480,18 @@ def run_batch(args):
 def run_e2e(g, args, torch, stream, world, dist, cells, Q):
     """Same metric through the public API with host buffers: every step
     uploads the state N' from pinned host memory, advances `chunk` time steps
-    and reads the moments rho, Ut^1, Ut^2 back to pinned host memory."""
+    and reads the moments rho, Ut^1, Ut^2 back into pinned host memory."""
     n1, n2 = g.n1, g.n2
     host_state = torch.empty((Q, n1, n2), dtype=torch.float64, pin_memory=True)
     host_state.copy_(g.state(device=True).cpu())
     state_np = host_state.numpy()
+    names = ("rho", "Ut1", "Ut2")
+    pinned = {k: torch.empty((n1, n2), dtype=torch.float64, pin_memory=True).numpy() for k in names}
 
     def one():
         g.set_state(state_np)
         g.step(args.chunk)
-        return g.moments(names=("rho", "Ut1", "Ut2"))
+        return g.moments(names=names, out=pinned)
 
     one()
     torch.cuda.synchronize()

@@ -234,11 +234,15 @@ class Grid:
         return v.value
 
     # diagnostics --------------------------------------------------------------
-    def moments(self, device=False, names=("rho", "U1", "U2", "Ut1", "Ut2", "F1", "F2")):
-        """Moments of the current state (what the next collision uses)."""
+    def moments(self, device=False, names=("rho", "U1", "U2", "Ut1", "Ut2", "F1", "F2"), out=None):
+        """Moments of the current state (what the next collision uses).  out:
+        optional dict of preallocated (n1, n2) float64 arrays (host, e.g. views
+        of pinned memory, or device tensors when device=True) to fill."""
         all_names = ("rho", "U1", "U2", "Ut1", "Ut2", "F1", "F2")
-        out = {}
+        out = dict(out) if out else {}
         for k in names:
+            if k in out:
+                continue
             if device:
                 out[k] = self._torch.empty((self.n1, self.n2), dtype=self._torch.float64,
                                            device=self.device)

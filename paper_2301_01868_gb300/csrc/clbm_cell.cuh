@@ -400,7 +400,9 @@ __device__ __forceinline__ C ghost_value(C x, const double* __restrict__ gt, C r
 // Periodic ghost column of interior column j when a row has at least 2 GC
 // columns: one copy, at column j + n2 (j < GC) or j - n2 (j >= n2 - GC), as
 // an offset from j; 0 when the cell has none.  Updates store it next to the
-// cell's own value.  Shorter rows need several copies: EdgeFill makes them.
+// cell's own value as it is produced (a read-back after the stores would
+// hold the warp for a round trip).  Shorter rows need several copies:
+// EdgeFill makes them.
 __device__ __forceinline__ int wrap_offset(int j, int n2) {
     if (n2 < 2 * GC) return 0;
     return j < GC ? n2 : (j >= n2 - GC ? -n2 : 0);
@@ -414,14 +416,14 @@ __device__ __forceinline__ int wrap_offset(int j, int n2) {
 // wall; * and hat are involutions), with the moving-wall correction from the
 // cell's own rho and Ut^2.  The values are those the boundary kernel would
 // compute from the stored state.  With own_wrap (rows shorter than 2 GC in
-// the per-cell kernels) it also makes the periodic ghost columns of the
-// cell's own row.
+// the kernels that store cells one by one) it also makes the periodic ghost
+// columns of the cell's own row.  needed(): the cells that have something
+// to fill.
 //
 // Called once per edge cell after the collision with vp pointing at the
 // cell's new stored N'_0 (N'_b at vp + b vstride, in global or shared
-// memory): a loop over b, not unrolled, in a function of its own, since edge
-// rows are few and the interior update should keep its registers and code
-// small.
+// memory), in a function of its own, since edge rows are few and the
+// interior update should keep its registers and code small.
 template <int Q, typename S>
 struct EdgeFill {
     using C = typename Store<S>::C;
@@ -439,9 +441,14 @@ struct EdgeFill {
 
     __device__ __noinline__ void fill(int i, int j, const S* vp, long long vstride, C rho, C ut2) const {
         constexpr int H = Lat<Q>::H;
-#pragma unroll 1
+        // all read-backs first (independent loads in flight together), then
+        // the stores; unrolled so that every direction's maps fold
+        C vb[Q];
+#pragma unroll
+        for (int b = 0; b < Q; ++b) vb[b] = Store<S>::lds(vp + b * vstride);
+#pragma unroll
         for (int b = 0; b < Q; ++b) {
-            const C v = Store<S>::lds(vp + b * vstride);
+            const C v = vb[b];
             if (own_wrap) store_wrap<S, C>(st + b * plane + (long long)(i + H) * ld, j, n2, v);
             if (i < H) {
                 const int k = i + 1;

@@ -306,8 +306,9 @@ struct WsLattice {
 };
 
 // One consumer thread's cell (i0 + r, j0 + cc) of a tile staged in shared
-// memory: pull, collide, store straight to global memory (plus the periodic
-// copy and, next to a wall, the ghost values it supplies), wall moments.
+// memory: pull, collide, store straight to global memory (plus, next to a
+// periodic end or a wall, the copies and ghost values it supplies), wall
+// moments.
 template <int Q, typename S, typename C>
 __device__ __forceinline__ void ws_update_cell(const WsLattice<S>& L, const Consts<C>& k, const S* in,
                                                const C* tab_rows, int i0, int j0, int r, int cc) {
