@@ -1,0 +1,94 @@
+"""Resolution ladders on the GPU, run to a steady state, against the exact
+profiles of the paper's flows (Sec. 3):
+
+* planar Poiseuille (Eqs. 24-25) on the geometrically stretched channel of
+  the planar configuration, D2Q21, tau = 1, stretch 1.02^(64 / n1) per cell
+  and g = 1e-6 (64 / n1)^2 (the same total stretch and peak speed on every
+  rung), n1 x n2 = 64 x 16, 128 x 32, 256 x 64, FP64 and FP32;
+* circular Couette (Eq. 27) in the annulus 1 <= r <= 2, uniform radial grid,
+  N_theta = round(2 pi N_r), tau = 0.8, inner wall at 0.01, D2Q21 at
+  N_r = 32, 64, 128 (D2Q9 at 32 and 64 beside it).
+
+Run with -s to see the tables (lines starting LADDER).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import clbm_inputs as I
+from oracle import exact as E
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _clbm():
+    from paper_2301_01868_gb300 import clbm
+    return clbm
+
+
+def run_to_steady(g, tol, chunk, max_steps):
+    g.residual()
+    steps = 0
+    res = math.inf
+    while steps < max_steps:
+        g.step(chunk)
+        steps += chunk
+        res, _ = g.residual()
+        if res <= tol:
+            break
+    return steps, res
+
+
+def l2rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-8)])
+def test_planar_poiseuille_ladder_converges_at_second_order(prec, tol):
+    c = _clbm()
+    tau, T0 = 1.0, 2.0 / 3.0
+    nu = E.nu_of_tau(tau, T0)
+    errs = []
+    for n1, n2 in ((64, 16), (128, 32), (256, 64)):
+        e = I.geometric_stretch_edges(n1, 1.02 ** (64.0 / n1), float(n1))
+        gacc = 1e-6 * (64.0 / n1) ** 2
+        g = c.Grid(21, n1, n2, e, kind=c.PLANAR, step2=1.0, precision=prec)
+        g.set_case(tau, 1.0, 0.0, 0.0, (0.0, gacc))
+        steps, res = run_to_steady(g, tol, 1000, 600000)
+        u = g.moments(names=("Ut2",))["Ut2"][:, 0]
+        x = 0.5 * (e[:-1] + e[1:])
+        err = l2rel(u, E.planar_poiseuille(x, float(n1), gacc, nu))
+        errs.append(err)
+        print("\nLADDER planar Poiseuille D2Q21 %s %dx%d stretch %.4f: %d steps, residual %.1e, "
+              "L2 error vs exact %.3e" % (prec, n1, n2, 1.02 ** (64.0 / n1), steps, res, err))
+        g.close()
+        assert res <= tol
+    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0
+
+
+def test_circular_couette_ladder_d2q21_converges_and_beats_d2q9():
+    c = _clbm()
+    R1, R2, uw, tau = 1.0, 2.0, 0.01, 0.8
+    errs = {}
+    for Q, rungs in ((21, (32, 64, 128)), (9, (32, 64))):
+        for Nr in rungs:
+            Nt = I.n_theta(Nr, R1, R2)
+            e = I.polar_edges(R1, R2, Nr)
+            dx = (R2 - R1) / Nr
+            M = R1 / dx
+            g = c.Grid(Q, Nr, Nt, e, kind=c.POLAR, precision="fp64", bc_lo=c.MOVING, bc_hi=c.NOSLIP)
+            g.set_case(tau, 1.0, c.wall_speed_polar(uw, R1, Nt, dx), 0.0)
+            steps, res = run_to_steady(g, 1e-10, 1000, 400000)
+            r_lat = 0.5 * (e[:-1] + e[1:]) / dx
+            u = g.moments(names=("Ut2",))["Ut2"][:, 0] * math.sin(2.0 * math.pi / Nt) * r_lat
+            ex = E.Annulus.couette(M, M + Nr, uw / M).u(r_lat)
+            errs[(Q, Nr)] = l2rel(u, ex)
+            print("\nLADDER circular Couette D2Q%d fp64 %dx%d: %d steps, residual %.1e, "
+                  "L2 error vs exact %.3e" % (Q, Nr, Nt, steps, res, errs[(Q, Nr)]))
+            g.close()
+    assert errs[(21, 64)] < errs[(21, 32)] and errs[(21, 128)] < errs[(21, 64)]
+    for Nr in (32, 64):
+        assert errs[(21, Nr)] < errs[(9, Nr)]
