@@ -59,10 +59,16 @@ KERNEL_SOURCES = ["paper_2301_01868_gb300/csrc/k_step.cu",
 
 
 def kernel_hash():
+    """Hash of the update kernels' code (comments and blank space left out, so
+    that only a change of the code makes a captured traffic figure stale)."""
+    import re
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

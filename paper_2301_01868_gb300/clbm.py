@@ -276,7 +276,9 @@ class Grid:
         return ms.value, n.value
 
     def set_kernel(self, variant):
-        """0 automatic, 1 one thread per cell, 2 TMA-staged tiles."""
+        """0 automatic, 1 one thread per cell, 2 TMA-staged tiles with a shared
+        output tile, 3 TMA-staged warp-specialised pipeline (the automatic
+        choice where the grid has TMA maps)."""
         _check(lib().clbm_set_kernel(self._h, int(variant)))
 
     def launch_count(self):
@@ -314,6 +316,8 @@ class Batch:
         return res, cons
 
     def set_variant(self, v):
+        """0-3: one thread per cell with tiles 128x1, 256x1 (2 per thread),
+        32x4, 64x1; 4: the pipelined TMA update over 64x8 tiles."""
         _check(lib().clbm_batch_set_variant(self._h, int(v)))
 
     def tune(self, steps=5):

@@ -4,15 +4,23 @@
 // persistent CTAs, one per SM, walk tiles of TR x TJ cells.  For every tile
 // one thread issues one TMA box per population: rows [i0 - max(c1,0),
 // i0 + TR + max(-c1,0)) and the columns the pull reaches (8-column halo only
-// where c2 != 0), so each population plane brings exactly the rows and columns
-// its pull and its lagged read touch (about 1.33 x the tile for D2Q21).  Tiles
-// are double buffered behind mbarriers, so the loads of tile k+1 overlap the
-// arithmetic of tile k.  Every shared-memory offset of a pull is a compile-time
-// constant.  New populations go to a shared output tile that one TMA store
-// writes back; cells at the periodic ends store their periodic copies, the
-// cells after the last whole 16-byte chunk of a row store themselves, and
-// cells next to a wall write the ghost values they supply (EdgeFill).  Waits on mbarriers are bounded: on time-out the kernel records
-// an error code and returns.
+// where c2 != 0), so each population plane brings exactly the rows and
+// columns its pull and its lagged read touch (about 1.33 x the tile for
+// D2Q21), plus the tile's table rows by a bulk copy.  Every shared-memory
+// offset of a pull is a compile-time constant.  Two kernels share this:
+//
+// k_fused_ws (default): a producer warp fills three stages; 16 consumer
+//   warps each update 32 cells of a tile row and store straight to global
+//   memory; full / empty mbarriers per stage, no CTA-wide barrier in the
+//   tile loop.  k_batch_ws runs the same loop over the tiles of a batch.
+// k_fused_tma: one elected thread, two stages, CTA-wide barriers, and a
+//   shared output tile written back by one TMA store; the CTA copies the
+//   periodic ghost columns and the ragged tail from that tile.
+//
+// Cells next to a wall write the ghost values they supply (EdgeFill).  Waits
+// on mbarriers are bounded: on time-out the kernel records an error code,
+// the other warps give up at their next wait, and loads in flight land
+// before the CTA exits.
 #include <cuda.h>
 
 #include <cstring>
