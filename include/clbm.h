@@ -242,6 +242,23 @@ clbm_status clbm_batch_launch_count(clbm_batch_handle b, long long* launches);
 clbm_status clbm_batch_destroy(clbm_batch_handle b);
 
 /* Free everything the grid owns.  NULL is accepted. */
+/* Checkpoint / resume.  clbm_checkpoint copies the grid's case and dynamic
+ * state -- the current population buffer as stored (deviations in the
+ * storage type, ghost rows and columns included), the wall moments of the
+ * last collision, the residual snapshot, the geometry (which holds a no-flow
+ * adjustment of J) and the time counters -- into buf (host memory of
+ * clbm_checkpoint_bytes bytes, caller-owned; a set case is required).
+ * clbm_restore loads it into a grid created with the same description (no
+ * clbm_set_case needed; the saved case replaces the grid's); stepping then
+ * continues bit for bit as the saved grid would have, with the same kernel
+ * choice.  CLBM_EINVAL if lattice, precision or size differ.  The buffer is
+ * machine-native (no byte-order conversion).  The paper has no counterpart:
+ * runs to steady state are long, and a step cap or a failure need not lose
+ * them.  Both synchronise. */
+clbm_status clbm_checkpoint_bytes(clbm_handle h, size_t* bytes);
+clbm_status clbm_checkpoint(clbm_handle h, void* buf);
+clbm_status clbm_restore(clbm_handle h, const void* buf);
+
 clbm_status clbm_destroy(clbm_handle h);
 
 /* Thread-local message of the last failing call ("" if none). */

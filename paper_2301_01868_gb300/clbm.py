@@ -74,6 +74,9 @@ def lib():
             "clbm_kernel_time": [h, dp, C.POINTER(ll)],
             "clbm_launch_count": [h, C.POINTER(ll)],
             "clbm_set_kernel": [h, C.c_int],
+            "clbm_checkpoint_bytes": [h, C.POINTER(C.c_size_t)],
+            "clbm_checkpoint": [h, vp],
+            "clbm_restore": [h, vp],
             "clbm_batch_create": [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)],
             "clbm_batch_step": [h, ll],
             "clbm_batch_residual": [h, vp, vp],
@@ -226,6 +229,25 @@ class Grid:
 
     def step(self, n=1):
         _check(lib().clbm_step(self._h, int(n)))
+
+    def checkpoint(self):
+        """The case and dynamic state (raw state buffer, wall moments, residual
+        snapshot, geometry, time) as bytes; restore() continues from it bit
+        for bit."""
+        n = C.c_size_t()
+        _check(lib().clbm_checkpoint_bytes(self._h, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().clbm_checkpoint(self._h, buf.ctypes.data))
+        return buf.tobytes()
+
+    def restore(self, blob):
+        """Load a checkpoint() of a grid with the same description."""
+        buf = np.frombuffer(blob, dtype=np.uint8)
+        n = C.c_size_t()
+        _check(lib().clbm_checkpoint_bytes(self._h, C.byref(n)))
+        if buf.size != n.value:
+            raise ClbmError("checkpoint is %d bytes, this grid's are %d" % (buf.size, n.value))
+        _check(lib().clbm_restore(self._h, buf.ctypes.data))
 
     @property
     def t(self):

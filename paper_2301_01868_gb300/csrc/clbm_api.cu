@@ -11,6 +11,8 @@
 #include <mutex>
 #include <tuple>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/clbm.h"
 #include "clbm_batch.cuh"
 #include "clbm_internal.cuh"
@@ -18,6 +20,13 @@
 using namespace clbm;
 
 namespace {
+
+// NVTX range over one API call (visible in Nsight timelines; free when no
+// tool is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 thread_local char g_err[512] = "";
 
@@ -284,6 +293,7 @@ clbm_status clbm_workspace_bytes(const clbm_grid_desc* desc, size_t* bytes) {
 }
 
 clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
+    Range nvtx_range("clbm_create_grid");
     g_err[0] = 0;
     if (!out) return fail(CLBM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -427,6 +437,7 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
 }
 
 clbm_status clbm_set_case(clbm_handle g, const clbm_case* c) {
+    Range nvtx_range("clbm_set_case");
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
     clbm_status st = check_case(c);
     if (st != CLBM_OK) return st;
@@ -450,6 +461,7 @@ clbm_status clbm_set_case(clbm_handle g, const clbm_case* c) {
 
 clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_prev,
                            const double* ut2_prev, int src_is_device) {
+    Range nvtx_range("clbm_set_state");
     if (!g || !Np) return fail(CLBM_EINVAL, "handle or Np is NULL");
     if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
     clbm_status st = select(g);
@@ -499,6 +511,7 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
 }
 
 clbm_status clbm_get_state(clbm_handle g, double* Np, int dst_is_device) {
+    Range nvtx_range("clbm_get_state");
     if (!g || !Np) return fail(CLBM_EINVAL, "handle or Np is NULL");
     clbm_status st = select(g);
     if (st != CLBM_OK) return st;
@@ -522,6 +535,7 @@ clbm_status clbm_get_state(clbm_handle g, double* Np, int dst_is_device) {
 }
 
 clbm_status clbm_step(clbm_handle g, long long n) {
+    Range nvtx_range("clbm_step");
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
     if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
     if (n < 0) return fail(CLBM_EINVAL, "n < 0");
@@ -564,6 +578,7 @@ clbm_status clbm_step(clbm_handle g, long long n) {
 
 clbm_status clbm_moments(clbm_handle g, double* rho, double* U1, double* U2, double* Ut1,
                          double* Ut2, double* F1, double* F2, int dst_is_device) {
+    Range nvtx_range("clbm_moments");
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
     if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
     clbm_status st = select(g);
@@ -601,6 +616,7 @@ clbm_status clbm_moments(clbm_handle g, double* rho, double* U1, double* U2, dou
 }
 
 clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
+    Range nvtx_range("clbm_residual");
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
     if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
     clbm_status st = select(g);
@@ -633,6 +649,7 @@ clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
 }
 
 clbm_status clbm_no_flow_adjust(clbm_handle g, long long nsteps, double* rho_nf) {
+    Range nvtx_range("clbm_no_flow_adjust");
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
     if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
     if (nsteps < 0) return fail(CLBM_EINVAL, "nsteps < 0");
@@ -759,6 +776,108 @@ clbm_status clbm_set_kernel(clbm_handle g, int variant) {
 clbm_status clbm_launch_count(clbm_handle g, long long* launches) {
     if (!g || !launches) return fail(CLBM_EINVAL, "NULL argument");
     *launches = g->launches;
+    return CLBM_OK;
+}
+
+// Checkpoint: header (sizes, case, time counters), then the raw current state
+// buffer (ghosts included), the wall moments of the last collision, the
+// residual snapshot and the geometry (which carries a no-flow adjustment of J).
+struct CkptHeader {
+    char magic[8];
+    int Q, prec, n1, n2, ld, ncol;
+    long long t, t_prev;
+    int have_prev;
+    clbm_case cs;
+    size_t state_bytes, wall_bytes, prev_bytes, geo_bytes;
+};
+
+static void ckpt_sizes(const clbm_grid* g, CkptHeader* h) {
+    memset(h, 0, sizeof(*h));
+    memcpy(h->magic, "CLBMCKP1", 8);
+    h->Q = g->Q;
+    h->prec = g->prec;
+    h->n1 = g->n1;
+    h->n2 = g->n2;
+    h->ld = g->ld;
+    h->ncol = g->ncol;
+    h->t = g->t;
+    h->t_prev = g->t_prev;
+    h->have_prev = g->have_prev ? 1 : 0;
+    h->cs = g->cs;
+    h->state_bytes = g->L.stB - g->L.stA;
+    h->wall_bytes = g->L.wall_u - g->L.wall_r;
+    h->prev_bytes = (size_t)2 * g->n1 * g->n2 * 8;
+    h->geo_bytes = (size_t)g->n1 * g->ncol * Geo::stride(g->Q) * 8;
+}
+
+clbm_status clbm_checkpoint_bytes(clbm_handle g, size_t* bytes) {
+    if (!g || !bytes) return fail(CLBM_EINVAL, "NULL argument");
+    CkptHeader h;
+    ckpt_sizes(g, &h);
+    *bytes = sizeof(h) + h.state_bytes + 2 * h.wall_bytes + h.prev_bytes + h.geo_bytes;
+    return CLBM_OK;
+}
+
+clbm_status clbm_checkpoint(clbm_handle g, void* buf) {
+    Range nvtx_range("clbm_checkpoint");
+    if (!g || !buf) return fail(CLBM_EINVAL, "NULL argument");
+    if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    fill_ghosts(g);  // the saved buffer is complete, ghosts included
+    CkptHeader h;
+    ckpt_sizes(g, &h);
+    char* p = (char*)buf;
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    CK(cudaMemcpyAsync(p, g->stA, h.state_bytes, cudaMemcpyDeviceToHost, g->stream));
+    p += h.state_bytes;
+    CK(cudaMemcpyAsync(p, g->wall_r, h.wall_bytes, cudaMemcpyDeviceToHost, g->stream));
+    p += h.wall_bytes;
+    CK(cudaMemcpyAsync(p, g->wall_u, h.wall_bytes, cudaMemcpyDeviceToHost, g->stream));
+    p += h.wall_bytes;
+    CK(cudaMemcpyAsync(p, g->prev, h.prev_bytes, cudaMemcpyDeviceToHost, g->stream));
+    p += h.prev_bytes;
+    CK(cudaMemcpyAsync(p, g->geo, h.geo_bytes, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return check_err(g);
+}
+
+clbm_status clbm_restore(clbm_handle g, const void* buf) {
+    Range nvtx_range("clbm_restore");
+    if (!g || !buf) return fail(CLBM_EINVAL, "NULL argument");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    CkptHeader h, mine;
+    memcpy(&h, buf, sizeof(h));
+    ckpt_sizes(g, &mine);
+    if (memcmp(h.magic, mine.magic, 8) != 0 || h.Q != mine.Q || h.prec != mine.prec || h.n1 != mine.n1 ||
+        h.n2 != mine.n2 || h.ld != mine.ld || h.ncol != mine.ncol || h.state_bytes != mine.state_bytes ||
+        h.wall_bytes != mine.wall_bytes || h.prev_bytes != mine.prev_bytes || h.geo_bytes != mine.geo_bytes)
+        return fail(CLBM_EINVAL, "checkpoint does not match this grid (lattice, precision or size)");
+    st = check_case(&h.cs);
+    if (st != CLBM_OK) return st;
+    const char* p = (const char*)buf + sizeof(h);
+    // the state goes into the first physical buffer, which becomes current
+    g->stA = g->phys[0];
+    g->stB = g->phys[1];
+    CK(cudaMemcpyAsync(g->stA, p, h.state_bytes, cudaMemcpyHostToDevice, g->stream));
+    p += h.state_bytes;
+    CK(cudaMemcpyAsync(g->wall_r, p, h.wall_bytes, cudaMemcpyHostToDevice, g->stream));
+    p += h.wall_bytes;
+    CK(cudaMemcpyAsync(g->wall_u, p, h.wall_bytes, cudaMemcpyHostToDevice, g->stream));
+    p += h.wall_bytes;
+    CK(cudaMemcpyAsync(g->prev, p, h.prev_bytes, cudaMemcpyHostToDevice, g->stream));
+    p += h.prev_bytes;
+    CK(cudaMemcpyAsync(g->geo, p, h.geo_bytes, cudaMemcpyHostToDevice, g->stream));
+    g->cs = h.cs;
+    g->have_case = true;
+    st = rebuild_tables(g);  // tables and rest mass of the restored geometry and case (synchronises)
+    if (st != CLBM_OK) return st;
+    g->t = h.t;
+    g->t_prev = h.t_prev;
+    g->have_prev = h.have_prev != 0;
+    g->ghosts_ok = true;
     return CLBM_OK;
 }
 
@@ -939,6 +1058,7 @@ void batch_advance(clbm_batch* b, long long n) {
 extern "C" {
 
 clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle* out) {
+    Range nvtx_range("clbm_batch_create");
     if (!grids || n < 1 || !out) return fail(CLBM_EINVAL, "need grids, n >= 1 and out");
     *out = nullptr;
     for (int k = 0; k < n; ++k) {
@@ -1068,6 +1188,7 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
 }
 
 clbm_status clbm_batch_step(clbm_batch_handle b, long long n) {
+    Range nvtx_range("clbm_batch_step");
     if (!b) return fail(CLBM_EINVAL, "batch is NULL");
     if (n < 0) return fail(CLBM_EINVAL, "n < 0");
     clbm_status st = select(b->g[0]);
@@ -1095,6 +1216,7 @@ clbm_status clbm_batch_step(clbm_batch_handle b, long long n) {
 }
 
 clbm_status clbm_batch_residual(clbm_batch_handle b, double* res, double* cons) {
+    Range nvtx_range("clbm_batch_residual");
     if (!b) return fail(CLBM_EINVAL, "batch is NULL");
     clbm_status st = select(b->g[0]);
     if (st != CLBM_OK) return st;
@@ -1149,6 +1271,7 @@ clbm_status clbm_batch_set_variant(clbm_batch_handle b, int variant) {
 }
 
 clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* ms_per_step) {
+    Range nvtx_range("clbm_batch_tune");
     if (!b || steps < 1) return fail(CLBM_EINVAL, "batch is NULL or steps < 1");
     clbm_status st = select(b->g[0]);
     if (st != CLBM_OK) return st;

@@ -4,10 +4,17 @@ profiles of the paper's flows (Sec. 3):
 * planar Poiseuille (Eqs. 24-25) on the geometrically stretched channel of
   the planar configuration, D2Q21, tau = 1, stretch 1.02^(64 / n1) per cell
   and g = 1e-6 (64 / n1)^2 (the same total stretch and peak speed on every
-  rung), n1 x n2 = 64 x 16, 128 x 32, 256 x 64, FP64 and FP32;
+  rung), n1 x n2 = 64 x 16, 128 x 32, 256 x 64, FP64 and FP32, each run for
+  14 decay times of the slowest mode (n1^2 / (pi^2 nu)), which leaves a
+  start-up remnant near 1e-6 of the profile: a residual threshold would stop
+  FP32 early, with a remnant that grows as n1^2;
 * circular Couette (Eq. 27) in the annulus 1 <= r <= 2, uniform radial grid,
   N_theta = round(2 pi N_r), tau = 0.8, inner wall at 0.01, D2Q21 at
-  N_r = 32, 64, 128 (D2Q9 at 32 and 64 beside it).
+  N_r = 32, 64, 128; D2Q9 at 32 and 64 beside it, with one implicit force
+  pass (the lagged force lets the inner-wall radial mode grow on this grid).
+  The paper finds D2Q9 converging to something other than the exact profile
+  and D2Q21 converging to it, slowly (Sec. 3, Sec. 4); here D2Q21 halves its
+  error per doubling.
 
 Run with -s to see the tables (lines starting LADDER).
 """
@@ -57,7 +64,11 @@ def test_planar_poiseuille_ladder_converges_at_second_order(prec, tol):
         gacc = 1e-6 * (64.0 / n1) ** 2
         g = c.Grid(21, n1, n2, e, kind=c.PLANAR, step2=1.0, precision=prec)
         g.set_case(tau, 1.0, 0.0, 0.0, (0.0, gacc))
-        steps, res = run_to_steady(g, tol, 1000, 600000)
+        steps = int(math.ceil(14.0 * n1 * n1 / (math.pi ** 2 * nu) / 1000.0)) * 1000
+        g.step(steps - 1000)
+        g.residual()
+        g.step(1000)
+        res, _ = g.residual()             # mean change per step over the last 1000
         u = g.moments(names=("Ut2",))["Ut2"][:, 0]
         x = 0.5 * (e[:-1] + e[1:])
         err = l2rel(u, E.planar_poiseuille(x, float(n1), gacc, nu))
@@ -80,7 +91,7 @@ def test_circular_couette_ladder_d2q21_converges_and_beats_d2q9():
             dx = (R2 - R1) / Nr
             M = R1 / dx
             g = c.Grid(Q, Nr, Nt, e, kind=c.POLAR, precision="fp64", bc_lo=c.MOVING, bc_hi=c.NOSLIP)
-            g.set_case(tau, 1.0, c.wall_speed_polar(uw, R1, Nt, dx), 0.0)
+            g.set_case(tau, 1.0, c.wall_speed_polar(uw, R1, Nt, dx), 0.0, force_iterations=int(Q == 9))
             steps, res = run_to_steady(g, 1e-10, 1000, 400000)
             r_lat = 0.5 * (e[:-1] + e[1:]) / dx
             u = g.moments(names=("Ut2",))["Ut2"][:, 0] * math.sin(2.0 * math.pi / Nt) * r_lat
@@ -89,6 +100,6 @@ def test_circular_couette_ladder_d2q21_converges_and_beats_d2q9():
             print("\nLADDER circular Couette D2Q%d fp64 %dx%d: %d steps, residual %.1e, "
                   "L2 error vs exact %.3e" % (Q, Nr, Nt, steps, res, errs[(Q, Nr)]))
             g.close()
-    assert errs[(21, 64)] < errs[(21, 32)] and errs[(21, 128)] < errs[(21, 64)]
+    assert errs[(21, 64)] < errs[(21, 32)] / 1.6 and errs[(21, 128)] < errs[(21, 64)] / 1.6
     for Nr in (32, 64):
-        assert errs[(21, Nr)] < errs[(9, Nr)]
+        assert errs[(21, Nr)] < errs[(9, Nr)] / 2.0
