@@ -126,6 +126,19 @@ clbm_status clbm_set_case(clbm_handle h, const clbm_case* cs);
 clbm_status clbm_set_state(clbm_handle h, const double* Np, const double* rho_prev,
                            const double* Ut2_prev, int src_is_device);
 
+/* Start from the local equilibrium of given macroscopic fields:
+ * N'(q,-1) = J f^eq(rho, U, Ut = U; g^{ij}(q)) with f^eq the third-order
+ * Hermite equilibrium of Eq. 19 (with no force known at the start Ut = U),
+ * formed on the device in FP64 and stored in the grid's precision; the
+ * moving-wall moments of the last collision are (rho, U^2) on the wall rows;
+ * t = 0.  rho, U1, U2: [n1][n2] FP64 (contravariant U^1, U^2, lattice units),
+ * host or device per src_is_device, caller-owned, read during the call; NULL
+ * gives rho0 / 0.  Starting a steady solve from the equilibrium of the exact
+ * or a coarser solution shortens the transient (the steady state does not
+ * depend on the start).  Requires clbm_set_case.  Synchronises. */
+clbm_status clbm_set_equilibrium(clbm_handle h, const double* rho, const double* U1,
+                                 const double* U2, int src_is_device);
+
 /* Read the state N'(q, t-1) as [Q][n1][n2] FP64 into host or device memory.
  * Synchronises. */
 clbm_status clbm_get_state(clbm_handle h, double* Np, int dst_is_device);

@@ -64,6 +64,7 @@ def lib():
             "clbm_set_case": [h, C.POINTER(_Case)],
             "clbm_set_state": [h, vp, vp, vp, C.c_int],
             "clbm_get_state": [h, vp, C.c_int],
+            "clbm_set_equilibrium": [h, vp, vp, vp, C.c_int],
             "clbm_step": [h, ll],
             "clbm_moments": [h, vp, vp, vp, vp, vp, vp, vp, C.c_int],
             "clbm_residual": [h, dp, dp],
@@ -216,6 +217,28 @@ class Grid:
         if arrs[0].shape != (self.Q, self.n1, self.n2):
             raise ValueError("state must be (Q, n1, n2)")
         _check(lib().clbm_set_state(self._h, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), int(dev)))
+
+    def set_equilibrium(self, rho=None, U1=None, U2=None):
+        """Start from J f^eq(rho, U, Ut = U) (Eq. 19) of the given fields:
+        contravariant U^1, U^2 and rho, each (n1, n2) or broadcastable to it
+        (e.g. an (n1, 1) wall-normal profile), numpy (host) or torch (either);
+        None gives rho0 / 0.  t restarts at 0."""
+        xs = [x for x in (rho, U1, U2) if x is not None]
+        dev = bool(xs) and _is_device(xs[0])
+        if any(_is_device(x) != dev for x in xs):
+            raise ValueError("rho, U1, U2 must all be on the host or all on the device")
+        arrs = []
+        for x in (rho, U1, U2):
+            if x is None:
+                arrs.append(None)
+            elif dev:
+                arrs.append(x.to(self._torch.float64).expand(self.n1, self.n2).contiguous())
+            else:
+                x = x.cpu().numpy() if hasattr(x, "cpu") else x
+                arrs.append(np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64),
+                                                                 (self.n1, self.n2))))
+        _check(lib().clbm_set_equilibrium(self._h, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
+                                          int(dev)))
 
     def state(self, device=False):
         """N'(q, t-1) as float64 (Q, n1, n2): numpy, or a torch CUDA tensor."""

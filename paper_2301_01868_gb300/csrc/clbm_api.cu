@@ -510,6 +510,44 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
     return CLBM_OK;
 }
 
+clbm_status clbm_set_equilibrium(clbm_handle g, const double* rho, const double* U1,
+                                 const double* U2, int src_is_device) {
+    Range nvtx_range("clbm_set_equilibrium");
+    if (!g) return fail(CLBM_EINVAL, "handle is NULL");
+    if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    const size_t nc = (size_t)g->n1 * g->n2;
+    double* sb = nullptr;
+    st = staging(g, &sb);
+    if (st != CLBM_OK) return st;
+    const double *dr = rho, *d1 = U1, *d2 = U2;
+    if (!src_is_device) {
+        // host fields go to the last three staging fields, which the
+        // equilibrium kernel overwrites cell by cell after reading them
+        double* f = sb + (size_t)(g->Q - 3) * nc;
+        const double* src[3] = {rho, U1, U2};
+        const double** dst[3] = {&dr, &d1, &d2};
+        for (int k = 0; k < 3; ++k) {
+            if (!src[k]) continue;
+            CK(cudaMemcpyAsync(f + k * nc, src[k], nc * 8, cudaMemcpyHostToDevice, g->stream));
+            *dst[k] = f + k * nc;
+        }
+    }
+    // wall moments of the "last collision": rho and Ut^2 of the start
+    launch_wall_init(g->prec, g->wall_r, g->wall_u, dr, d2, g->n1, g->n2, g->h, g->cs.rho0, g->stream);
+    launch_equilibrium(g->Q, dr, d1, d2, g->geo, sb, g->n1, g->n2, g->ncol, g->cs.rho0, g->stream);
+    launch_state_from_fp64(g->Q, g->prec, sb, g->geo, g->stA, g->n1, g->n2, g->ld, g->h, g->ncol,
+                           g->stream);
+    g->launches += 3;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(g->stream));
+    g->t = 0;
+    g->have_prev = false;
+    g->ghosts_ok = false;
+    return check_err(g);
+}
+
 clbm_status clbm_get_state(clbm_handle g, double* Np, int dst_is_device) {
     Range nvtx_range("clbm_get_state");
     if (!g || !Np) return fail(CLBM_EINVAL, "handle or Np is NULL");

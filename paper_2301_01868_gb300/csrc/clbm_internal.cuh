@@ -141,6 +141,9 @@ void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo,
 void launch_wall_copy(int prec, void* wall_rho, void* wall_ut2, const double* src_rho,
                       const double* src_ut2, const double* rho_nf, int n1, int n2, int h,
                       double rho0, int ncol, cudaStream_t stream);
+void launch_equilibrium(int Q, const double* rho, const double* U1, const double* U2,
+                        const double* geo, double* Np, int n1, int n2, int ncol, double rho0,
+                        cudaStream_t s);
 void launch_wall_init(int prec, void* wall_rho, void* wall_ut2, const double* rho,
                       const double* ut2, int n1, int n2, int h, double rho0, cudaStream_t stream);
 // rho0 times the total volume of `count` geometry entries of `mult` cells

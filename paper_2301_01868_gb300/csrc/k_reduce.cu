@@ -149,6 +149,46 @@ __global__ void k_from_fp64(const double* __restrict__ Np, const double* __restr
     }
 }
 
+// Equilibrium start N(q, 0) = J f^eq(rho, U, Ut = U; g^{ij}(q)) in FP64
+// (Eq. 19: the third-order Hermite polynomial whose second moment is
+// T0 g^{ij} + Ut^i Ut^j and whose third is built from Ut, U and g^{ij}; with
+// no force known at the start Ut = U).  Absent fields are rho0 and 0.  The
+// inputs may alias fields of the output: each thread reads its own cell's
+// rho, U before it writes that cell's Q values.
+template <int Q>
+__global__ void k_equilibrium(const double* rho, const double* U1, const double* U2,
+                              const double* __restrict__ geo, double* Np, int n1, int n2, int ncol,
+                              double rho0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= n2) return;
+    const size_t m = (size_t)i * n2 + j;
+    const double r = rho ? rho[m] : rho0;
+    const double u1 = U1 ? U1[m] : 0.0, u2 = U2 ? U2[m] : 0.0;
+    const double* ge = geo_of(geo, Q, ncol, i, j);
+    const double T0 = Lat<Q>::T0, J = ge[Geo::J];
+    const double e11 = ge[Geo::GI11] - 1.0, e12 = ge[Geo::GI12], e22 = ge[Geo::GI22] - 1.0;
+    // second- and third-order Hermite coefficients (symmetric)
+    const double A11 = u1 * u1 + T0 * e11, A12 = u1 * u2 + T0 * e12, A22 = u2 * u2 + T0 * e22;
+    const double C111 = u1 * u1 * u1 + 3.0 * T0 * e11 * u1;
+    const double C112 = u1 * u1 * u2 + T0 * (e11 * u2 + 2.0 * e12 * u1);
+    const double C122 = u1 * u2 * u2 + T0 * (2.0 * e12 * u2 + e22 * u1);
+    const double C222 = u2 * u2 * u2 + 3.0 * T0 * e22 * u2;
+    double out[Q];
+#pragma unroll
+    for (int al = 0; al < Q; ++al) {
+        const double c1 = c1_of(al), c2 = c2_of(al);
+        const double h1 = c1 * u1 + c2 * u2;
+        const double h2 = c1 * c1 * A11 + 2.0 * c1 * c2 * A12 + c2 * c2 * A22 - T0 * (A11 + A22);
+        const double h3 = c1 * c1 * c1 * C111 + 3.0 * c1 * c1 * c2 * C112 + 3.0 * c1 * c2 * c2 * C122 +
+                          c2 * c2 * c2 * C222 - 3.0 * T0 * (c1 * (C111 + C122) + c2 * (C112 + C222));
+        const double P = 1.0 + h1 / T0 + h2 / (2.0 * T0 * T0) + h3 / (6.0 * T0 * T0 * T0);
+        out[al] = J * Lat<Q>::w(al) * r * P;
+    }
+#pragma unroll
+    for (int al = 0; al < Q; ++al) Np[((size_t)al * n1 + i) * n2 + j] = out[al];
+}
+
 template <int Q, typename S>
 __global__ void k_to_fp64(const S* __restrict__ st, const double* __restrict__ geo,
                           double* __restrict__ Np, int n1, int n2, int ld, int h, int ncol) {
@@ -310,6 +350,14 @@ void launch_state_to_fp64(int Q, int prec, const void* state, const double* geo,
                           int n1, int n2, int ld, int h, int ncol, cudaStream_t s) {
     if (Q == 9) to64<9>(prec, state, geo, Np, n1, n2, ld, h, ncol, s);
     else to64<21>(prec, state, geo, Np, n1, n2, ld, h, ncol, s);
+}
+
+void launch_equilibrium(int Q, const double* rho, const double* U1, const double* U2,
+                        const double* geo, double* Np, int n1, int n2, int ncol, double rho0,
+                        cudaStream_t s) {
+    dim3 b(128), g((n2 + 127) / 128, n1);
+    if (Q == 9) k_equilibrium<9><<<g, b, 0, s>>>(rho, U1, U2, geo, Np, n1, n2, ncol, rho0);
+    else k_equilibrium<21><<<g, b, 0, s>>>(rho, U1, U2, geo, Np, n1, n2, ncol, rho0);
 }
 
 void launch_wall_init(int prec, void* wr, void* wu, const double* rho, const double* ut2, int n1,
