@@ -269,7 +269,7 @@ class Grid:
         n = C.c_size_t()
         _check(lib().clbm_checkpoint_bytes(self._h, C.byref(n)))
         if buf.size != n.value:
-            raise ClbmError("checkpoint is %d bytes, this grid's are %d" % (buf.size, n.value))
+            raise ClbmError(1, "checkpoint is %d bytes, this grid's are %d" % (buf.size, n.value))
         _check(lib().clbm_restore(self._h, buf.ctypes.data))
 
     @property

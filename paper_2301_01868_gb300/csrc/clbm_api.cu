@@ -217,6 +217,7 @@ MomArgs mom_args(const clbm_grid* g) {
     m.ncol = g->ncol;
     m.ut_prev = g->prev;
     m.partial = g->partial;
+    m.err = g->err;
     return m;
 }
 
@@ -662,8 +663,16 @@ clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
     fill_ghosts(g);
     MomArgs m = mom_args(g);
     m.have_prev = g->have_prev ? 1 : 0;
-    launch_moments(g->Q, g->prec, m, g->cs.force_iterations, 1, g->stream);
-    launch_reduce_final(g->partial, moments_blocks(g->n1, g->n2), g->red, g->stream);
+    // the pipelined pass where the update runs pipelined, else one thread
+    // per cell loading from global memory
+    int nb = -1;
+    if (use_tma(g)) nb = launch_residual_tma(g->Q, g->prec, *g->tma, m, g->stA == g->phys[0] ? 0 : 1,
+                                             g->nsm, g->stream);
+    if (nb < 0) {
+        launch_moments(g->Q, g->prec, m, g->cs.force_iterations, 1, g->stream);
+        nb = moments_blocks(g->n1, g->n2);
+    }
+    launch_reduce_final(g->partial, nb, g->red, g->stream);
     g->launches += 2;
     CK(cudaGetLastError());
     double v[NRED];

@@ -362,6 +362,35 @@ template <> struct ResAcc<float> {
     }
 };
 
+// One CTA's partial of the residual sums: warp shuffles, then the warps in
+// order (a fixed tree, so repeated runs give identical bits); slot 7 is the
+// largest |u|^2, reduced by max and rooted here.  Every thread of the CTA
+// calls it with its own sums.
+template <int NT>
+__device__ __forceinline__ void block_partial(double (&v)[NRED], double* out) {
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, off);
+            x = (k == 7) ? fmax(x, y) : x + y;
+        }
+        v[k] = x;
+    }
+    __shared__ double sh[NT / 32][NRED];
+    const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (ln == 0)
+        for (int k = 0; k < NRED; ++k) sh[w][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NRED) {
+        const int k = threadIdx.x;
+        double x = sh[0][k];
+        for (int q = 1; q < NT / 32; ++q) x = (k == 7) ? fmax(x, sh[q][k]) : x + sh[q][k];
+        out[k] = k == 7 ? sqrt(x) : x;
+    }
+}
+
 // Reference N of direction a at 1-based row r and geometry column jc (FP64
 // geometry table of ncol columns); rows beyond a wall are the mirror image
 // of the row inside, which flips c^1.

@@ -112,6 +112,7 @@ struct MomArgs {
     double* ut_prev;        // [2][n1][n2] FP64 snapshot of Ut^k
     double* partial;        // [blocks][NRED]
     int have_prev;
+    int* err;               // device error word of bounded waits (pipelined residual)
 };
 
 constexpr int NRED = 10;  // reduced quantities per block
@@ -163,6 +164,11 @@ void free_tma_maps(TmaMaps* m);
 // Copy the 2 x 8 load maps of both buffers to out (host); returns their bytes
 // (out may be NULL to ask the size).
 size_t tma_load_maps(const TmaMaps* m, void* out);
+// Residual sums of the pipelined (TMA-staged) pass over the current buffer
+// src of the maps: one partial per CTA; returns the number of partials, or
+// -1 when it cannot run (FP64 storage, launch failure).
+int launch_residual_tma(int Q, int prec, const TmaMaps& maps, const MomArgs& m, int src, int nsm,
+                        cudaStream_t s);
 int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
                     int pipelined, cudaStream_t s);
 

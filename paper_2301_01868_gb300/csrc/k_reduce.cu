@@ -86,27 +86,7 @@ __global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, 
     }
     double v[NRED];
     acc.out(v);
-#pragma unroll
-    for (int k = 0; k < NRED; ++k) {
-        double x = v[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, x, off);
-            x = (k == 7) ? fmax(x, y) : x + y;
-        }
-        v[k] = x;
-    }
-    __shared__ double sh[RB / 32][NRED];
-    const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    if (ln == 0)
-        for (int k = 0; k < NRED; ++k) sh[w][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x < NRED) {
-        const int k = threadIdx.x;
-        double x = sh[0][k];
-        for (int q = 1; q < RB / 32; ++q) x = (k == 7) ? fmax(x, sh[q][k]) : x + sh[q][k];
-        a.partial[(size_t)blockIdx.x * NRED + k] = k == 7 ? sqrt(x) : x;
-    }
+    block_partial<RB>(v, a.partial + (size_t)blockIdx.x * NRED);
 }
 
 // Final reduction: block k reduces quantity k over all block partials, each

@@ -375,14 +375,17 @@ __device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0,
     bulk_load(sm_tab, tab + (size_t)i0 * Tab<Q>::S, (uint32_t)nrows * Tab<Q>::S * 4, bar);
 }
 
-// The pipelined loop shared by the single-lattice and the batched kernels:
-// tile t of this CTA is tile_of(blockIdx.x + t gridDim.x); tile_of fills
-// (load maps, table, lattice, i0, j0) of a tile index.  The producer warp
-// re-fills a stage once all consumer warps released it; waits are bounded
-// and a time-out records an error, stops the other warps at their next
-// wait, and lets the loads in flight land before the CTA exits.
-template <int Q, typename S, typename C, typename TileOf>
-__device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_of) {
+// The pipelined loop shared by the single-lattice and the batched updates
+// and the residual: tile t of this CTA is tile_of(blockIdx.x + t gridDim.x);
+// tile_of fills (load maps, table, lat.n1, i0, j0) of a tile index, and every
+// consumer thread then runs cell(tile, staged boxes, staged table rows, r, cc)
+// for its cell (r, cc) of the tile.  The producer warp re-fills a stage once
+// all consumer warps released it; waits are bounded and a time-out records
+// an error, stops the other warps at their next wait, and lets the loads in
+// flight land before the CTA exits.  Every thread returns (the producer warp
+// first), so a caller may follow with CTA-wide work.
+template <int Q, typename S, typename C, typename TileOf, typename CellFn>
+__device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_of, CellFn&& cell) {
     using G = TileGeom<Q, S>;
     using P = PipeGeom<Q, S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -437,8 +440,7 @@ __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_
         }
         if (*s_abort) break;
         const auto t = tile_of(tile);
-        ws_update_cell<Q, S, C>(t.lat, t.k, (const S*)stage_in(st), (const C*)stage_tab(st), t.i0, t.j0,
-                                r, cc);
+        cell(t, (const S*)stage_in(st), (const C*)stage_tab(st), r, cc);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
     }
@@ -451,6 +453,15 @@ struct WsTile {
     WsLattice<S> lat;
     Consts<C> k;
     int i0, j0;
+};
+
+// The update of the consumer's cell of a WsTile.
+template <int Q, typename S, typename C>
+struct WsUpdate {
+    __device__ __forceinline__ void operator()(const WsTile<Q, S, C>& t, const S* in, const C* tab, int r,
+                                               int cc) const {
+        ws_update_cell<Q, S, C>(t.lat, t.k, in, tab, t.i0, t.j0, r, cc);
+    }
 };
 
 // The pipelined update of one lattice (PipeGeom): tile k of a CTA uses stage
@@ -467,7 +478,7 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     ws_pipeline<Q, S, C>(ntiles, a.err, [&](int tile) {
         return WsTile<Q, S, C>{maps.ld[src], (const C*)a.tab, lat, k, (tile / tiles_j) * G::TR,
                                (tile % tiles_j) * G::TJ};
-    });
+    }, WsUpdate<Q, S, C>{});
 }
 
 // The pipelined update of a batch: work item e = (lattice, i0, j0) over all
@@ -493,7 +504,60 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
         const WsLattice<S> lat{(S*)g.phys[src ^ 1], g.ghost, g.wall_rho, g.wall_ut2, g.plane, g.ld,
                                g.n1, g.n2, g.bc_lo, g.bc_hi, g.U0_lo, g.U0_hi};
         return WsTile<Q, S, C>{ld8, (const C*)g.tab, lat, Consts<C>::make(g.k), w.y, w.z};
+    }, WsUpdate<Q, S, C>{});
+}
+
+// A tile of the residual: what the producer needs (maps, table, n1, origin).
+template <typename C>
+struct ResTile {
+    const CUtensorMap* ld8;
+    const C* tab;
+    struct {
+        int n1;
+    } lat;
+    int i0, j0;
+};
+
+// The residual and conservation sums of clbm_residual over tiles staged by
+// the same pipeline as the update: each consumer thread pulls its cell from
+// shared memory, forms rho, U, F and Ut exactly as the update does (Eqs. 7-18,
+// lagged force), and accumulates the cell's residual terms (ResAcc, a fixed
+// order per thread: the tiles of a CTA are fixed); the CTA then reduces its
+// threads in a fixed tree into one partial.  The loads stream through three
+// stages instead of waiting cell by cell, so the pass runs near the
+// bandwidth of one read of the state.
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+    k_residual_ws(const __grid_constant__ TmaMaps maps, const MomArgs a, int src) {
+    using G = TileGeom<Q, S>;
+    const int tiles_j = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * tiles_j;
+    const Consts<C> k = Consts<C>::make(a.k);
+    const size_t nc = (size_t)a.n1 * a.n2;
+    C* const prev = (C*)a.ut_prev;
+    const bool have_prev = a.have_prev != 0;
+    ResAcc<C> acc;
+    ws_pipeline<Q, S, C>(ntiles, a.err, [&](int tile) {
+        return ResTile<C>{maps.ld[src], (const C*)a.tab, {a.n1}, (tile / tiles_j) * G::TR,
+                          (tile % tiles_j) * G::TJ};
+    }, [&](const ResTile<C>& t, const S* in, const C* tab, int r, int cc) {
+        const int i = t.i0 + r, j = t.j0 + cc;
+        if (i >= a.n1 || j >= a.n2) return;
+        const RowTab<Q, C> tb{tab + r * Tab<Q>::S};
+        Cell<Q, C> c;
+        pull_cell<Q, C>(
+            [&](int al, int dr, int dc) -> C {
+                return C(Store<S>::lds(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) + cc +
+                                       G::col0(al) + dc));
+            },
+            tb, k, c);
+        collide_emit<Q, C>(tb, c, k, [](int, C) {});
+        const size_t m = (size_t)i * a.n2 + j;
+        acc.add(residual_terms<Q, C>(c, tb, prev + m, prev + nc + m, have_prev));
     });
+    double v[NRED];
+    acc.out(v);
+    block_partial<PipeGeom<Q, S>::NTHREADS>(v, a.partial + (size_t)blockIdx.x * NRED);
 }
 
 }  // namespace
@@ -536,6 +600,44 @@ static int run_batch_ws(const BatchGrid* grids, const void* maps, const int4* wo
     k_batch_ws<Q, S, C><<<grid, P::NTHREADS, P::SMEM, s>>>(grids, (const CUtensorMap*)maps, work, nwork,
                                                           parity, err);
     return 0;
+}
+
+template <int Q, typename S>
+static int run_residual_ws(const TmaMaps& maps, const MomArgs& m, int src, int nsm, cudaStream_t s) {
+    using G = TileGeom<Q, S>;
+    using P = PipeGeom<Q, S>;
+    using C = typename Store<S>::C;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_residual_ws<Q, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 P::SMEM) != cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    const int tiles = ((m.n1 + G::TR - 1) / G::TR) * ((m.n2 + G::TJ - 1) / G::TJ);
+    const int grid = tiles < nsm ? tiles : nsm;
+    k_residual_ws<Q, S, C><<<grid, P::NTHREADS, P::SMEM, s>>>(maps, m, src);
+    return grid;
+}
+
+int launch_residual_tma(int Q, int prec, const TmaMaps& maps, const MomArgs& m, int src, int nsm,
+                        cudaStream_t s) {
+    if (Q == 9) {
+        switch (prec) {
+            case 1: return run_residual_ws<9, float>(maps, m, src, nsm, s);
+            case 2: return run_residual_ws<9, __half>(maps, m, src, nsm, s);
+            case 3: return run_residual_ws<9, __nv_bfloat16>(maps, m, src, nsm, s);
+            default: return -1;
+        }
+    }
+    switch (prec) {
+        case 1: return run_residual_ws<21, float>(maps, m, src, nsm, s);
+        case 2: return run_residual_ws<21, __half>(maps, m, src, nsm, s);
+        case 3: return run_residual_ws<21, __nv_bfloat16>(maps, m, src, nsm, s);
+        default: return -1;
+    }
 }
 
 int launch_batch_ws(int Q, int prec, const BatchGrid* grids, const void* maps, const int4* work, int nwork,
