@@ -285,8 +285,9 @@ struct CellTerms {
     bool bad;
 };
 
+// p1, p2: Ut of the last call (read only when have_prev).
 template <int Q, typename C, typename TB>
-__device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, const TB& tb, C* prev1, C* prev2,
+__device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, const TB& tb, C p1, C p2,
                                                        bool have_prev) {
     using T = Tab<Q>;
     const C g11 = tb.s(T::C11), g12 = tb.s(T::C12), g22 = tb.s(T::C22);
@@ -296,11 +297,9 @@ __device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, cons
     t.uu = g11 * u1 * u1 + C(2) * g12 * u1 * u2 + g22 * u2 * u2;
     t.dd = C(0);
     if (have_prev) {
-        const C e1 = u1 - *prev1, e2 = u2 - *prev2;
+        const C e1 = u1 - p1, e2 = u2 - p2;
         t.dd = J * (g11 * e1 * e1 + C(2) * g12 * e1 * e2 + g22 * e2 * e2);
     }
-    *prev1 = u1;
-    *prev2 = u2;
     t.uu_j = J * t.uu;
     t.ls = c.ls;
     t.ls1 = c.ls1;
@@ -308,6 +307,17 @@ __device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, cons
     t.ke = C(0.5) * J * c.rho * t.uu;
     t.am = J * c.rho * (tb.s(T::AM1) * u1 + tb.s(T::AM2) * u2);
     t.bad = !(c.rho > C(0) && isfinite(c.rho) && isfinite(t.uu));
+    return t;
+}
+
+// The same with the snapshot in memory: reads the last Ut, writes this one.
+template <int Q, typename C, typename TB>
+__device__ __forceinline__ CellTerms<C> residual_terms(const Cell<Q, C>& c, const TB& tb, C* prev1, C* prev2,
+                                                       bool have_prev) {
+    const CellTerms<C> t = residual_terms<Q, C, TB>(c, tb, have_prev ? *prev1 : C(0),
+                                                    have_prev ? *prev2 : C(0), have_prev);
+    *prev1 = c.Ut1;
+    *prev2 = c.Ut2;
     return t;
 }
 

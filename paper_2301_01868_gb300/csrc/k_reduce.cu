@@ -77,12 +77,16 @@ __global__ void __launch_bounds__(RB, ITER ? 2 : 4) k_residual(const MomArgs a, 
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int i = it / bx, j = (it % bx) * RB + threadIdx.x;
         if (j >= a.n2) continue;
-        Cell<Q, C> c;
-        cell_moments<Q, S, C, ITER, GEN>(a, iters, i, j, c);
         const size_t m = (size_t)i * a.n2 + j;
         C* prev = (C*)a.ut_prev;
-        acc.add(residual_terms<Q, C>(c, TabOf<Q, C, GEN>::at(a.tab, i, j, a.n1, a.n2), prev + m, prev + nc + m,
-                                     a.have_prev != 0));
+        const bool hp = a.have_prev != 0;
+        // the snapshot first: its load overlaps the pull
+        const C p1 = hp ? prev[m] : C(0), p2 = hp ? prev[nc + m] : C(0);
+        Cell<Q, C> c;
+        cell_moments<Q, S, C, ITER, GEN>(a, iters, i, j, c);
+        acc.add(residual_terms<Q, C>(c, TabOf<Q, C, GEN>::at(a.tab, i, j, a.n1, a.n2), p1, p2, hp));
+        prev[m] = c.Ut1;
+        prev[nc + m] = c.Ut2;
     }
     double v[NRED];
     acc.out(v);

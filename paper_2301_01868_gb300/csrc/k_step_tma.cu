@@ -376,8 +376,9 @@ __device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0,
 }
 
 // The pipelined loop shared by the single-lattice and the batched updates
-// and the residual: tile t of this CTA is tile_of(blockIdx.x + t gridDim.x);
-// tile_of fills (load maps, table, lat.n1, i0, j0) of a tile index, and every
+// and the residual: the CTA's t-th tile is tile_of(blockIdx.x + t gridDim.x, t)
+// (every thread asks for t = 0, 1, 2, ... in order); tile_of fills (load
+// maps, table, lat.n1, i0, j0) of a tile, and every
 // consumer thread then runs cell(tile, staged boxes, staged table rows, r, cc)
 // for its cell (r, cc) of the tile.  The producer warp re-fills a stage once
 // all consumer warps released it; waits are bounded and a time-out records
@@ -418,7 +419,7 @@ __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_
                     break;
                 }
                 if (*s_abort) break;
-                const auto t = tile_of(tile);
+                const auto t = tile_of(tile, it);
                 ws_issue<Q, S, C>(t.ld8, t.i0, t.j0, t.lat.n1, t.tab, stage_in(st), stage_tab(st),
                                   &full[st]);
             }
@@ -439,7 +440,7 @@ __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_
             break;
         }
         if (*s_abort) break;
-        const auto t = tile_of(tile);
+        const auto t = tile_of(tile, it);
         cell(t, (const S*)stage_in(st), (const C*)stage_tab(st), r, cc);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
@@ -464,20 +465,43 @@ struct WsUpdate {
     }
 };
 
-// The pipelined update of one lattice (PipeGeom): tile k of a CTA uses stage
-// k mod STAGES.
+// The order in which a CTA walks the tiles of one lattice: CTA b takes a
+// contiguous run of the tiles numbered down the columns of tiles (tile L is
+// band L mod bands of strip L / bands), so each next tile sits just below the
+// last one and its upper halo rows are still in L2, and CTAs b and b + 1 walk
+// neighbouring runs.  Each thread steps its own copy from its t-th to its
+// (t+1)-th tile without a division.
+struct StripWalk {
+    int band, strip, bands;
+    __device__ __forceinline__ StripWalk(int ntiles, int bands_) : bands(bands_) {
+        const int q = ntiles / (int)gridDim.x, r = ntiles % (int)gridDim.x, b = blockIdx.x;
+        const int L = b * q + (b < r ? b : r);
+        strip = L / bands;
+        band = L - strip * bands;
+    }
+    __device__ __forceinline__ void next() {
+        if (++band == bands) {
+            band = 0;
+            ++strip;
+        }
+    }
+};
+
+// The pipelined update of one lattice (PipeGeom): tile t of a CTA uses stage
+// t mod STAGES.
 template <int Q, typename S, typename C>
 __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     k_fused_ws(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
     using G = TileGeom<Q, S>;
-    const int tiles_j = (a.n2 + G::TJ - 1) / G::TJ;
-    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * tiles_j;
+    const int bands = (a.n1 + G::TR - 1) / G::TR;
+    const int ntiles = bands * ((a.n2 + G::TJ - 1) / G::TJ);
     const WsLattice<S> lat{(S*)a.dst, a.ghost, a.wall_rho, a.wall_ut2, a.plane, a.ld, a.n1, a.n2,
                            a.bc_lo, a.bc_hi, a.U0_lo, a.U0_hi};
     const Consts<C> k = Consts<C>::make(a.k);
-    ws_pipeline<Q, S, C>(ntiles, a.err, [&](int tile) {
-        return WsTile<Q, S, C>{maps.ld[src], (const C*)a.tab, lat, k, (tile / tiles_j) * G::TR,
-                               (tile % tiles_j) * G::TJ};
+    StripWalk w(ntiles, bands);
+    ws_pipeline<Q, S, C>(ntiles, a.err, [&](int, int t) {
+        if (t > 0) w.next();
+        return WsTile<Q, S, C>{maps.ld[src], (const C*)a.tab, lat, k, w.band * G::TR, w.strip * G::TJ};
     }, WsUpdate<Q, S, C>{});
 }
 
@@ -490,7 +514,7 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     k_batch_ws(const BatchGrid* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                const int4* __restrict__ work, int nwork, int parity, int* err) {
     const CUtensorMap* fenced = nullptr;  // producer: maps acquired last
-    ws_pipeline<Q, S, C>(nwork, err, [&](int e) {
+    ws_pipeline<Q, S, C>(nwork, err, [&](int e, int) {
         const int4 w = work[e];
         const BatchGrid& g = grids[w.x];
         const int src = g.parity ^ parity;
@@ -530,19 +554,24 @@ template <int Q, typename S, typename C>
 __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     k_residual_ws(const __grid_constant__ TmaMaps maps, const MomArgs a, int src) {
     using G = TileGeom<Q, S>;
-    const int tiles_j = (a.n2 + G::TJ - 1) / G::TJ;
-    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * tiles_j;
+    const int bands = (a.n1 + G::TR - 1) / G::TR;
+    const int ntiles = bands * ((a.n2 + G::TJ - 1) / G::TJ);
     const Consts<C> k = Consts<C>::make(a.k);
     const size_t nc = (size_t)a.n1 * a.n2;
     C* const prev = (C*)a.ut_prev;
     const bool have_prev = a.have_prev != 0;
     ResAcc<C> acc;
-    ws_pipeline<Q, S, C>(ntiles, a.err, [&](int tile) {
-        return ResTile<C>{maps.ld[src], (const C*)a.tab, {a.n1}, (tile / tiles_j) * G::TR,
-                          (tile % tiles_j) * G::TJ};
+    StripWalk w(ntiles, bands);
+    ws_pipeline<Q, S, C>(ntiles, a.err, [&](int, int t) {
+        if (t > 0) w.next();
+        return ResTile<C>{maps.ld[src], (const C*)a.tab, {a.n1}, w.band * G::TR, w.strip * G::TJ};
     }, [&](const ResTile<C>& t, const S* in, const C* tab, int r, int cc) {
         const int i = t.i0 + r, j = t.j0 + cc;
         if (i >= a.n1 || j >= a.n2) return;
+        const size_t m = (size_t)i * a.n2 + j;
+        // the snapshot comes from global memory: load it first, so that its
+        // latency hides behind the pull and the moments
+        const C p1 = have_prev ? prev[m] : C(0), p2 = have_prev ? prev[nc + m] : C(0);
         const RowTab<Q, C> tb{tab + r * Tab<Q>::S};
         Cell<Q, C> c;
         pull_cell<Q, C>(
@@ -552,8 +581,9 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
             },
             tb, k, c);
         collide_emit<Q, C>(tb, c, k, [](int, C) {});
-        const size_t m = (size_t)i * a.n2 + j;
-        acc.add(residual_terms<Q, C>(c, tb, prev + m, prev + nc + m, have_prev));
+        acc.add(residual_terms<Q, C>(c, tb, p1, p2, have_prev));
+        prev[m] = c.Ut1;
+        prev[nc + m] = c.Ut2;
     });
     double v[NRED];
     acc.out(v);
