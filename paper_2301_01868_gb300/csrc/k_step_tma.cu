@@ -9,10 +9,11 @@
 // D2Q21), plus the tile's table rows by a bulk copy.  Every shared-memory
 // offset of a pull is a compile-time constant.  Two kernels share this:
 //
-// k_fused_ws (default): a producer warp fills three stages; 16 consumer
-//   warps each update 32 cells of a tile row and store straight to global
-//   memory; full / empty mbarriers per stage, no CTA-wide barrier in the
-//   tile loop.  k_batch_ws runs the same loop over the tiles of a batch.
+// k_fused_ws (default): a producer warp fills 3 to 8 stages (as many as
+//   fit in shared memory); 16 consumer warps each update 32 cells of a tile
+//   row and store straight to global memory; full / empty mbarriers per
+//   stage, no CTA-wide barrier in the tile loop.  k_batch_ws runs the same
+//   loop over the tiles of a batch, k_residual_ws the residual sums.
 // k_fused_tma: one elected thread, two stages, CTA-wide barriers, and a
 //   shared output tile written back by one TMA store; the CTA copies the
 //   periodic ghost columns and the ragged tail from that tile.
@@ -72,12 +73,17 @@ struct TileGeom {
 template <int Q, typename S>
 struct PipeGeom {
     using G = TileGeom<Q, S>;
-    static constexpr int STAGES = 3;
     static constexpr int CONSUMERS = G::NT / 32;
     static constexpr int NTHREADS = G::NT + 32;
     static constexpr int IN_BYTES = (G::BUF * (int)sizeof(S) + 127) / 128 * 128;
     static constexpr int STAGE_BYTES = IN_BYTES + (G::TABB + 127) / 128 * 128;
+    // as many stages as fit in 220 KB of shared memory (2 to 8): the smaller
+    // the stage (D2Q9, 16-bit storage), the more tiles are in flight, so every
+    // configuration keeps about the same bytes on their way from HBM per SM
+    static constexpr int FIT = (220 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = FIT > 8 ? 8 : (FIT < 2 ? 2 : FIT);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16 + 128;
+    static_assert(SMEM + 2048 <= 227 * 1024, "pipeline stages exceed shared memory");
 };
 
 // Tensor maps of both state buffers: per buffer, the 8 box shapes of the loads
@@ -465,24 +471,25 @@ struct WsUpdate {
     }
 };
 
-// The order in which a CTA walks the tiles of one lattice: CTA b takes a
-// contiguous run of the tiles numbered down the columns of tiles (tile L is
-// band L mod bands of strip L / bands), so each next tile sits just below the
-// last one and its upper halo rows are still in L2, and CTAs b and b + 1 walk
-// neighbouring runs.  Each thread steps its own copy from its t-th to its
-// (t+1)-th tile without a division.
-struct StripWalk {
-    int band, strip, bands;
-    __device__ __forceinline__ StripWalk(int ntiles, int bands_) : bands(bands_) {
-        const int q = ntiles / (int)gridDim.x, r = ntiles % (int)gridDim.x, b = blockIdx.x;
-        const int L = b * q + (b < r ? b : r);
-        strip = L / bands;
-        band = L - strip * bands;
+// The order in which a CTA walks the tiles of one lattice: tile
+// blockIdx.x + t gridDim.x in row-major order (band-major: all CTAs work on a
+// few neighbouring bands at a time, so every TMA box row is part of a long
+// contiguous run that the other CTAs read at the same time).  Each thread
+// steps its own copy from its t-th to its (t+1)-th tile without a division.
+struct RowWalk {
+    int band, col, cols, dband, dcol;
+    __device__ __forceinline__ explicit RowWalk(int cols_) : cols(cols_) {
+        band = (int)blockIdx.x / cols;
+        col = (int)blockIdx.x - band * cols;
+        dband = (int)gridDim.x / cols;
+        dcol = (int)gridDim.x - dband * cols;
     }
     __device__ __forceinline__ void next() {
-        if (++band == bands) {
-            band = 0;
-            ++strip;
+        band += dband;
+        col += dcol;
+        if (col >= cols) {
+            col -= cols;
+            ++band;
         }
     }
 };
@@ -493,15 +500,15 @@ template <int Q, typename S, typename C>
 __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     k_fused_ws(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
     using G = TileGeom<Q, S>;
-    const int bands = (a.n1 + G::TR - 1) / G::TR;
-    const int ntiles = bands * ((a.n2 + G::TJ - 1) / G::TJ);
+    const int cols = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * cols;
     const WsLattice<S> lat{(S*)a.dst, a.ghost, a.wall_rho, a.wall_ut2, a.plane, a.ld, a.n1, a.n2,
                            a.bc_lo, a.bc_hi, a.U0_lo, a.U0_hi};
     const Consts<C> k = Consts<C>::make(a.k);
-    StripWalk w(ntiles, bands);
+    RowWalk w(cols);
     ws_pipeline<Q, S, C>(ntiles, a.err, [&](int, int t) {
         if (t > 0) w.next();
-        return WsTile<Q, S, C>{maps.ld[src], (const C*)a.tab, lat, k, w.band * G::TR, w.strip * G::TJ};
+        return WsTile<Q, S, C>{maps.ld[src], (const C*)a.tab, lat, k, w.band * G::TR, w.col * G::TJ};
     }, WsUpdate<Q, S, C>{});
 }
 
@@ -554,17 +561,17 @@ template <int Q, typename S, typename C>
 __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     k_residual_ws(const __grid_constant__ TmaMaps maps, const MomArgs a, int src) {
     using G = TileGeom<Q, S>;
-    const int bands = (a.n1 + G::TR - 1) / G::TR;
-    const int ntiles = bands * ((a.n2 + G::TJ - 1) / G::TJ);
+    const int cols = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * cols;
     const Consts<C> k = Consts<C>::make(a.k);
     const size_t nc = (size_t)a.n1 * a.n2;
     C* const prev = (C*)a.ut_prev;
     const bool have_prev = a.have_prev != 0;
     ResAcc<C> acc;
-    StripWalk w(ntiles, bands);
+    RowWalk w(cols);
     ws_pipeline<Q, S, C>(ntiles, a.err, [&](int, int t) {
         if (t > 0) w.next();
-        return ResTile<C>{maps.ld[src], (const C*)a.tab, {a.n1}, w.band * G::TR, w.strip * G::TJ};
+        return ResTile<C>{maps.ld[src], (const C*)a.tab, {a.n1}, w.band * G::TR, w.col * G::TJ};
     }, [&](const ResTile<C>& t, const S* in, const C* tab, int r, int cc) {
         const int i = t.i0 + r, j = t.j0 + cc;
         if (i >= a.n1 || j >= a.n2) return;
