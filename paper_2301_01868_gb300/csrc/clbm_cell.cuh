@@ -30,6 +30,27 @@ template <> struct Consts<float> {
     }
 };
 
+// Two compute values operated on together.  An FP32 pair is a float2, and
+// pfma / padd / pmul issue one packed FP32 instruction (sm_100 and later)
+// for both lanes, each lane rounded exactly as the scalar operation; an FP64
+// pair is two scalar operations.  The update keeps the two directions of a
+// +/- pair (and the two lanes of its sums) in one pair wherever the same
+// operation applies to both, so the packed form halves those instructions.
+template <typename C> struct PairOf;
+template <> struct PairOf<float> { using T = float2; };
+template <> struct PairOf<double> { using T = double2; };
+
+__device__ __forceinline__ float2 mkp(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 mkp(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+
 template <int Q, typename C>
 struct Cell {
     C d[Q];                                   // pulled deviations from this row's reference
@@ -38,8 +59,10 @@ struct Cell {
 };
 
 // Coefficient tables as the update reads them.  s(k): header value k of
-// Tab<Q> (INVJ .. M2); pa(q), pd(q): Christoffel contractions and pull
-// offsets of pair q; pb(q): (P0_a, E11, E22, E12); p0(q): P0_a alone.
+// Tab<Q> (INVJ .. M2); pair q = (a, b = -a): pa(q) the Christoffel
+// contractions (a^1_b, a^1_a, a^2_b, a^2_a), pd(q) the pull offsets
+// (Delta_a, Delta_b), pb(q) the dPi weights and rest polynomial
+// (E11, E22, E12, P0_a); p0(q): P0_a alone.
 //
 // RowTab: one Tab<Q> block per row (planar and polar grids), read as
 // aligned vectors (global or shared memory).
@@ -51,7 +74,7 @@ struct RowTab {
     __device__ __forceinline__ C s(int k) const { return p[k]; }
     __device__ __forceinline__ V4<C> pa(int q) const { return ld4(p + Tab<Q>::pa(q)); }
     __device__ __forceinline__ V4<C> pb(int q) const { return ld4(p + Tab<Q>::pb(q)); }
-    __device__ __forceinline__ C p0(int q) const { return p[Tab<Q>::pb(q)]; }
+    __device__ __forceinline__ C p0(int q) const { return p[Tab<Q>::pb(q) + 3]; }
     __device__ __forceinline__ V4<C> pd(int q) const { return ld4(p + Tab<Q>::pd(q)); }
 };
 
@@ -93,8 +116,8 @@ struct CellTab {
         const int a = Lat<Q>::plus(q);
         const C w = C(Lat<Q>::w(a)), c1 = C(c1_of(a)), c2 = C(c2_of(a));
         const V4<C> A = pa(q);
-        const C D1 = A.x + A.z, D2 = A.y + A.w;
-        return {p0(q), C(2) * w * c1 * D1, C(2) * w * c2 * D2, w * (c1 * D2 + c2 * D1)};
+        const C D1 = A.x + A.y, D2 = A.z + A.w;
+        return {C(2) * w * c1 * D1, C(2) * w * c2 * D2, w * (c1 * D2 + c2 * D1), p0(q)};
     }
 };
 
@@ -121,50 +144,52 @@ template <int Q, typename C, typename LD, typename TB>
 __device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>& k, Cell<Q, C>& c) {
     using L = Lat<Q>;
     using T = Tab<Q>;
-    C Sd = tb.s(T::D0), S1 = tb.s(T::M1), S2 = tb.s(T::M2);
-    C f1 = tb.s(T::F01), f2 = tb.s(T::F02);
+    using P = typename PairOf<C>::T;
+    // two-lane sums: lane x collects direction a of each pair, lane y b
+    P sd = mkp(tb.s(T::D0), C(0));
+    P s1 = mkp(tb.s(T::M1), C(0)), s2 = mkp(tb.s(T::M2), C(0));
+    P f1 = mkp(tb.s(T::F01), C(0)), f2 = mkp(tb.s(T::F02), C(0));
+    P ls = mkp(C(0), C(0)), ls1 = mkp(C(0), C(0)), ls2 = mkp(C(0), C(0));
     c.d[0] = ld(0, 0, 0);
-    Sd += c.d[0];
-    c.ls = c.d[0];
-    c.ls1 = C(0);
-    c.ls2 = C(0);
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const int c1 = c1_of(a), c2 = c2_of(a);
         const V4<C> A = tb.pa(q);
         // pulled: N_a(q) from q - c_a, N_b(q) from q + c_a; lagged: own values
-        const C pa = ld(a, -c1, -c2);
-        const C pb = ld(b, c1, c2);
-        const C la = ld(a, 0, 0);
-        const C lb = ld(b, 0, 0);
-        Sd += pa + pb;
-        const C dp = pa - pb;
-        if (c1 != 0) S1 += C(c1) * dp;
-        if (c2 != 0) S2 += C(c2) * dp;
-        const C ta = la + pb, tbv = lb + pa;
-        f1 += A.x * ta + A.z * tbv;
-        f2 += A.y * ta + A.w * tbv;
-        c.ls += la + lb;
-        if (c1 != 0) c.ls1 += C(c1) * (la - lb);
-        if (c2 != 0) c.ls2 += C(c2) * (la - lb);
+        const P pp = mkp(ld(a, -c1, -c2), ld(b, c1, c2));
+        const P lg = mkp(ld(b, 0, 0), ld(a, 0, 0));        // (lagged b, lagged a)
+        sd = padd(sd, pp);
+        if (c1 != 0) s1 = pfma(mkp(C(c1), C(-c1)), pp, s1);
+        if (c2 != 0) s2 = pfma(mkp(C(c2), C(-c2)), pp, s2);
+        // (N'_b + N_a, N'_a + N_b): the two sums the contractions of a and b weigh
+        const P t = padd(lg, pp);
+        f1 = pfma(mkp(A.x, A.y), t, f1);
+        f2 = pfma(mkp(A.z, A.w), t, f2);
+        ls = padd(ls, lg);
+        if (c1 != 0) ls1 = pfma(mkp(C(-c1), C(c1)), lg, ls1);
+        if (c2 != 0) ls2 = pfma(mkp(C(-c2), C(c2)), lg, ls2);
         if (c1 != 0 || TB::ALL_OFFSETS) {
             const V4<C> D = tb.pd(q);
-            c.d[a] = pa + D.x;
-            c.d[b] = pb + D.y;
+            const P dd = padd(pp, mkp(D.x, D.y));
+            c.d[a] = dd.x;
+            c.d[b] = dd.y;
         } else {
-            c.d[a] = pa;
-            c.d[b] = pb;
+            c.d[a] = pp.x;
+            c.d[b] = pp.y;
         }
     }
+    c.ls = c.d[0] + (ls.x + ls.y);
+    c.ls1 = ls1.x + ls1.y;
+    c.ls2 = ls2.x + ls2.y;
     const C invJ = tb.s(T::INVJ);
-    c.drho = Sd * invJ;
+    c.drho = (c.d[0] + sd.x + sd.y) * invJ;
     c.rho = k.rho0 + c.drho;
     c.irho = C(1) / c.rho;
-    c.U1 = S1 * invJ * c.irho;
-    c.U2 = S2 * invJ * c.irho;
-    c.F1 = -C(0.5) * invJ * f1 + c.rho * k.g1;
-    c.F2 = -C(0.5) * invJ * f2 + c.rho * k.g2;
+    c.U1 = (s1.x + s1.y) * invJ * c.irho;
+    c.U2 = (s2.x + s2.y) * invJ * c.irho;
+    c.F1 = -C(0.5) * invJ * (f1.x + f1.y) + c.rho * k.g1;
+    c.F2 = -C(0.5) * invJ * (f2.x + f2.y) + c.rho * k.g2;
 }
 
 // Loader of the global buffer: p points at the cell in population plane 0,
@@ -186,18 +211,19 @@ __device__ __forceinline__ void force_again(const TB& tb, const C (&out)[Q], con
                                             Cell<Q, C>& c) {
     using T = Tab<Q>;
     using L = Lat<Q>;
-    C f1 = tb.s(T::FI1), f2 = tb.s(T::FI2);
+    using P = typename PairOf<C>::T;
+    P f1 = mkp(tb.s(T::FI1), C(0)), f2 = mkp(tb.s(T::FI2), C(0));
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const V4<C> A = tb.pa(q);
-        const C ta = out[a] + c.d[b], tbv = out[b] + c.d[a];
-        f1 += A.x * ta + A.z * tbv;
-        f2 += A.y * ta + A.w * tbv;
+        const P t = padd(mkp(out[b], out[a]), mkp(c.d[a], c.d[b]));
+        f1 = pfma(mkp(A.x, A.y), t, f1);
+        f2 = pfma(mkp(A.z, A.w), t, f2);
     }
     const C invJ = tb.s(T::INVJ);
-    c.F1 = -C(0.5) * invJ * f1 + c.rho * k.g1;
-    c.F2 = -C(0.5) * invJ * f2 + c.rho * k.g2;
+    c.F1 = -C(0.5) * invJ * (f1.x + f1.y) + c.rho * k.g1;
+    c.F2 = -C(0.5) * invJ * (f2.x + f2.y) + c.rho * k.g2;
 }
 
 // Ut (Eq. 18), equilibrium coefficients (Eq. 19), odd parts, the momentum-flux
@@ -241,9 +267,9 @@ __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const 
         O[q] = K11 * c1 + K12 * c2 + K111 * (c1 * c1 * c1) + K112 * (c1 * c1 * c2) +
                K122 * (c1 * c2 * c2) + K222 * (c2 * c2 * c2);
         const V4<C> B = tb.pb(q);
-        S11 += B.y * O[q];
-        S22 += B.z * O[q];
-        S12 += B.w * O[q];
+        S11 += B.x * O[q];
+        S22 += B.y * O[q];
+        S12 += B.z * O[q];
     }
     const C pr = k.pref * c.rho;
     S11 *= pr;
@@ -258,16 +284,20 @@ __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const 
     const C Ea = rt * dK11 + S11 * (iT0 * iT0);
     const C Eb = rt * dK12 + C(2) * S12 * (iT0 * iT0);
     const C Ec = rt * dK22 + S22 * (iT0 * iT0);
+    using P = typename PairOf<C>::T;
     emit(0, c.d[0] * omt + J * C(L::w(0)) * (drt * tb.s(T::P00) + base));
+    const P omt2 = mkp(omt, omt), J2 = mkp(J, J);
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
         const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
         const C X = drt * tb.p0(q) + base + Ea * (c1 * c1) + Eb * (c1 * c2) + Ec * (c2 * c2);
         const C Y = rt * O[q] + Fa * c1 + Fb * c2;
-        const C Jw = J * C(L::w(a));
-        emit(a, c.d[a] * omt + Jw * (X + Y));
-        emit(b, c.d[b] * omt + Jw * (X - Y));
+        const C w = C(L::w(a));
+        // (N'_a, N'_b) = (d_a, d_b) (1 - 1/tau) + J w (X + Y, X - Y)
+        const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(mkp(c.d[a], c.d[b]), omt2));
+        emit(a, o.x);
+        emit(b, o.y);
     }
 }
 

@@ -79,9 +79,9 @@ template <> struct Lat<21> {
 // Per-row coefficient table of the fused update, in the compute type.
 // Slots: a 16-value header (metric, rest-state sums evaluated in FP64), then
 // 12 values per +/- pair (a = plus(p), b = opp(a)), each group of four read
-// as one vector:
-//   A = (a^1_a, a^2_a, a^1_b, a^2_b)          Christoffel contractions
-//   B = (P0_a, E11, E22, E12)                  rest polynomial, dPi weights
+// as one vector, in the lane order of the update's paired arithmetic:
+//   A = (a^1_b, a^1_a, a^2_b, a^2_a)          Christoffel contractions
+//   B = (E11, E22, E12, P0_a)                  dPi weights, rest polynomial
 //   D = (Delta_a, Delta_b, 0, 0)               pull offsets ref(i - c1) - ref(i)
 template <int Q> struct Tab {
     static constexpr int INVJ = 0, J = 1, G11 = 2, G12 = 3, G22 = 4;
@@ -98,7 +98,7 @@ template <int Q> struct Tab {
 
 // Per-cell table of a general grid, one plane of n1 n2 values per entry:
 // the Tab<Q> header values INVJ .. AM2 at the same indices, then per pair the
-// contractions (a^1_a, a^2_a, a^1_b, a^2_b) and the pull offsets
+// contractions (a^1_b, a^1_a, a^2_b, a^2_a) and the pull offsets
 // (Delta_a, Delta_b); P0 and the dPi weights are formed when read.
 template <int Q>
 struct CellTabLayout {

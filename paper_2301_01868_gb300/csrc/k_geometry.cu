@@ -164,14 +164,15 @@ __global__ void k_tables(const double* __restrict__ geo, C* __restrict__ tab, in
         const double c1 = c1_of(a), c2 = c2_of(a);
         const double D1 = g[Geo::a1(a)] + g[Geo::a1(ab)];
         const double D2 = g[Geo::a2(a)] + g[Geo::a2(ab)];
-        t[T::pa(p) + 0] = C(g[Geo::a1(a)]);
-        t[T::pa(p) + 1] = C(g[Geo::a2(a)]);
-        t[T::pa(p) + 2] = C(g[Geo::a1(ab)]);
-        t[T::pa(p) + 3] = C(g[Geo::a2(ab)]);
-        t[T::pb(p) + 0] = C(rest_poly<Q>(a, g[Geo::GI11], g[Geo::GI12], g[Geo::GI22]));
-        t[T::pb(p) + 1] = C(2.0 * w * c1 * D1);
-        t[T::pb(p) + 2] = C(2.0 * w * c2 * D2);
-        t[T::pb(p) + 3] = C(w * (c1 * D2 + c2 * D1));
+        // pair order of the update: (b, a) contractions, then the dPi weights
+        t[T::pa(p) + 0] = C(g[Geo::a1(ab)]);
+        t[T::pa(p) + 1] = C(g[Geo::a1(a)]);
+        t[T::pa(p) + 2] = C(g[Geo::a2(ab)]);
+        t[T::pa(p) + 3] = C(g[Geo::a2(a)]);
+        t[T::pb(p) + 0] = C(2.0 * w * c1 * D1);
+        t[T::pb(p) + 1] = C(2.0 * w * c2 * D2);
+        t[T::pb(p) + 2] = C(w * (c1 * D2 + c2 * D1));
+        t[T::pb(p) + 3] = C(rest_poly<Q>(a, g[Geo::GI11], g[Geo::GI12], g[Geo::GI22]));
         t[T::pd(p) + 0] = C(dl[a]);
         t[T::pd(p) + 1] = C(dl[ab]);
     }
@@ -237,10 +238,10 @@ __global__ void k_tables_cell(const double* __restrict__ geo, C* __restrict__ ta
 #pragma unroll
     for (int p = 0; p < Lat<Q>::NP; ++p) {
         const int a = Lat<Q>::plus(p), ab = opp_of(a);
-        put(L::pa(p) + 0, g[Geo::a1(a)]);
-        put(L::pa(p) + 1, g[Geo::a2(a)]);
-        put(L::pa(p) + 2, g[Geo::a1(ab)]);
-        put(L::pa(p) + 3, g[Geo::a2(ab)]);
+        put(L::pa(p) + 0, g[Geo::a1(ab)]);
+        put(L::pa(p) + 1, g[Geo::a1(a)]);
+        put(L::pa(p) + 2, g[Geo::a2(ab)]);
+        put(L::pa(p) + 3, g[Geo::a2(a)]);
         put(L::pd(p) + 0, dl[a]);
         put(L::pd(p) + 1, dl[ab]);
     }
