@@ -9,19 +9,19 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "clbm_oracle.c")
+SRCS = [os.path.join(HERE, f) for f in ("clbm_oracle.c", "clbm_oracle3d.c")]
+HDRS = [os.path.join(HERE, f) for f in ("clbm_oracle.h", "clbm_oracle3d.h")]
 LIB = os.path.join(HERE, "liborc.so")
 
 
 def build(force: bool = False) -> str:
-    """Build liborc.so if it is missing or older than its source; return its path."""
+    """Build liborc.so if it is missing or older than its sources; return its path."""
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)
-            and os.path.getmtime(LIB) >= os.path.getmtime(os.path.join(HERE, "clbm_oracle.h"))):
+            and all(os.path.getmtime(LIB) >= os.path.getmtime(p) for p in SRCS + HDRS)):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fopenmp",
-           "-fPIC", "-shared", SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared"] + SRCS + ["-o", tmp, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB
