@@ -48,6 +48,18 @@ class _Case(C.Structure):
 _lib = None
 
 
+class _Desc3(C.Structure):
+    _fields_ = [("precision", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int),
+                ("kind", C.c_int), ("edges", C.POINTER(C.c_double)), ("step2", C.c_double),
+                ("step3", C.c_double), ("dx", C.c_double), ("bc_lo", C.c_int), ("bc_hi", C.c_int),
+                ("device", C.c_int), ("stream", C.c_void_p)]
+
+
+class _Case3(C.Structure):
+    _fields_ = [("tau", C.c_double), ("rho0", C.c_double), ("u_wall_lo", C.c_double),
+                ("u_wall_hi", C.c_double), ("g_ext", C.c_double * 3)]
+
+
 def lib():
     """Load the CUDA library (raises if it has not been built)."""
     global _lib
@@ -86,6 +98,15 @@ def lib():
             "clbm_batch_launch_count": [h, C.POINTER(ll)],
             "clbm_batch_destroy": [h],
             "clbm_destroy": [h],
+            "clbm3_create_grid": [C.POINTER(_Desc3), C.POINTER(C.c_void_p)],
+            "clbm3_set_case": [h, C.POINTER(_Case3)],
+            "clbm3_set_state": [h, vp, vp, vp, vp, C.c_int],
+            "clbm3_get_state": [h, vp, C.c_int],
+            "clbm3_step": [h, ll],
+            "clbm3_moments": [h, vp, vp, C.c_int],
+            "clbm3_totals": [h, dp],
+            "clbm3_time": [h, C.POINTER(ll)],
+            "clbm3_destroy": [h],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -399,3 +420,100 @@ def wall_speed_polar(u_phys, R_wall, n2, dx):
     """Contravariant U0^2 of a rigidly rotating circle of radius R_wall with
     surface speed u_phys (|g_2| = R sin(2 pi / n2) / dx, App. D)."""
     return u_phys * dx / (R_wall * math.sin(2.0 * math.pi / n2))
+
+
+CHANNEL3, ANNULUS3 = 0, 1
+
+
+class Grid3:
+    """A three-dimensional lattice (D3Q39, clbm3.h) on one GPU: q^1 wall-normal
+    between two walls, q^2 and q^3 periodic.  kind CHANNEL3 (edges along q^1,
+    uniform q^2 / q^3 spacings) or ANNULUS3 (radial edges, n2 angular nodes,
+    axial spacing step3).  precision FP64 or FP32.  Populations are float64
+    (39, n1, n2, n3) arrays of N'(q, t-1)."""
+
+    Q = 39
+
+    def __init__(self, n1, n2, n3, edges, kind=CHANNEL3, step2=1.0, step3=1.0, precision=FP64, dx=0.0,
+                 bc_lo=NOSLIP, bc_hi=NOSLIP, device=0, stream=None):
+        import torch
+
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.n1, self.n2, self.n3 = int(n1), int(n2), int(n3)
+        self.device = torch.device("cuda", device)
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._edges = np.ascontiguousarray(edges, dtype=np.float64)
+        if self._edges.shape != (self.n1 + 1,):
+            raise ValueError("edges must have n1 + 1 entries")
+        d = _Desc3(int(precision), self.n1, self.n2, self.n3, int(kind),
+                   self._edges.ctypes.data_as(C.POINTER(C.c_double)), float(step2), float(step3),
+                   float(dx), int(bc_lo), int(bc_hi), self.device.index, self.stream.cuda_stream)
+        h = C.c_void_p()
+        _check(lib().clbm3_create_grid(C.byref(d), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().clbm3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.n1, self.n2, self.n3)
+
+    def set_case(self, tau, rho0=1.0, u_wall_lo=0.0, u_wall_hi=0.0, g_ext=(0.0, 0.0, 0.0)):
+        c = _Case3(float(tau), float(rho0), float(u_wall_lo), float(u_wall_hi),
+                   (C.c_double * 3)(*[float(x) for x in g_ext]))
+        _check(lib().clbm3_set_case(self._h, C.byref(c)))
+
+    def set_state(self, Np, rho_prev=None, ut2_prev=None, ut3_prev=None):
+        dev = _is_device(Np)
+        arrs = []
+        for x in (Np, rho_prev, ut2_prev, ut3_prev):
+            if x is None:
+                arrs.append(None)
+            elif dev:
+                arrs.append(x.to(self._torch.float64).contiguous())
+            else:
+                x = x.cpu().numpy() if hasattr(x, "cpu") else x
+                arrs.append(np.ascontiguousarray(x, dtype=np.float64))
+        if tuple(arrs[0].shape) != (self.Q,) + self.shape:
+            raise ValueError("state must be (39, n1, n2, n3)")
+        _check(lib().clbm3_set_state(self._h, *[_ptr(a) for a in arrs], int(dev)))
+
+    def state(self, device=False):
+        sh = (self.Q,) + self.shape
+        out = (self._torch.empty(sh, dtype=self._torch.float64, device=self.device) if device
+               else np.empty(sh))
+        _check(lib().clbm3_get_state(self._h, _ptr(out), int(device)))
+        return out
+
+    def step(self, n=1):
+        _check(lib().clbm3_step(self._h, int(n)))
+
+    def moments(self):
+        """dict: rho (n1, n2, n3) and Ut (3, n1, n2, n3), float64 numpy."""
+        rho = np.empty(self.shape)
+        ut = np.empty((3,) + self.shape)
+        _check(lib().clbm3_moments(self._h, rho.ctypes.data, ut.ctypes.data, 0))
+        return {"rho": rho, "Ut": ut}
+
+    def totals(self):
+        """(mass, momentum[3]) of the current state: sum N', sum c N'."""
+        out = (C.c_double * 4)()
+        _check(lib().clbm3_totals(self._h, out))
+        return np.array(list(out))
+
+    @property
+    def t(self):
+        v = C.c_longlong()
+        _check(lib().clbm3_time(self._h, C.byref(v)))
+        return v.value

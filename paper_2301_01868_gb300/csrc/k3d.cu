@@ -1,0 +1,820 @@
+// k3d.cu -- the three-dimensional update on D3Q39 (Sec. 2 in three
+// coordinates) and its C ABI (clbm3.h).
+//
+// Layout: deviations sigma_a = N'_a - ref_a(i) in the storage type, one
+// plane per population of (n1 + 2H) x n2 x n3 values, rows 0..H-1 and
+// n1+H..n1+2H-1 the ghost rows of App. B (filled before every update by
+// k3_boundary from the rows inside and the last collision's wall moments),
+// q^2 and q^3 periodic by index wrap.  The geometry of a row (the grids are
+// invariant along q^2 and q^3) is evaluated once in FP64 (k3_geometry,
+// k3_reference) and condensed into a per-row table in the compute type
+// (k3_tables).  One thread per cell (k3_step): pull with the lagged read,
+// moments, lagged force, Ut, the odd part of f^eq for the momentum-flux
+// correction, dN and BGK, written in deviations as the 2-D kernels are.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "clbm3.cuh"
+#include "clbm3.h"
+
+namespace clbm {
+namespace d3 {
+namespace {
+
+constexpr int TB = 128;  // threads per block of the cell kernels
+
+__device__ __forceinline__ int wrapm(int x, int n) {
+    while (x < 0) x += n;
+    while (x >= n) x -= n;
+    return x;
+}
+
+// ------------------------------------------------------------- geometry
+
+struct Shape {
+    int kind, n1, n2;
+    const double* edges;    // device, n1 + 1
+    double step2, step3, dx;
+};
+
+// Wall-normal node coordinate of 1-based row i: midpoints of the edges
+// inside (App. C), mirror images through the walls outside (App. B).
+__device__ double node_coord(const Shape& s, int i) {
+    const double* e = s.edges;
+    if (i >= 1 && i <= s.n1) return 0.5 * (e[i - 1] + e[i]);
+    if (i < 1) {
+        const int m = 1 - i;
+        return 2.0 * e[0] - 0.5 * (e[m - 1] + e[m]);
+    }
+    const int m = s.n1 + 1 - (i - s.n1);
+    return 2.0 * e[s.n1] - 0.5 * (e[m - 1] + e[m]);
+}
+
+__device__ void node_pos(const Shape& s, int i, int j, int k, double x[3]) {
+    const double r = node_coord(s, i);
+    if (s.kind == CLBM3_CHANNEL) {
+        x[0] = r;
+        x[1] = (j - 0.5) * s.step2;
+    } else {
+        const double th = (j - 0.5) * (2.0 * 3.14159265358979323846 / s.n2);
+        x[0] = r * cos(th);
+        x[1] = r * sin(th);
+    }
+    x[2] = (k - 0.5) * s.step3;
+}
+
+// Tangent vector g_m at node (i, j, k): central difference of the node
+// positions over the grid step, divided by 2 Delta x (Eq. 1 and below).
+__device__ void tangent(const Shape& s, int m, int i, int j, int k, double t[3]) {
+    double xp[3], xm[3];
+    node_pos(s, i + (m == 0), j + (m == 1), k + (m == 2), xp);
+    node_pos(s, i - (m == 0), j - (m == 1), k - (m == 2), xm);
+    for (int r = 0; r < 3; ++r) t[r] = (xp[r] - xm[r]) / (2.0 * s.dx);
+}
+
+__device__ void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Row i: J = g_1 . (g_2 x g_3), g^1 = g_2 x g_3 / J and cyclic, g^{pq}, g_pq
+// (Eqs. 2, 3), and a^k_a = sum_m c^m_a (g_m(q + c_a) - g_m(q)) . g^k (Eq. 5).
+__global__ void k3_geometry(Shape s, double* __restrict__ geo) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= s.n1) return;
+    const int i = r + 1;
+    double t[3][3], u[3][3];
+    for (int m = 0; m < 3; ++m) tangent(s, m, i, 1, 1, t[m]);
+    double c12[3];
+    cross3(t[1], t[2], c12);
+    const double J = dot3(t[0], c12);
+    for (int m = 0; m < 3; ++m) {
+        double c[3];
+        cross3(t[(m + 1) % 3], t[(m + 2) % 3], c);
+        for (int q = 0; q < 3; ++q) u[m][q] = c[q] / J;
+    }
+    double* o = geo + (size_t)r * Geo3::S;
+    o[Geo3::J] = J;
+    const int P[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int q = 0; q < 6; ++q) {
+        o[Geo3::GI + q] = dot3(u[P[q][0]], u[P[q][1]]);
+        o[Geo3::GC + q] = dot3(t[P[q][0]], t[P[q][1]]);
+    }
+    for (int a = 0; a < Q; ++a) {
+        const int c[3] = {c1_3(a), c2_3(a), c3_3(a)};
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int m = 0; m < 3; ++m) {
+            if (c[m] == 0) continue;
+            double tn[3], d[3];
+            tangent(s, m, i + c[0], 1 + c[1], 1 + c[2], tn);
+            for (int q = 0; q < 3; ++q) d[q] = tn[q] - t[m][q];
+            for (int kk = 0; kk < 3; ++kk) acc[kk] += c[m] * dot3(d, u[kk]);
+        }
+        for (int kk = 0; kk < 3; ++kk) o[Geo3::A + 3 * a + kk] = acc[kk];
+    }
+}
+
+// Rest polynomial of Eq. 19 at U = Ut = 0: 1 + [c.(g - 1).c / T0 - tr(g - 1)] / 2.
+__device__ double rest_poly3(int a, const double* gi) {
+    const double c[3] = {(double)c1_3(a), (double)c2_3(a), (double)c3_3(a)};
+    const double e11 = gi[0] - 1.0, e12 = gi[1], e13 = gi[2], e22 = gi[3] - 1.0, e23 = gi[4],
+                 e33 = gi[5] - 1.0;
+    const double q = c[0] * c[0] * e11 + c[1] * c[1] * e22 + c[2] * c[2] * e33 +
+                     2.0 * (c[0] * c[1] * e12 + c[0] * c[2] * e13 + c[1] * c[2] * e23);
+    return 1.0 + 0.5 * (q / T0 - (e11 + e22 + e33));
+}
+
+__global__ void k3_reference(double* __restrict__ geo, int n1, double rho0) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n1) return;
+    double* o = geo + (size_t)r * Geo3::S;
+    for (int a = 0; a < Q; ++a) o[Geo3::REF + a] = o[Geo3::J] * w3(a) * rho0 * rest_poly3(a, o + Geo3::GI);
+}
+
+// Reference of direction a at 1-based row i; rows beyond a wall are the
+// mirror images of the rows inside, which flips c^1.
+__device__ double ref_row(const double* geo, int n1, int a, int i) {
+    if (i < 1) return geo[(size_t)(-i) * Geo3::S + Geo3::REF + hat3(a)];
+    if (i > n1) return geo[(size_t)(2 * n1 - i) * Geo3::S + Geo3::REF + hat3(a)];
+    return geo[(size_t)(i - 1) * Geo3::S + Geo3::REF + a];
+}
+
+template <typename C>
+__global__ void k3_tables(const double* __restrict__ geo, C* __restrict__ tab, int n1) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n1) return;
+    const int i = r + 1;
+    const double* g = geo + (size_t)r * Geo3::S;
+    C* t = tab + (size_t)r * Tab3::S;
+    for (int q = 0; q < Tab3::S; ++q) t[q] = C(0);
+    const double J = g[Geo3::J];
+    t[Tab3::INVJ] = C(1.0 / J);
+    t[Tab3::J] = C(J);
+    for (int q = 0; q < 6; ++q) {
+        t[Tab3::G11 + q] = C(g[Geo3::GI + q]);
+        t[Tab3::C11 + q] = C(g[Geo3::GC + q]);
+    }
+    double F0[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < Q; ++a) {
+        const int b = opp3(a);
+        const double ref = g[Geo3::REF + a];
+        for (int k = 0; k < 3; ++k) {
+            t[Tab3::A(a) + k] = C(g[Geo3::A + 3 * a + k]);
+            F0[k] += (g[Geo3::A + 3 * a + k] + g[Geo3::A + 3 * b + k]) * ref;
+        }
+        t[Tab3::A(a) + 3] = C(ref_row(geo, n1, a, i - c1_3(a)) - ref);
+        t[Tab3::P0 + a] = C(rest_poly3(a, g + Geo3::GI));
+    }
+    for (int k = 0; k < 3; ++k) t[Tab3::F0 + k] = C(F0[k]);
+    const int P[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int p = 0; p < NP; ++p) {
+        const int a = plus3(p), b = opp3(a);
+        const double c[3] = {(double)c1_3(a), (double)c2_3(a), (double)c3_3(a)};
+        double D[3];
+        for (int k = 0; k < 3; ++k) D[k] = g[Geo3::A + 3 * a + k] + g[Geo3::A + 3 * b + k];
+        for (int q = 0; q < 6; ++q) {
+            const int x = P[q][0], y = P[q][1];
+            t[Tab3::E(p) + q] = C(w3(a) * (c[x] * D[y] + c[y] * D[x]));
+        }
+    }
+}
+
+// ------------------------------------------------------------- kernels
+
+template <typename S> struct St3;
+template <> struct St3<double> {
+    __device__ static double ld(const double* p) { return *p; }
+    __device__ static void st(double* p, double v) { *p = v; }
+};
+template <> struct St3<float> {
+    __device__ static float ld(const float* p) { return *p; }
+    __device__ static void st(float* p, float v) { *p = v; }
+};
+
+template <typename C>
+__device__ __forceinline__ C* wall_ptr(void* wall, int field, int w, int m, int n23) {
+    return (C*)wall + ((size_t)(field * 2 + w) * H + (m - 1)) * n23;
+}
+
+// Ghost rows of App. B for the buffer the next update reads: at depth m of
+// the low wall the directions with c^1 >= m (high wall: <= -m) take the
+// mirrored fluid node's N'_{a*} (no-slip) or N'_{a-hat} plus the moving-wall
+// term (2/T0) w J rho [c^2 (U0 - Ut^2) + c^3 (0 - Ut^3)] from the last
+// collision's moments there; stored as deviations from the ghost row's
+// reference (the mirrored row's reference of a-hat).
+template <typename S, typename C>
+__global__ void __launch_bounds__(TB) k3_boundary(Args3 A, S* __restrict__ st) {
+    const int n23 = A.n2 * A.n3;
+    const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jk >= n23) return;
+    const int wall = blockIdx.y / H, m = blockIdx.y % H + 1;
+    const int gi = wall == 0 ? 1 - m : A.n1 + m;       // ghost row (1-based)
+    const int mi = wall == 0 ? m : A.n1 + 1 - m;       // mirrored fluid row
+    const bool moving = (wall == 0 ? A.bc_lo : A.bc_hi) == CLBM_BC_MOVING;
+    const C U0 = C(wall == 0 ? A.U0_lo : A.U0_hi);
+    const double* g = A.geo + (size_t)(mi - 1) * Geo3::S;
+    const C rho = wall_ptr<C>(A.wall, 0, wall, m, n23)[jk];
+    const C u2 = wall_ptr<C>(A.wall, 1, wall, m, n23)[jk];
+    const C u3 = wall_ptr<C>(A.wall, 2, wall, m, n23)[jk];
+    const C coef = C(2.0 / T0) * C(g[Geo3::J]) * rho;
+    const S* src = st + (size_t)(mi - 1 + H) * n23 + jk;
+    S* dst = st + (size_t)(gi - 1 + H) * n23 + jk;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int c1 = c1_3(a);
+        if (wall == 0 ? c1 < m : c1 > -m) continue;
+        const int h = hat3(a);
+        C v;
+        if (moving) {
+            v = C(St3<S>::ld(src + (size_t)h * A.plane)) +
+                coef * C(w3(h)) * (C(c2_3(h)) * (U0 - u2) + C(c3_3(h)) * (C(0) - u3));
+        } else {
+            const int b = opp3(a);
+            v = C(St3<S>::ld(src + (size_t)b * A.plane)) + C(g[Geo3::REF + b] - g[Geo3::REF + h]);
+        }
+        St3<S>::st(dst + (size_t)a * A.plane, v);
+    }
+}
+
+// One cell (i, j, k) of the update; MOM: write rho and Ut instead.
+template <typename S, typename C, bool MOM>
+__global__ void __launch_bounds__(TB) k3_step(Args3 A, double* __restrict__ mrho, double* __restrict__ mut) {
+    const int n23 = A.n2 * A.n3;
+    const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jk >= n23) return;
+    const int r = blockIdx.y, i = r + 1;
+    const int j = jk / A.n3, k = jk - j * A.n3;
+    const C* t = (const C*)A.tab + (size_t)r * Tab3::S;
+    const S* src = (const S*)A.src;
+    int jo[7], ko[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        jo[q] = wrapm(j - (q - 3), A.n2) * A.n3;
+        ko[q] = wrapm(k - (q - 3), A.n3);
+    }
+    const size_t own = (size_t)(i - 1 + H) * n23 + jk;
+
+    // pull (Eq. 12) with the lagged read, moments (Eqs. 7-10), lagged force (Eq. 15)
+    C d[Q];
+    C sd = C(0), s1 = C(0), s2 = C(0), s3 = C(0);
+    C f1 = __ldg(t + Tab3::F0), f2 = __ldg(t + Tab3::F0 + 1), f3 = __ldg(t + Tab3::F0 + 2);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int c1 = c1_3(a), c2 = c2_3(a), c3 = c3_3(a);
+        const size_t pidx = (size_t)(i - c1 - 1 + H) * n23 + jo[c2 + 3] + ko[c3 + 3];
+        const C p = C(St3<S>::ld(src + (size_t)a * A.plane + pidx));
+        const C l = C(St3<S>::ld(src + (size_t)a * A.plane + own));
+        const C* ta = t + Tab3::A(a);
+        const C* tb = t + Tab3::A(opp3(a));
+        const C da = c1 != 0 ? p + __ldg(ta + 3) : p;
+        d[a] = da;
+        sd += da;
+        if (c1) s1 += C(c1) * da;
+        if (c2) s2 += C(c2) * da;
+        if (c3) s3 += C(c3) * da;
+        f1 += __ldg(ta) * l + __ldg(tb) * da;
+        f2 += __ldg(ta + 1) * l + __ldg(tb + 1) * da;
+        f3 += __ldg(ta + 2) * l + __ldg(tb + 2) * da;
+    }
+    const C invJ = __ldg(t + Tab3::INVJ), J = __ldg(t + Tab3::J);
+    const C drho = sd * invJ, rho = C(A.rho0) + drho, irho = C(1) / rho;
+    const C U1 = s1 * invJ * irho, U2 = s2 * invJ * irho, U3 = s3 * invJ * irho;
+    const C F1 = C(-0.5) * invJ * f1 + rho * C(A.g1);
+    const C F2 = C(-0.5) * invJ * f2 + rho * C(A.g2);
+    const C F3 = C(-0.5) * invJ * f3 + rho * C(A.g3);
+    const C V1 = U1 + C(0.5) * F1 * irho, V2 = U2 + C(0.5) * F2 * irho, V3 = U3 + C(0.5) * F3 * irho;
+    if (MOM) {
+        const size_t m = (size_t)r * n23 + jk, nc = (size_t)A.n1 * n23;
+        if (mrho) mrho[m] = double(rho);
+        if (mut) {
+            mut[m] = double(V1);
+            mut[nc + m] = double(V2);
+            mut[2 * nc + m] = double(V3);
+        }
+        return;
+    }
+
+    // Eq. 19: third-order coefficients C^{pqr} = Ut Ut Ut + T0 (g Ut - delta U)
+    // (symmetrised), their contraction with the first Hermite term, and the
+    // odd part O_a = c.U / T0 + H3(c) : C / (6 T0^3) of f^eq / (rho w)
+    constexpr C iT0 = C(1.0 / T0), i2T02 = C(0.5 / (T0 * T0)), i6T03 = C(1.0 / (6.0 * T0 * T0 * T0));
+    const C g11 = __ldg(t + Tab3::G11), g12 = __ldg(t + Tab3::G12), g13 = __ldg(t + Tab3::G13);
+    const C g22 = __ldg(t + Tab3::G22), g23 = __ldg(t + Tab3::G23), g33 = __ldg(t + Tab3::G33);
+    const C T = C(T0);
+    const C C111 = V1 * V1 * V1 + T * (C(3) * g11 * V1 - C(3) * U1);
+    const C C222 = V2 * V2 * V2 + T * (C(3) * g22 * V2 - C(3) * U2);
+    const C C333 = V3 * V3 * V3 + T * (C(3) * g33 * V3 - C(3) * U3);
+    const C C112 = V1 * V1 * V2 + T * (g11 * V2 + C(2) * g12 * V1 - U2);
+    const C C113 = V1 * V1 * V3 + T * (g11 * V3 + C(2) * g13 * V1 - U3);
+    const C C122 = V1 * V2 * V2 + T * (g22 * V1 + C(2) * g12 * V2 - U1);
+    const C C133 = V1 * V3 * V3 + T * (g33 * V1 + C(2) * g13 * V3 - U1);
+    const C C223 = V2 * V2 * V3 + T * (g22 * V3 + C(2) * g23 * V2 - U3);
+    const C C233 = V2 * V3 * V3 + T * (g33 * V2 + C(2) * g23 * V3 - U2);
+    const C C123 = V1 * V2 * V3 + T * (g12 * V3 + g23 * V1 + g13 * V2);
+    const C K1 = U1 * iT0 - (C111 + C122 + C133) * i2T02;
+    const C K2 = U2 * iT0 - (C112 + C222 + C233) * i2T02;
+    const C K3 = U3 * iT0 - (C113 + C223 + C333) * i2T02;
+    const C k111 = C111 * i6T03, k222 = C222 * i6T03, k333 = C333 * i6T03;
+    const C k112 = C(3) * C112 * i6T03, k113 = C(3) * C113 * i6T03, k122 = C(3) * C122 * i6T03;
+    const C k133 = C(3) * C133 * i6T03, k223 = C(3) * C223 * i6T03, k233 = C(3) * C233 * i6T03;
+    const C k123 = C(6) * C123 * i6T03;
+
+    // symmetric momentum-flux correction (Eq. 16): only the odd part of f^eq
+    // survives the pair sums, weighed by w (c^p D^r + c^r D^p)
+    C O[NP];
+    C P11 = C(0), P22 = C(0), P33 = C(0), P12 = C(0), P13 = C(0), P23 = C(0);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int a = plus3(p);
+        const C x = C(c1_3(a)), y = C(c2_3(a)), z = C(c3_3(a));
+        const C o = K1 * x + K2 * y + K3 * z + k111 * (x * x * x) + k222 * (y * y * y) + k333 * (z * z * z) +
+                    k112 * (x * x * y) + k113 * (x * x * z) + k122 * (x * y * y) + k133 * (x * z * z) +
+                    k223 * (y * y * z) + k233 * (y * z * z) + k123 * (x * y * z);
+        O[p] = o;
+        const C* e = t + Tab3::E(p);
+        P11 += __ldg(e) * o;
+        P22 += __ldg(e + 1) * o;
+        P33 += __ldg(e + 2) * o;
+        P12 += __ldg(e + 3) * o;
+        P13 += __ldg(e + 4) * o;
+        P23 += __ldg(e + 5) * o;
+    }
+    const C pr = C(A.pref) * rho;
+    P11 *= pr;
+    P22 *= pr;
+    P33 *= pr;
+    P12 *= pr;
+    P13 *= pr;
+    P23 *= pr;
+    const C trP = P11 + P22 + P33;
+
+    // BGK (Eqs. 6, 11) with dN (Eq. 17), in deviations:
+    // sigma'_a = (1 - 1/tau) d_a + J w [(drho P0_a + rho Pi_a) / tau + c.F / T0
+    //            + (c.dPi.c / T0 - tr dPi) / T0],  Pi_a = f^eq_a / (rho w) - P0_a
+    const C tinv = C(A.tau_inv), omt = C(A.omt);
+    const C uu = V1 * V1 + V2 * V2 + V3 * V3;
+    const C base = C(-0.5) * iT0 * uu * rho * tinv - trP * iT0;
+    S* dst = (S*)A.dst + own;
+    St3<S>::st(dst, S(omt * d[0] + J * C(w3(0)) * (drho * __ldg(t + Tab3::P0) * tinv + base)));
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int a = plus3(p), b = opp3(a);
+        const C x = C(c1_3(a)), y = C(c2_3(a)), z = C(c3_3(a));
+        const C cu = x * V1 + y * V2 + z * V3;
+        const C cPc = x * x * P11 + y * y * P22 + z * z * P33 + C(2) * (x * y * P12 + x * z * P13 + y * z * P23);
+        const C X = drho * __ldg(t + Tab3::P0 + a) * tinv + rho * tinv * (cu * cu) * i2T02 + cPc * (iT0 * iT0) +
+                    base;
+        const C Y = rho * tinv * O[p] + (x * F1 + y * F2 + z * F3) * iT0;
+        const C Jw = J * C(w3(a));
+        St3<S>::st(dst + (size_t)a * A.plane, S(omt * d[a] + Jw * (X + Y)));
+        St3<S>::st(dst + (size_t)b * A.plane, S(omt * d[b] + Jw * (X - Y)));
+    }
+    // the moments the walls read next (rows within H of a wall)
+    if (i <= H) {
+        wall_ptr<C>(A.wall, 0, 0, i, n23)[jk] = rho;
+        wall_ptr<C>(A.wall, 1, 0, i, n23)[jk] = V2;
+        wall_ptr<C>(A.wall, 2, 0, i, n23)[jk] = V3;
+    }
+    if (i > A.n1 - H) {
+        const int m = A.n1 + 1 - i;
+        wall_ptr<C>(A.wall, 0, 1, m, n23)[jk] = rho;
+        wall_ptr<C>(A.wall, 1, 1, m, n23)[jk] = V2;
+        wall_ptr<C>(A.wall, 2, 1, m, n23)[jk] = V3;
+    }
+}
+
+// State conversions between FP64 N' ([a][cell]) and stored deviations.
+template <typename S>
+__global__ void k3_from64(const double* __restrict__ Np, const double* __restrict__ geo, S* __restrict__ st,
+                          int n1, int n23, long long plane) {
+    const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jk >= n23) return;
+    const int r = blockIdx.y;
+    const size_t nc = (size_t)n1 * n23, m = (size_t)r * n23 + jk, own = (size_t)(r + H) * n23 + jk;
+    const double* g = geo + (size_t)r * Geo3::S;
+    for (int a = 0; a < Q; ++a) st[(size_t)a * plane + own] = S(Np ? Np[a * nc + m] - g[Geo3::REF + a] : 0.0);
+}
+
+template <typename S>
+__global__ void k3_to64(const S* __restrict__ st, const double* __restrict__ geo, double* __restrict__ Np, int n1,
+                        int n23, long long plane) {
+    const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jk >= n23) return;
+    const int r = blockIdx.y;
+    const size_t nc = (size_t)n1 * n23, m = (size_t)r * n23 + jk, own = (size_t)(r + H) * n23 + jk;
+    const double* g = geo + (size_t)r * Geo3::S;
+    for (int a = 0; a < Q; ++a) Np[a * nc + m] = double(st[(size_t)a * plane + own]) + g[Geo3::REF + a];
+}
+
+// Wall moments of rows 1..H and n1-H+1..n1 from cell fields (NULL: rho0, 0).
+template <typename C>
+__global__ void k3_wall_init(void* wall, const double* rho, const double* u2, const double* u3, int n1, int n23,
+                             double rho0) {
+    const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jk >= n23) return;
+    const int w = blockIdx.y / H, m = blockIdx.y % H + 1;
+    const int row = w == 0 ? m - 1 : n1 - m;          // 0-based fluid row
+    const size_t c = (size_t)row * n23 + jk;
+    wall_ptr<C>(wall, 0, w, m, n23)[jk] = C(rho ? rho[c] : rho0);
+    wall_ptr<C>(wall, 1, w, m, n23)[jk] = C(u2 ? u2[c] : 0.0);
+    wall_ptr<C>(wall, 2, w, m, n23)[jk] = C(u3 ? u3[c] : 0.0);
+}
+
+// Totals of the stored deviations per block (sum sigma, sum c sigma), fixed
+// order; the rest part sum ref = rho0 J per cell is added on the host.
+template <typename S>
+__global__ void __launch_bounds__(TB) k3_totals(const S* __restrict__ st, int n1, int n23, long long plane,
+                                                double* __restrict__ partial) {
+    const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (jk < n23) {
+        const size_t own = (size_t)(r + H) * n23 + jk;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const double s = double(st[(size_t)a * plane + own]);
+            v[0] += s;
+            v[1] += c1_3(a) * s;
+            v[2] += c2_3(a) * s;
+            v[3] += c3_3(a) * s;
+        }
+    }
+    __shared__ double sh[4][TB];
+    for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int w = TB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) partial[((size_t)r * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k3_totals_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+    __shared__ double sh[256];
+    const int q = blockIdx.x;
+    double x = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) x += partial[(size_t)b * 4 + q];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sh[0];
+}
+
+}  // namespace
+}  // namespace d3
+}  // namespace clbm
+
+// ------------------------------------------------------------------ C ABI
+
+using namespace clbm::d3;
+
+struct clbm3_grid {
+    int prec, n1, n2, n3, kind, bc_lo, bc_hi, device;
+    double step2, step3, dx;
+    cudaStream_t stream;
+    double *edges, *geo, *partial, *red, *stage;
+    void *tab, *st[2], *wall;
+    int cur;                  // index of the buffer holding N'(t-1)
+    clbm3_case cs;
+    bool have_case;
+    long long t;
+    std::vector<double> hedges;
+};
+
+namespace {
+
+clbm_status fail3(clbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    clbm::set_last_error(buf);
+    return s;
+}
+
+#define CK3(call)                                                                             \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail3(CLBM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                           \
+    } while (0)
+
+size_t sbytes(const clbm3_grid* g) { return g->prec == CLBM_FP64 ? 8 : 4; }
+int n23(const clbm3_grid* g) { return g->n2 * g->n3; }
+long long plane(const clbm3_grid* g) { return (long long)(g->n1 + 2 * H) * g->n2 * g->n3; }
+size_t ncells(const clbm3_grid* g) { return (size_t)g->n1 * g->n2 * g->n3; }
+dim3 cell_grid(const clbm3_grid* g) { return dim3((n23(g) + TB - 1) / TB, g->n1); }
+
+Args3 args(const clbm3_grid* g) {
+    Args3 A;
+    memset(&A, 0, sizeof(A));
+    A.src = g->st[g->cur];
+    A.dst = g->st[g->cur ^ 1];
+    A.tab = g->tab;
+    A.geo = g->geo;
+    A.wall = g->wall;
+    A.n1 = g->n1;
+    A.n2 = g->n2;
+    A.n3 = g->n3;
+    A.plane = plane(g);
+    A.bc_lo = g->bc_lo;
+    A.bc_hi = g->bc_hi;
+    A.rho0 = g->cs.rho0;
+    A.tau_inv = 1.0 / g->cs.tau;
+    A.omt = 1.0 - 1.0 / g->cs.tau;
+    A.pref = -0.5 * (1.0 - 1.0 / (2.0 * g->cs.tau));
+    A.g1 = g->cs.g_ext[0];
+    A.g2 = g->cs.g_ext[1];
+    A.g3 = g->cs.g_ext[2];
+    A.U0_lo = g->cs.u_wall_lo;
+    A.U0_hi = g->cs.u_wall_hi;
+    return A;
+}
+
+void launch_boundary(const clbm3_grid* g, const Args3& A) {
+    dim3 grid((n23(g) + TB - 1) / TB, 2 * H);
+    if (g->prec == CLBM_FP64)
+        k3_boundary<double, double><<<grid, TB, 0, g->stream>>>(A, (double*)A.src);
+    else
+        k3_boundary<float, float><<<grid, TB, 0, g->stream>>>(A, (float*)A.src);
+}
+
+template <bool MOM>
+void launch_cells(const clbm3_grid* g, const Args3& A, double* rho, double* ut) {
+    if (g->prec == CLBM_FP64)
+        k3_step<double, double, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
+    else
+        k3_step<float, float, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
+}
+
+clbm_status staging(clbm3_grid* g, double** out) {
+    if (!g->stage) {
+        const size_t n = (size_t)Q * ncells(g);
+        if (cudaMalloc((void**)&g->stage, n * 8) != cudaSuccess) {
+            g->stage = nullptr;
+            cudaGetLastError();
+            return fail3(CLBM_ENOMEM, "no device memory for the FP64 staging buffer (%zu bytes)", n * 8);
+        }
+    }
+    *out = g->stage;
+    return CLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+clbm_status clbm3_create_grid(const clbm3_grid_desc* d, clbm3_handle* out) {
+    if (!d || !out) return fail3(CLBM_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (d->precision != CLBM_FP64 && d->precision != CLBM_FP32)
+        return fail3(CLBM_EINVAL, "precision must be CLBM_FP64 or CLBM_FP32");
+    if (d->n1 < 4 || d->n2 < 1 || d->n3 < 1) return fail3(CLBM_EINVAL, "need n1 >= 4 and n2, n3 >= 1");
+    if ((long long)(d->n1 + 2 * H) * d->n2 * d->n3 > (1LL << 31) / 2)
+        return fail3(CLBM_EINVAL, "grid too large");
+    if (d->kind != CLBM3_CHANNEL && d->kind != CLBM3_ANNULUS) return fail3(CLBM_EINVAL, "bad kind");
+    if (!d->edges) return fail3(CLBM_EINVAL, "edges is NULL");
+    for (int i = 0; i < d->n1; ++i)
+        if (!(d->edges[i + 1] > d->edges[i])) return fail3(CLBM_EINVAL, "edges must increase");
+    if (d->kind == CLBM3_ANNULUS && !(d->edges[0] > 0.0)) return fail3(CLBM_EINVAL, "radii must be > 0");
+    if (!(d->step3 > 0.0) || (d->kind == CLBM3_CHANNEL && !(d->step2 > 0.0)))
+        return fail3(CLBM_EINVAL, "node spacings must be > 0");
+    if ((d->bc_lo != CLBM_BC_NOSLIP && d->bc_lo != CLBM_BC_MOVING) ||
+        (d->bc_hi != CLBM_BC_NOSLIP && d->bc_hi != CLBM_BC_MOVING))
+        return fail3(CLBM_EINVAL, "bad wall condition");
+    CK3(cudaSetDevice(d->device));
+    clbm3_grid* g = new clbm3_grid();
+    g->prec = d->precision;
+    g->n1 = d->n1;
+    g->n2 = d->n2;
+    g->n3 = d->n3;
+    g->kind = d->kind;
+    g->bc_lo = d->bc_lo;
+    g->bc_hi = d->bc_hi;
+    g->device = d->device;
+    g->step2 = d->step2;
+    g->step3 = d->step3;
+    g->dx = d->dx > 0.0 ? d->dx : (d->edges[d->n1] - d->edges[0]) / d->n1;
+    g->stream = (cudaStream_t)d->stream;
+    g->hedges.assign(d->edges, d->edges + d->n1 + 1);
+    const size_t sb = sbytes(g), cb = sb;  // compute type = storage type
+    const size_t nb = (size_t)((n23(g) + TB - 1) / TB) * g->n1;
+    bool ok = cudaMalloc((void**)&g->edges, (g->n1 + 1) * 8) == cudaSuccess &&
+              cudaMalloc((void**)&g->geo, (size_t)g->n1 * Geo3::S * 8) == cudaSuccess &&
+              cudaMalloc(&g->tab, (size_t)g->n1 * Tab3::S * cb) == cudaSuccess &&
+              cudaMalloc(&g->st[0], (size_t)Q * plane(g) * sb) == cudaSuccess &&
+              cudaMalloc(&g->st[1], (size_t)Q * plane(g) * sb) == cudaSuccess &&
+              cudaMalloc(&g->wall, (size_t)3 * 2 * H * n23(g) * cb) == cudaSuccess &&
+              cudaMalloc((void**)&g->partial, nb * 4 * 8) == cudaSuccess &&
+              cudaMalloc((void**)&g->red, 4 * 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        clbm3_destroy(g);
+        return fail3(CLBM_ENOMEM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(g->edges, d->edges, (g->n1 + 1) * 8, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->st[0], 0, (size_t)Q * plane(g) * sb, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->st[1], 0, (size_t)Q * plane(g) * sb, g->stream);
+    if (e == cudaSuccess) {
+        Shape s{g->kind, g->n1, g->n2, g->edges, g->step2, g->step3, g->dx};
+        k3_geometry<<<(g->n1 + 63) / 64, 64, 0, g->stream>>>(s, g->geo);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        clbm3_destroy(g);
+        return fail3(CLBM_ECUDA, "geometry precompute failed: %s", cudaGetErrorString(e));
+    }
+    *out = g;
+    return CLBM_OK;
+}
+
+clbm_status clbm3_set_case(clbm3_handle g, const clbm3_case* c) {
+    if (!g || !c) return fail3(CLBM_EINVAL, "NULL argument");
+    if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return fail3(CLBM_EINVAL, "tau must be > 1/2");
+    if (!(c->rho0 > 0.0) || !std::isfinite(c->rho0)) return fail3(CLBM_EINVAL, "rho0 must be > 0");
+    CK3(cudaSetDevice(g->device));
+    g->cs = *c;
+    g->have_case = true;
+    k3_reference<<<(g->n1 + 63) / 64, 64, 0, g->stream>>>(g->geo, g->n1, c->rho0);
+    if (g->prec == CLBM_FP64)
+        k3_tables<double><<<(g->n1 + 63) / 64, 64, 0, g->stream>>>(g->geo, (double*)g->tab, g->n1);
+    else
+        k3_tables<float><<<(g->n1 + 63) / 64, 64, 0, g->stream>>>(g->geo, (float*)g->tab, g->n1);
+    g->cur = 0;
+    CK3(cudaMemsetAsync(g->st[0], 0, (size_t)Q * plane(g) * sbytes(g), g->stream));
+    dim3 wg((n23(g) + TB - 1) / TB, 2 * H);
+    if (g->prec == CLBM_FP64)
+        k3_wall_init<double><<<wg, TB, 0, g->stream>>>(g->wall, nullptr, nullptr, nullptr, g->n1, n23(g), c->rho0);
+    else
+        k3_wall_init<float><<<wg, TB, 0, g->stream>>>(g->wall, nullptr, nullptr, nullptr, g->n1, n23(g), c->rho0);
+    CK3(cudaGetLastError());
+    CK3(cudaStreamSynchronize(g->stream));
+    g->t = 0;
+    return CLBM_OK;
+}
+
+clbm_status clbm3_set_state(clbm3_handle g, const double* Np, const double* rho, const double* u2,
+                            const double* u3, int src_is_device) {
+    if (!g || !Np) return fail3(CLBM_EINVAL, "NULL argument");
+    if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
+    CK3(cudaSetDevice(g->device));
+    const size_t nc = ncells(g);
+    const double *dN = Np, *dr = rho, *d2 = u2, *d3 = u3;
+    double* extra = nullptr;
+    if (!src_is_device) {
+        double* sb = nullptr;
+        clbm_status st = staging(g, &sb);
+        if (st != CLBM_OK) return st;
+        CK3(cudaMemcpyAsync(sb, Np, (size_t)Q * nc * 8, cudaMemcpyHostToDevice, g->stream));
+        dN = sb;
+        dr = d2 = d3 = nullptr;
+        if (rho || u2 || u3) {
+            CK3(cudaMalloc((void**)&extra, 3 * nc * 8));
+            const double* h[3] = {rho, u2, u3};
+            const double** dd[3] = {&dr, &d2, &d3};
+            for (int q = 0; q < 3; ++q)
+                if (h[q]) {
+                    CK3(cudaMemcpyAsync(extra + q * nc, h[q], nc * 8, cudaMemcpyHostToDevice, g->stream));
+                    *dd[q] = extra + q * nc;
+                }
+        }
+    }
+    dim3 cg((n23(g) + TB - 1) / TB, g->n1), wg((n23(g) + TB - 1) / TB, 2 * H);
+    g->cur = 0;
+    if (g->prec == CLBM_FP64) {
+        k3_from64<double><<<cg, TB, 0, g->stream>>>(dN, g->geo, (double*)g->st[0], g->n1, n23(g), plane(g));
+        k3_wall_init<double><<<wg, TB, 0, g->stream>>>(g->wall, dr, d2, d3, g->n1, n23(g), g->cs.rho0);
+    } else {
+        k3_from64<float><<<cg, TB, 0, g->stream>>>(dN, g->geo, (float*)g->st[0], g->n1, n23(g), plane(g));
+        k3_wall_init<float><<<wg, TB, 0, g->stream>>>(g->wall, dr, d2, d3, g->n1, n23(g), g->cs.rho0);
+    }
+    CK3(cudaGetLastError());
+    CK3(cudaStreamSynchronize(g->stream));
+    if (extra) cudaFree(extra);
+    return CLBM_OK;
+}
+
+clbm_status clbm3_get_state(clbm3_handle g, double* Np, int dst_is_device) {
+    if (!g || !Np) return fail3(CLBM_EINVAL, "NULL argument");
+    if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
+    CK3(cudaSetDevice(g->device));
+    double* dN = Np;
+    if (!dst_is_device) {
+        clbm_status st = staging(g, &dN);
+        if (st != CLBM_OK) return st;
+    }
+    dim3 cg((n23(g) + TB - 1) / TB, g->n1);
+    if (g->prec == CLBM_FP64)
+        k3_to64<double><<<cg, TB, 0, g->stream>>>((const double*)g->st[g->cur], g->geo, dN, g->n1, n23(g), plane(g));
+    else
+        k3_to64<float><<<cg, TB, 0, g->stream>>>((const float*)g->st[g->cur], g->geo, dN, g->n1, n23(g), plane(g));
+    CK3(cudaGetLastError());
+    if (!dst_is_device)
+        CK3(cudaMemcpyAsync(Np, dN, (size_t)Q * ncells(g) * 8, cudaMemcpyDeviceToHost, g->stream));
+    CK3(cudaStreamSynchronize(g->stream));
+    return CLBM_OK;
+}
+
+clbm_status clbm3_step(clbm3_handle g, long long n) {
+    if (!g) return fail3(CLBM_EINVAL, "handle is NULL");
+    if (n < 0) return fail3(CLBM_EINVAL, "n < 0");
+    if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
+    CK3(cudaSetDevice(g->device));
+    for (long long s = 0; s < n; ++s) {
+        const Args3 A = args(g);
+        launch_boundary(g, A);
+        launch_cells<false>(g, A, nullptr, nullptr);
+        g->cur ^= 1;
+        g->t++;
+    }
+    CK3(cudaGetLastError());
+    return CLBM_OK;
+}
+
+clbm_status clbm3_moments(clbm3_handle g, double* rho, double* ut, int dst_is_device) {
+    if (!g) return fail3(CLBM_EINVAL, "handle is NULL");
+    if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
+    CK3(cudaSetDevice(g->device));
+    const size_t nc = ncells(g);
+    double *dr = rho, *du = ut;
+    if (!dst_is_device) {
+        double* sb = nullptr;
+        clbm_status st = staging(g, &sb);
+        if (st != CLBM_OK) return st;
+        dr = rho ? sb : nullptr;
+        du = ut ? sb + nc : nullptr;
+    }
+    const Args3 A = args(g);
+    launch_boundary(g, A);
+    launch_cells<true>(g, A, dr, du);
+    CK3(cudaGetLastError());
+    if (!dst_is_device) {
+        if (rho) CK3(cudaMemcpyAsync(rho, dr, nc * 8, cudaMemcpyDeviceToHost, g->stream));
+        if (ut) CK3(cudaMemcpyAsync(ut, du, 3 * nc * 8, cudaMemcpyDeviceToHost, g->stream));
+    }
+    CK3(cudaStreamSynchronize(g->stream));
+    return CLBM_OK;
+}
+
+clbm_status clbm3_totals(clbm3_handle g, double out[4]) {
+    if (!g || !out) return fail3(CLBM_EINVAL, "NULL argument");
+    if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
+    CK3(cudaSetDevice(g->device));
+    dim3 cg((n23(g) + TB - 1) / TB, g->n1);
+    const int nb = (int)(cg.x * cg.y);
+    if (g->prec == CLBM_FP64)
+        k3_totals<double><<<cg, TB, 0, g->stream>>>((const double*)g->st[g->cur], g->n1, n23(g), plane(g), g->partial);
+    else
+        k3_totals<float><<<cg, TB, 0, g->stream>>>((const float*)g->st[g->cur], g->n1, n23(g), plane(g), g->partial);
+    k3_totals_final<<<4, 256, 0, g->stream>>>(g->partial, nb, g->red);
+    CK3(cudaGetLastError());
+    double v[4];
+    std::vector<double> geo((size_t)g->n1 * Geo3::S);
+    CK3(cudaMemcpyAsync(v, g->red, sizeof(v), cudaMemcpyDeviceToHost, g->stream));
+    CK3(cudaMemcpyAsync(geo.data(), g->geo, geo.size() * 8, cudaMemcpyDeviceToHost, g->stream));
+    CK3(cudaStreamSynchronize(g->stream));
+    double rest = 0.0;  // sum of ref over the cells: rho0 J per cell
+    for (int r = 0; r < g->n1; ++r) rest += g->cs.rho0 * geo[(size_t)r * Geo3::S + Geo3::J];
+    out[0] = v[0] + rest * n23(g);
+    for (int q = 1; q < 4; ++q) out[q] = v[q];
+    return CLBM_OK;
+}
+
+clbm_status clbm3_time(clbm3_handle g, long long* t) {
+    if (!g || !t) return fail3(CLBM_EINVAL, "NULL argument");
+    *t = g->t;
+    return CLBM_OK;
+}
+
+clbm_status clbm3_destroy(clbm3_handle g) {
+    if (!g) return CLBM_OK;
+    cudaSetDevice(g->device);
+    cudaFree(g->edges);
+    cudaFree(g->geo);
+    cudaFree(g->tab);
+    cudaFree(g->st[0]);
+    cudaFree(g->st[1]);
+    cudaFree(g->wall);
+    cudaFree(g->partial);
+    cudaFree(g->red);
+    cudaFree(g->stage);
+    delete g;
+    return CLBM_OK;
+}
+
+}  // extern "C"

@@ -16,7 +16,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(clbm_\w+)\s*\(", txt, flags=re.M):
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(clbm3?_\w+)\s*\(", txt, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
 
@@ -34,7 +34,8 @@ def libpath():
 def test_header_declares_entry_points():
     names = _declared()
     for must in ("clbm_create_grid", "clbm_set_case", "clbm_step", "clbm_moments",
-                 "clbm_residual", "clbm_destroy"):
+                 "clbm_residual", "clbm_destroy", "clbm3_create_grid", "clbm3_step",
+                 "clbm3_moments", "clbm3_totals"):
         assert must in names
 
 

@@ -1,0 +1,151 @@
+"""The three-dimensional update (D3Q39, clbm3.h) on the GPU against the 3-D
+FP64 oracle: state, moments and totals on channel and annulus grids, both
+wall conditions, body force, ragged block tails, degenerate periodic sizes,
+FP32; plus conservation and run-to-run identity."""
+import math
+
+import numpy as np
+import pytest
+
+import clbm_inputs as I
+from oracle import oracle3d as O3
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _clbm():
+    from paper_2301_01868_gb300 import clbm
+    return clbm
+
+
+class Case3:
+    def __init__(self, n1, n2, n3, kind=0, edges=None, step2=1.0, step3=1.0, bc=(0, 0), tau=0.8,
+                 U0=(0.0, 0.0), g=(0.0, 0.0, 0.0)):
+        self.n1, self.n2, self.n3, self.kind = n1, n2, n3, kind
+        self.edges = np.arange(n1 + 1.0) if edges is None else edges
+        self.step2, self.step3, self.bc, self.tau, self.U0, self.g = step2, step3, bc, tau, U0, g
+
+    def oracle(self):
+        o = O3.Grid(self.n1, self.n2, self.n3, self.kind, edges=self.edges, step2=self.step2,
+                    step3=self.step3, bc_lo=self.bc[0], bc_hi=self.bc[1])
+        o.set_case(self.tau, 1.0, self.U0[0], self.U0[1], self.g)
+        o.init_rest()
+        return o
+
+    def gpu(self, prec=0):
+        c = _clbm()
+        g = c.Grid3(self.n1, self.n2, self.n3, self.edges, kind=self.kind, step2=self.step2,
+                    step3=self.step3, precision=prec, bc_lo=self.bc[0], bc_hi=self.bc[1])
+        g.set_case(self.tau, 1.0, self.U0[0], self.U0[1], self.g)
+        return g
+
+
+def perturbed(o, seed, amp):
+    st = o.state()
+    Q, n1, n2, n3 = st.shape
+    f = I.smooth_field((Q * n1, n2, n3), seed=seed, amplitude=amp).reshape(st.shape)
+    return st * (1.0 + f)
+
+
+def run_pair(case, steps, prec=0, seed=5, amp=2e-3):
+    o = case.oracle()
+    g = case.gpu(prec)
+    if amp:
+        st = perturbed(o, seed, amp)
+        o.set_state(st)
+        g.set_state(st)
+    o.step(steps)
+    g.step(steps)
+    return o, g
+
+
+def rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def stretched_channel(n1=10, n2=6, n3=5, **kw):
+    e = I.geometric_stretch_edges(n1, 1.06, float(n1))
+    dx = (e[-1] - e[0]) / n1
+    return Case3(n1, n2, n3, 0, edges=e, step2=dx, step3=dx, **kw)
+
+
+def test_fp64_channel_state_matches_oracle():
+    """Stretched channel, moving low wall, body force along q^3, a start
+    that depends on all three coordinates."""
+    case = stretched_channel(bc=(1, 0), U0=(0.02, 0.0), g=(0.0, 1e-6, 2e-6))
+    o, g = run_pair(case, 100)
+    assert rel(g.state(), o.state()) <= 1e-13
+    mo, mg = o.moments(), g.moments()
+    assert np.abs(mg["rho"] - mo["rho"]).max() <= 1e-13
+    assert rel(mg["Ut"], mo["Ut"]) <= 1e-11
+
+
+def test_fp64_annulus_matches_oracle():
+    e = I.polar_edges(1.0, 2.0, 8, 0.35)
+    case = Case3(8, 50, 3, 1, edges=e, step3=0.15, bc=(1, 0), U0=(0.05, 0.0), g=(0.0, 0.0, 1e-6))
+    o, g = run_pair(case, 100, amp=1e-3)
+    assert rel(g.state(), o.state()) <= 1e-13
+    mo, mg = o.moments(), g.moments()
+    assert rel(mg["Ut"], mo["Ut"]) <= 1e-11
+
+
+def test_fp64_no_slip_walls_ragged_blocks():
+    """Rows of 13 x 11 = 143 cells: two blocks, the second ragged."""
+    case = stretched_channel(n1=6, n2=13, n3=11, g=(0.0, 2e-6, 0.0))
+    o, g = run_pair(case, 60, seed=9)
+    assert rel(g.state(), o.state()) <= 1e-13
+
+
+def test_fp64_degenerate_periodic_sizes():
+    """n2 = n3 = 1: every neighbour along q^2 and q^3 is the cell itself."""
+    case = Case3(8, 1, 1, 0, bc=(1, 0), U0=(0.03, 0.0), g=(0.0, 0.0, 1e-5))
+    o, g = run_pair(case, 300, amp=0.0)
+    assert rel(g.state(), o.state()) <= 1e-13
+
+
+def test_fp32_channel_velocity_matches_oracle():
+    case = stretched_channel(bc=(1, 0), U0=(0.02, 0.0), g=(0.0, 1e-6, 2e-6))
+    o, g = run_pair(case, 200, prec=1)
+    assert rel(g.moments()["Ut"], o.moments()["Ut"]) <= 1e-5
+
+
+def test_totals_conserve_mass_and_match_oracle():
+    case = stretched_channel(bc=(0, 0), g=(0.0, 0.0, 0.0))
+    o, g = run_pair(case, 0)
+    t0 = g.totals()
+    np.testing.assert_allclose(t0, o.totals(), rtol=1e-13, atol=1e-13)
+    o.step(150)
+    g.step(150)
+    t1 = g.totals()
+    assert abs(t1[0] - t0[0]) <= 1e-13 * abs(t0[0])
+    np.testing.assert_allclose(t1, o.totals(), rtol=1e-12, atol=1e-12)
+
+
+def test_two_runs_are_bitwise_identical():
+    case = stretched_channel(n1=12, n2=20, n3=16, bc=(1, 0), U0=(0.02, 0.0))
+    out = []
+    for _ in range(2):
+        o = case.oracle()
+        g = case.gpu(1)
+        g.set_state(perturbed(o, 3, 1e-3))
+        g.step(50)
+        out.append(g.state())
+        g.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_grid_rejects_bad_descriptions():
+    c = _clbm()
+    with pytest.raises(c.ClbmError):
+        c.Grid3(3, 4, 4, np.arange(4.0))
+    with pytest.raises(c.ClbmError):
+        c.Grid3(6, 4, 4, np.array([0, 1, 2, 2, 3, 4, 5.0]))
+    with pytest.raises(c.ClbmError):
+        c.Grid3(6, 4, 4, np.arange(7.0), precision=2)
+    g = c.Grid3(6, 4, 4, np.arange(7.0))
+    with pytest.raises(c.ClbmError):
+        g.step(1)                 # no case yet
+    with pytest.raises(c.ClbmError):
+        g.set_case(0.5)
