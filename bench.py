@@ -48,6 +48,11 @@ GENERAL_WORKLOADS = {
     "wavy_channel_d2q21_fp32_1024x4096": (21, "fp32", 1024, 4096, 0.15, 0.8, 0.01),
 }
 TABLE_VALUES_PER_CELL = {21: 73, 9: 37}   # per-cell table entries of general grids
+# three-dimensional workloads (D3Q39): name -> (precision, n1, n2, n3, R1, R2, CR, tau, u_wall)
+THREE_D_WORKLOADS = {
+    "annulus3d_d3q39_fp32_128x804x32": ("fp32", 128, 804, 32, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "annulus3d_d3q39_fp64_128x804x32": ("fp64", 128, 804, 32, 1.0, 2.0, 0.35, 0.8, 0.01),
+}
 DEFAULT = "circular_couette_d2q21_fp32_1024x4096"
 METRIC = "D2Q21 curvilinear MLUPS and % HBM roofline; served solves/s, p99 latency"
 STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
@@ -279,11 +284,15 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="only the batched form against per-lattice launches (512 lattices)")
     ap.add_argument("--batch-lattices", type=int, default=512)
+    ap.add_argument("--three-d", default=None, choices=sorted(THREE_D_WORKLOADS),
+                    help="only the three-dimensional (D3Q39) update on this workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.three_d:
+        return run_3d(args)
     if args.serve:
         print(json.dumps(run_serving(args.serve_requests, verbose=True)))
         return
@@ -379,6 +388,90 @@ def main():
     g.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def annulus3d(wl):
+    prec, n1, n2, n3, R1, R2, CR, tau, uw = THREE_D_WORKLOADS[wl]
+    e = I.polar_edges(R1, R2, n1, CR)
+    dx = (R2 - R1) / n1
+    U0 = uw * dx / (R1 * math.sin(2.0 * math.pi / n2))
+    return prec, n1, n2, n3, e, dx, tau, U0
+
+
+def cpu_baseline_3d(wl, target_s=10.0):
+    """The FP64 3-D oracle on this host: MLUPS on a bounded sample of the
+    workload (the same annulus at n1 / 8 x n2 / 8 x 4 cells)."""
+    from oracle import oracle3d as O3
+    prec, n1, n2, n3, e, dx, tau, U0 = annulus3d(wl)
+    m1, m2, m3 = n1 // 8, n2 // 8, 4
+    R1, R2 = e[0], e[-1]
+    es = I.polar_edges(R1, R2, m1, THREE_D_WORKLOADS[wl][6])
+    o = O3.Grid(m1, m2, m3, O3.ANNULUS, edges=es, step3=(R2 - R1) / m1, bc_lo=O3.MOVING, bc_hi=O3.NOSLIP)
+    o.set_case(tau, 1.0, U0, 0.0)
+    o.init_rest()
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(50, int(target_s / max(t1, 1e-9)) - 1))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": m1 * m2 * m3 * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d time steps of the same annulus at %dx%dx%d, D3Q39 FP64 oracle (%.1f s)"
+                      % (n, m1, m2, m3, dt)}
+
+
+def run_3d(args):
+    """--three-d WL: the D3Q39 update on an extruded annulus, timed like the
+    main line (chunk time steps per bench step, CUDA events on the grid's
+    stream); roofline on the whole step (ghost rows + update launches)."""
+    import torch
+    from paper_2301_01868_gb300 import clbm
+    wl = args.three_d
+    prec, n1, n2, n3, e, dx, tau, U0 = annulus3d(wl)
+    stream = torch.cuda.Stream()
+    g = clbm.Grid3(n1, n2, n3, e, kind=clbm.ANNULUS3, step3=dx, precision=prec, bc_lo=clbm.MOVING,
+                   bc_hi=clbm.NOSLIP, stream=stream)
+    g.set_case(tau, 1.0, U0, 0.0)
+    chunk = args.chunk
+    for _ in range(args.warmup):
+        g.step(chunk)
+    torch.cuda.synchronize()
+    clocks = Clocks(smi_index(0))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.step(chunk)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    cells = n1 * n2 * n3
+    steps = chunk * args.steps
+    sb = STORAGE_BYTES[prec]
+    bytes_per_step = 2 * 39 * sb * cells
+    achieved = bytes_per_step / (ms * 1e-3 / steps) / 1e9
+    peak, peak_src = peaks()
+    tot = g.totals()
+    out = {"metric": "D3Q39 curvilinear MLUPS and % HBM roofline", "value": cells * steps / (ms * 1e-3) / 1e6,
+           "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp32": "f32"}[prec], "data": "synthetic",
+           "config": {"workload": wl, "lattice": "D3Q39", "n1": n1, "n2": n2, "n3": n3,
+                      "geometry": "annulus R2/R1=2 extruded along z, radial CR=%g" % THREE_D_WORKLOADS[wl][6],
+                      "tau": tau, "u_wall": THREE_D_WORKLOADS[wl][8], "storage": prec, "chunk": chunk,
+                      "l2": "inputs larger than L2 (state %d MB)" % (2 * 39 * cells * sb >> 20)},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src + " (hbm_gbs)",
+                        "algorithmic_bytes_per_launch": bytes_per_step,
+                        "kernel_ms_avg": ms / steps, "timed": "whole time step: ghost-row and update launches"},
+           "gpu_launches": 2 * steps, "clocks": ck, "mass_after": tot[0]}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_3d(wl)
+    print(json.dumps(out))
+    g.close()
 
 
 def run_serving(n, verbose=False):
