@@ -244,15 +244,27 @@ __global__ void __launch_bounds__(TB) k3_boundary(Args3 A, S* __restrict__ st) {
     }
 }
 
-// One cell (i, j, k) of the update; MOM: write rho and Ut instead.
+template <typename C>
+__device__ __forceinline__ C ldt(const C* p) { return *p; }
+
+// One cell (i, j, k) of the update; MOM: write rho and Ut instead.  A block
+// covers 128 cells of one row, so the row's table is staged in shared
+// memory once per block and every coefficient is a shared-memory read.
 template <typename S, typename C, bool MOM>
-__global__ void __launch_bounds__(TB) k3_step(Args3 A, double* __restrict__ mrho, double* __restrict__ mut) {
+__global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
+    k3_step(Args3 A, double* __restrict__ mrho, double* __restrict__ mut) {
+    __shared__ __align__(16) C ts[Tab3::S];
     const int n23 = A.n2 * A.n3;
     const int jk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (jk >= n23) return;
     const int r = blockIdx.y, i = r + 1;
+    {
+        const C* tg = (const C*)A.tab + (size_t)r * Tab3::S;
+        for (int q = threadIdx.x; q < Tab3::S; q += TB) ts[q] = tg[q];
+    }
+    __syncthreads();
+    if (jk >= n23) return;
     const int j = jk / A.n3, k = jk - j * A.n3;
-    const C* t = (const C*)A.tab + (size_t)r * Tab3::S;
+    const C* t = ts;
     const S* src = (const S*)A.src;
     int jo[7], ko[7];
 #pragma unroll
@@ -265,26 +277,26 @@ __global__ void __launch_bounds__(TB) k3_step(Args3 A, double* __restrict__ mrho
     // pull (Eq. 12) with the lagged read, moments (Eqs. 7-10), lagged force (Eq. 15)
     C d[Q];
     C sd = C(0), s1 = C(0), s2 = C(0), s3 = C(0);
-    C f1 = __ldg(t + Tab3::F0), f2 = __ldg(t + Tab3::F0 + 1), f3 = __ldg(t + Tab3::F0 + 2);
+    C f1 = ldt(t + Tab3::F0), f2 = ldt(t + Tab3::F0 + 1), f3 = ldt(t + Tab3::F0 + 2);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int c1 = c1_3(a), c2 = c2_3(a), c3 = c3_3(a);
         const size_t pidx = (size_t)(i - c1 - 1 + H) * n23 + jo[c2 + 3] + ko[c3 + 3];
         const C p = C(St3<S>::ld(src + (size_t)a * A.plane + pidx));
         const C l = C(St3<S>::ld(src + (size_t)a * A.plane + own));
-        const C* ta = t + Tab3::A(a);
-        const C* tb = t + Tab3::A(opp3(a));
-        const C da = c1 != 0 ? p + __ldg(ta + 3) : p;
+        const V4<C> ta = ld4(t + Tab3::A(a));           // (a^1, a^2, a^3, Delta) of a
+        const V4<C> tb = ld4(t + Tab3::A(opp3(a)));     // ... of its reverse
+        const C da = c1 != 0 ? p + ta.w : p;
         d[a] = da;
         sd += da;
         if (c1) s1 += C(c1) * da;
         if (c2) s2 += C(c2) * da;
         if (c3) s3 += C(c3) * da;
-        f1 += __ldg(ta) * l + __ldg(tb) * da;
-        f2 += __ldg(ta + 1) * l + __ldg(tb + 1) * da;
-        f3 += __ldg(ta + 2) * l + __ldg(tb + 2) * da;
+        f1 += ta.x * l + tb.x * da;
+        f2 += ta.y * l + tb.y * da;
+        f3 += ta.z * l + tb.z * da;
     }
-    const C invJ = __ldg(t + Tab3::INVJ), J = __ldg(t + Tab3::J);
+    const C invJ = ldt(t + Tab3::INVJ), J = ldt(t + Tab3::J);
     const C drho = sd * invJ, rho = C(A.rho0) + drho, irho = C(1) / rho;
     const C U1 = s1 * invJ * irho, U2 = s2 * invJ * irho, U3 = s3 * invJ * irho;
     const C F1 = C(-0.5) * invJ * f1 + rho * C(A.g1);
@@ -306,8 +318,8 @@ __global__ void __launch_bounds__(TB) k3_step(Args3 A, double* __restrict__ mrho
     // (symmetrised), their contraction with the first Hermite term, and the
     // odd part O_a = c.U / T0 + H3(c) : C / (6 T0^3) of f^eq / (rho w)
     constexpr C iT0 = C(1.0 / T0), i2T02 = C(0.5 / (T0 * T0)), i6T03 = C(1.0 / (6.0 * T0 * T0 * T0));
-    const C g11 = __ldg(t + Tab3::G11), g12 = __ldg(t + Tab3::G12), g13 = __ldg(t + Tab3::G13);
-    const C g22 = __ldg(t + Tab3::G22), g23 = __ldg(t + Tab3::G23), g33 = __ldg(t + Tab3::G33);
+    const C g11 = ldt(t + Tab3::G11), g12 = ldt(t + Tab3::G12), g13 = ldt(t + Tab3::G13);
+    const C g22 = ldt(t + Tab3::G22), g23 = ldt(t + Tab3::G23), g33 = ldt(t + Tab3::G33);
     const C T = C(T0);
     const C C111 = V1 * V1 * V1 + T * (C(3) * g11 * V1 - C(3) * U1);
     const C C222 = V2 * V2 * V2 + T * (C(3) * g22 * V2 - C(3) * U2);
@@ -339,13 +351,13 @@ __global__ void __launch_bounds__(TB) k3_step(Args3 A, double* __restrict__ mrho
                     k112 * (x * x * y) + k113 * (x * x * z) + k122 * (x * y * y) + k133 * (x * z * z) +
                     k223 * (y * y * z) + k233 * (y * z * z) + k123 * (x * y * z);
         O[p] = o;
-        const C* e = t + Tab3::E(p);
-        P11 += __ldg(e) * o;
-        P22 += __ldg(e + 1) * o;
-        P33 += __ldg(e + 2) * o;
-        P12 += __ldg(e + 3) * o;
-        P13 += __ldg(e + 4) * o;
-        P23 += __ldg(e + 5) * o;
+        const V4<C> e0 = ld4(t + Tab3::E(p)), e1 = ld4(t + Tab3::E(p) + 4);
+        P11 += e0.x * o;
+        P22 += e0.y * o;
+        P33 += e0.z * o;
+        P12 += e0.w * o;
+        P13 += e1.x * o;
+        P23 += e1.y * o;
     }
     const C pr = C(A.pref) * rho;
     P11 *= pr;
@@ -363,14 +375,14 @@ __global__ void __launch_bounds__(TB) k3_step(Args3 A, double* __restrict__ mrho
     const C uu = V1 * V1 + V2 * V2 + V3 * V3;
     const C base = C(-0.5) * iT0 * uu * rho * tinv - trP * iT0;
     S* dst = (S*)A.dst + own;
-    St3<S>::st(dst, S(omt * d[0] + J * C(w3(0)) * (drho * __ldg(t + Tab3::P0) * tinv + base)));
+    St3<S>::st(dst, S(omt * d[0] + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base)));
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = plus3(p), b = opp3(a);
         const C x = C(c1_3(a)), y = C(c2_3(a)), z = C(c3_3(a));
         const C cu = x * V1 + y * V2 + z * V3;
         const C cPc = x * x * P11 + y * y * P22 + z * z * P33 + C(2) * (x * y * P12 + x * z * P13 + y * z * P23);
-        const C X = drho * __ldg(t + Tab3::P0 + a) * tinv + rho * tinv * (cu * cu) * i2T02 + cPc * (iT0 * iT0) +
+        const C X = drho * ldt(t + Tab3::P0 + a) * tinv + rho * tinv * (cu * cu) * i2T02 + cPc * (iT0 * iT0) +
                     base;
         const C Y = rho * tinv * O[p] + (x * F1 + y * F2 + z * F3) * iT0;
         const C Jw = J * C(w3(a));
