@@ -1138,7 +1138,7 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
     b->ws_ok = true;
     for (int k = 0; k < n; ++k) b->ws_ok = b->ws_ok && grids[k]->tma != nullptr;
     int tj0, tr0;
-    batch_tile_shape(0, b->prec, &tj0, &tr0);
+    batch_tile_shape(0, &tj0, &tr0);
     for (int k = 0; k < n; ++k) {
         clbm_grid* g = grids[k];
         for (int j = 0; j < g->n2; j += 128) {
@@ -1154,7 +1154,7 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
         for (int v = 0; v < BATCH_ALL; ++v) {
             if (v == BATCH_WS && !b->ws_ok) continue;
             int tj, tr;
-            batch_tile_shape(v, b->prec, &tj, &tr);
+            batch_tile_shape(v, &tj, &tr);
             for (int i = 0; i < g->n1; i += tr)
                 for (int j = 0; j < g->n2; j += tj) ws[v].push_back(make_int4(k, i, j, 0));
         }

@@ -33,10 +33,10 @@ void launch_batch(int Q, int prec, int what, int variant, const BatchGrid* grids
                   int nwork, int parity, int nblk, double* partial, cudaStream_t s);
 void launch_batch_reduce(const double* partial, const int2* range, int ngrids, double* out,
                          cudaStream_t s);
-// Update tile (columns x rows) of a variant at storage precision prec.
-void batch_tile_shape(int variant, int prec, int* tj, int* tr);
+// Update tile (columns x rows) of a variant.
+void batch_tile_shape(int variant, int* tj, int* tr);
 
-// Variant BATCH_WS: the pipelined TMA update over 8 x 64 (16-bit: 10 x 64) tiles of every
+// Variant BATCH_WS: the pipelined TMA update over 8 x 64 tiles of every
 // lattice (k_step_tma.cu).  maps: per lattice the 2 x 8 load maps of its two
 // state buffers (device memory, tma_load_maps layout); err: device error word
 // of bounded waits.  Returns nonzero if it could not be launched.

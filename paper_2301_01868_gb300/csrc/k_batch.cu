@@ -249,14 +249,13 @@ void run_all(int what, int v, const BatchGrid* grids, const int4* work, int nwor
 
 }  // namespace
 
-void batch_tile_shape(int variant, int prec, int* tj, int* tr) {
+void batch_tile_shape(int variant, int* tj, int* tr) {
     switch (variant) {
         case 0: *tj = Var<0>::TJ; *tr = Var<0>::TR; break;
         case 1: *tj = Var<1>::TJ; *tr = Var<1>::TR; break;
         case 2: *tj = Var<2>::TJ; *tr = Var<2>::TR; break;
         case 3: *tj = Var<3>::TJ; *tr = Var<3>::TR; break;
-        // BATCH_WS: the TMA tile of k_step_tma.cu (10 rows at 16-bit storage)
-        default: *tj = 64; *tr = prec >= 2 ? 10 : 8; break;
+        default: *tj = 64; *tr = 8; break;  // BATCH_WS: the TMA tile of k_step_tma.cu
     }
 }
 
