@@ -60,7 +60,8 @@ KERNEL_SOURCES = ["paper_2301_01868_gb300/csrc/k_step.cu",
                   "paper_2301_01868_gb300/csrc/k_step_tma.cu",
                   "paper_2301_01868_gb300/csrc/clbm_cell.cuh",
                   "paper_2301_01868_gb300/csrc/clbm_internal.cuh",
-                  "paper_2301_01868_gb300/csrc/clbm_lattice.cuh"]
+                  "paper_2301_01868_gb300/csrc/clbm_lattice.cuh",
+                  "paper_2301_01868_gb300/csrc/clbm_sync.cuh"]
 
 
 def kernel_hash():

@@ -98,6 +98,7 @@ def lib():
             "clbm_batch_launch_count": [h, C.POINTER(ll)],
             "clbm_batch_destroy": [h],
             "clbm_destroy": [h],
+            "clbm_selftest_bounded_wait": [C.c_int, C.c_int, dp],
             "clbm3_create_grid": [C.POINTER(_Desc3), C.POINTER(C.c_void_p)],
             "clbm3_set_case": [h, C.POINTER(_Case3)],
             "clbm3_set_state": [h, vp, vp, vp, vp, C.c_int],
@@ -517,3 +518,10 @@ class Grid3:
         v = C.c_longlong()
         _check(lib().clbm3_time(self._h, C.byref(v)))
         return v.value
+
+
+def selftest_bounded_wait(polls=4096, device=0):
+    """(status, ms) of the bounded-wait self-test: status must be ETIMEOUT (4)."""
+    ms = C.c_double()
+    st = lib().clbm_selftest_bounded_wait(int(device), int(polls), C.byref(ms))
+    return st, ms.value
