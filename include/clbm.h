@@ -277,10 +277,10 @@ clbm_status clbm_destroy(clbm_handle h);
 /* Self-test of failure detection.  One CTA waits, with at most `polls` polls
  * (1..2^22), on an mbarrier that nothing completes, through the same bounded
  * wait that every spin of the pipelined kernels uses (the update's waits
- * take 2^22 polls).  The wait must give up and the kernel return:
- * CLBM_ETIMEOUT is the expected result, *ms the kernel's duration, and the
- * context stays usable; CLBM_OK would mean the barrier completed.  The
- * paper has no counterpart. */
+ * take 2^18 polls, about one second).  The wait must give up and the kernel
+ * return: CLBM_ETIMEOUT is the expected result, *ms the kernel's duration,
+ * and the context stays usable; CLBM_OK would mean the barrier completed.
+ * The paper has no counterpart. */
 clbm_status clbm_selftest_bounded_wait(int device, int polls, double* ms);
 
 /* Thread-local message of the last failing call ("" if none). */
