@@ -57,18 +57,20 @@ struct Geo3 {
     static constexpr int J = 0, GI = 1, GC = 7, A = 13, REF = 13 + 3 * Q, S = 13 + 4 * Q;
 };
 
-// Per-row table of the update in the compute type: header, then per
-// direction (a^1, a^2, a^3, Delta) with Delta_alpha = ref_alpha(i - c1) -
-// ref_alpha(i), the rest polynomial P0 per direction, and per pair the
-// symmetric dPi weights w (c^p D^r + c^r D^p), D = a_alpha + a_opp(alpha),
-// in the order 11, 22, 33, 12, 13, 23.
+// Per-row table of the update in the compute type: header, then per pair
+// (a = plus3(p), b = opp3(a)) the contractions and pull offsets in the lane
+// order of the paired arithmetic, (a^1_b, a^1_a, a^2_b, a^2_a, a^3_b, a^3_a,
+// Delta_a, Delta_b) with Delta_alpha = ref_alpha(i - c1) - ref_alpha(i), the
+// rest polynomial P0 per direction, and per pair the symmetric dPi weights
+// w (c^p D^r + c^r D^p), D = a_alpha + a_opp(alpha), in the order 11, 22, 33,
+// 12, 13, 23.  (The rest direction has a = 0 and Delta = 0.)
 struct Tab3 {
     static constexpr int INVJ = 0, J = 1, G11 = 2, G12 = 3, G13 = 4, G22 = 5, G23 = 6, G33 = 7;
     static constexpr int F0 = 8;                         // 3 values
     static constexpr int C11 = 11, C12 = 12, C13 = 13, C22 = 14, C23 = 15, C33 = 16;
     static constexpr int HDR = 20;
-    __host__ __device__ static constexpr int A(int a) { return HDR + 4 * a; }
-    static constexpr int P0 = HDR + 4 * Q;               // 39 values
+    __host__ __device__ static constexpr int PA(int p) { return HDR + 8 * p; }
+    static constexpr int P0 = HDR + 8 * NP;              // 39 values
     __host__ __device__ static constexpr int E(int p) { return P0 + 40 + 8 * p; }
     static constexpr int S = P0 + 40 + 8 * NP;           // stride, a multiple of 4
 };

@@ -21,6 +21,7 @@
 
 #include "clbm3.cuh"
 #include "clbm3.h"
+#include "clbm_cell.cuh"
 
 namespace clbm {
 namespace d3 {
@@ -166,12 +167,17 @@ __global__ void k3_tables(const double* __restrict__ geo, C* __restrict__ tab, i
     for (int a = 0; a < Q; ++a) {
         const int b = opp3(a);
         const double ref = g[Geo3::REF + a];
-        for (int k = 0; k < 3; ++k) {
-            t[Tab3::A(a) + k] = C(g[Geo3::A + 3 * a + k]);
-            F0[k] += (g[Geo3::A + 3 * a + k] + g[Geo3::A + 3 * b + k]) * ref;
-        }
-        t[Tab3::A(a) + 3] = C(ref_row(geo, n1, a, i - c1_3(a)) - ref);
+        for (int k = 0; k < 3; ++k) F0[k] += (g[Geo3::A + 3 * a + k] + g[Geo3::A + 3 * b + k]) * ref;
         t[Tab3::P0 + a] = C(rest_poly3(a, g + Geo3::GI));
+    }
+    for (int p = 0; p < NP; ++p) {
+        const int a = plus3(p), b = opp3(a);
+        for (int k = 0; k < 3; ++k) {
+            t[Tab3::PA(p) + 2 * k] = C(g[Geo3::A + 3 * b + k]);
+            t[Tab3::PA(p) + 2 * k + 1] = C(g[Geo3::A + 3 * a + k]);
+        }
+        t[Tab3::PA(p) + 6] = C(ref_row(geo, n1, a, i - c1_3(a)) - g[Geo3::REF + a]);
+        t[Tab3::PA(p) + 7] = C(ref_row(geo, n1, b, i - c1_3(b)) - g[Geo3::REF + b]);
     }
     for (int k = 0; k < 3; ++k) t[Tab3::F0 + k] = C(F0[k]);
     const int P[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
@@ -274,34 +280,41 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     }
     const size_t own = (size_t)(i - 1 + H) * n23 + jk;
 
-    // pull (Eq. 12) with the lagged read, moments (Eqs. 7-10), lagged force (Eq. 15)
-    C d[Q];
-    C sd = C(0), s1 = C(0), s2 = C(0), s3 = C(0);
-    C f1 = ldt(t + Tab3::F0), f2 = ldt(t + Tab3::F0 + 1), f3 = ldt(t + Tab3::F0 + 2);
+    // pull (Eq. 12) with the lagged read, moments (Eqs. 7-10), lagged force
+    // (Eq. 15), two directions a, b = -a at a time in the two lanes of a pair
+    using P = typename PairOf<C>::T;
+    P dd[NP];
+    const C d0 = C(St3<S>::ld(src + own));
+    P sd = mkp(d0, C(0)), s1 = mkp(C(0), C(0)), s2 = s1, s3 = s1;
+    P f1 = mkp(ldt(t + Tab3::F0), C(0)), f2 = mkp(ldt(t + Tab3::F0 + 1), C(0)), f3 = mkp(ldt(t + Tab3::F0 + 2), C(0));
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
+    for (int p = 0; p < NP; ++p) {
+        const int a = plus3(p), b = opp3(a);
         const int c1 = c1_3(a), c2 = c2_3(a), c3 = c3_3(a);
-        const size_t pidx = (size_t)(i - c1 - 1 + H) * n23 + jo[c2 + 3] + ko[c3 + 3];
-        const C p = C(St3<S>::ld(src + (size_t)a * A.plane + pidx));
-        const C l = C(St3<S>::ld(src + (size_t)a * A.plane + own));
-        const V4<C> ta = ld4(t + Tab3::A(a));           // (a^1, a^2, a^3, Delta) of a
-        const V4<C> tb = ld4(t + Tab3::A(opp3(a)));     // ... of its reverse
-        const C da = c1 != 0 ? p + ta.w : p;
-        d[a] = da;
-        sd += da;
-        if (c1) s1 += C(c1) * da;
-        if (c2) s2 += C(c2) * da;
-        if (c3) s3 += C(c3) * da;
-        f1 += ta.x * l + tb.x * da;
-        f2 += ta.y * l + tb.y * da;
-        f3 += ta.z * l + tb.z * da;
+        // N_a from q - c_a, N_b from q + c_a; the lagged values are the cell's own
+        const size_t ia = (size_t)(i - c1 - 1 + H) * n23 + jo[c2 + 3] + ko[c3 + 3];
+        const size_t ib = (size_t)(i + c1 - 1 + H) * n23 + jo[3 - c2] + ko[3 - c3];
+        const P pp = mkp(C(St3<S>::ld(src + (size_t)a * A.plane + ia)), C(St3<S>::ld(src + (size_t)b * A.plane + ib)));
+        const P lg = mkp(C(St3<S>::ld(src + (size_t)b * A.plane + own)), C(St3<S>::ld(src + (size_t)a * A.plane + own)));
+        const V4<C> w0 = ld4(t + Tab3::PA(p)), w1 = ld4(t + Tab3::PA(p) + 4);
+        const P d = c1 != 0 ? padd(pp, mkp(w1.z, w1.w)) : pp;
+        dd[p] = d;
+        sd = padd(sd, d);
+        if (c1) s1 = pfma(mkp(C(c1), C(-c1)), d, s1);
+        if (c2) s2 = pfma(mkp(C(c2), C(-c2)), d, s2);
+        if (c3) s3 = pfma(mkp(C(c3), C(-c3)), d, s3);
+        // (N'_b + N_a, N'_a + N_b), weighed by (a^k_b, a^k_a)
+        const P tt = padd(lg, d);
+        f1 = pfma(mkp(w0.x, w0.y), tt, f1);
+        f2 = pfma(mkp(w0.z, w0.w), tt, f2);
+        f3 = pfma(mkp(w1.x, w1.y), tt, f3);
     }
     const C invJ = ldt(t + Tab3::INVJ), J = ldt(t + Tab3::J);
-    const C drho = sd * invJ, rho = C(A.rho0) + drho, irho = C(1) / rho;
-    const C U1 = s1 * invJ * irho, U2 = s2 * invJ * irho, U3 = s3 * invJ * irho;
-    const C F1 = C(-0.5) * invJ * f1 + rho * C(A.g1);
-    const C F2 = C(-0.5) * invJ * f2 + rho * C(A.g2);
-    const C F3 = C(-0.5) * invJ * f3 + rho * C(A.g3);
+    const C drho = (sd.x + sd.y) * invJ, rho = C(A.rho0) + drho, irho = C(1) / rho;
+    const C U1 = (s1.x + s1.y) * invJ * irho, U2 = (s2.x + s2.y) * invJ * irho, U3 = (s3.x + s3.y) * invJ * irho;
+    const C F1 = C(-0.5) * invJ * (f1.x + f1.y) + rho * C(A.g1);
+    const C F2 = C(-0.5) * invJ * (f2.x + f2.y) + rho * C(A.g2);
+    const C F3 = C(-0.5) * invJ * (f3.x + f3.y) + rho * C(A.g3);
     const C V1 = U1 + C(0.5) * F1 * irho, V2 = U2 + C(0.5) * F2 * irho, V3 = U3 + C(0.5) * F3 * irho;
     if (MOM) {
         const size_t m = (size_t)r * n23 + jk, nc = (size_t)A.n1 * n23;
@@ -375,7 +388,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     const C uu = V1 * V1 + V2 * V2 + V3 * V3;
     const C base = C(-0.5) * iT0 * uu * rho * tinv - trP * iT0;
     S* dst = (S*)A.dst + own;
-    St3<S>::st(dst, S(omt * d[0] + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base)));
+    St3<S>::st(dst, S(omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base)));
+    const P omt2 = mkp(omt, omt), J2 = mkp(J, J);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = plus3(p), b = opp3(a);
@@ -385,9 +399,11 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         const C X = drho * ldt(t + Tab3::P0 + a) * tinv + rho * tinv * (cu * cu) * i2T02 + cPc * (iT0 * iT0) +
                     base;
         const C Y = rho * tinv * O[p] + (x * F1 + y * F2 + z * F3) * iT0;
-        const C Jw = J * C(w3(a));
-        St3<S>::st(dst + (size_t)a * A.plane, S(omt * d[a] + Jw * (X + Y)));
-        St3<S>::st(dst + (size_t)b * A.plane, S(omt * d[b] + Jw * (X - Y)));
+        const C w = C(w3(a));
+        // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
+        const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
+        St3<S>::st(dst + (size_t)a * A.plane, S(o.x));
+        St3<S>::st(dst + (size_t)b * A.plane, S(o.y));
     }
     // the moments the walls read next (rows within H of a wall)
     if (i <= H) {
