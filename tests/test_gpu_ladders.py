@@ -4,7 +4,8 @@ profiles of the paper's flows (Sec. 3):
 * planar Poiseuille (Eqs. 24-25) on the geometrically stretched channel of
   the planar configuration, D2Q21, tau = 1, stretch 1.02^(64 / n1) per cell
   and g = 1e-6 (64 / n1)^2 (the same total stretch and peak speed on every
-  rung), n1 x n2 = 64 x 16, 128 x 32, 256 x 64: FP64 to a residual of 1e-10,
+  rung), n1 x n2 = 64 x 16, 128 x 32, 256 x 64 (and 512 x 128 in FP64): FP64
+  to a residual of 1e-10,
   FP32 for a fixed 20 decay times of the slowest mode (a residual threshold
   near FP32's floor would stop it early, with a start-up remnant that grows
   as n1^2);
@@ -55,6 +56,7 @@ def l2rel(a, b):
 
 
 RUNGS = ((64, 16), (128, 32), (256, 64))
+RUNGS_FP64 = RUNGS + ((512, 128),)
 
 
 def poiseuille(c, n1, n2, tau, prec):
@@ -75,16 +77,16 @@ def test_planar_poiseuille_ladder_fp64_converges_at_second_order():
     tau, T0 = 1.0, 2.0 / 3.0
     nu = E.nu_of_tau(tau, T0)
     errs = []
-    for n1, n2 in RUNGS:
+    for n1, n2 in RUNGS_FP64:
         g, e, gacc = poiseuille(c, n1, n2, tau, "fp64")
-        steps, res = run_to_steady(g, 1e-10, 1000, 600000)
+        steps, res = run_to_steady(g, 1e-10, 2000, 2000000)
         err = l2rel(g.moments(names=("Ut2",))["Ut2"][:, 0], poiseuille_exact(e, n1, gacc, nu))
         errs.append(err)
         print("\nLADDER planar Poiseuille D2Q21 fp64 %dx%d stretch %.4f: %d steps, residual %.1e, "
               "L2 error vs exact %.3e" % (n1, n2, 1.02 ** (64.0 / n1), steps, res, err))
         g.close()
         assert res <= 1e-10
-    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0
+    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0 and errs[3] < errs[2] / 3.0
 
 
 def test_planar_poiseuille_fp32_reaches_its_rounding_floor():
@@ -146,3 +148,34 @@ def test_circular_couette_ladder_d2q21_converges_and_beats_d2q9():
             g.close()
     assert errs[(21, 64)] < errs[(21, 32)] / 1.6 and errs[(21, 128)] < errs[(21, 64)] / 1.6
     assert errs[(21, 32)] < errs[(9, 32)] / 2.0
+
+
+def test_precision_ladder_on_the_contracted_annulus_at_128():
+    """Circular Couette on the bench's radial grid (App. C contraction
+    CR = 0.35) at N_r = 128, N_theta = 804, tau = 0.8, 14 diffusion times from
+    rest: every storage precision against FP64 and against Eq. 27."""
+    c = _clbm()
+    R1, R2, uw, tau, Nr = 1.0, 2.0, 0.01, 0.8, 128
+    Nt = I.n_theta(Nr, R1, R2)
+    e = I.polar_edges(R1, R2, Nr, 0.35)
+    dx = (R2 - R1) / Nr
+    M = R1 / dx
+    nu = (tau - 0.5) * 2.0 / 3.0
+    steps = int(math.ceil(14 * Nr * Nr / (math.pi ** 2 * nu) / 1000.0)) * 1000
+    r_lat = 0.5 * (e[:-1] + e[1:]) / dx
+    ex = E.Annulus.couette(M, M + Nr, uw / M).u(r_lat)
+    u = {}
+    for prec in ("fp64", "fp32", "fp16", "bf16"):
+        g = c.Grid(21, Nr, Nt, e, kind=c.POLAR, precision=prec, bc_lo=c.MOVING, bc_hi=c.NOSLIP)
+        g.set_case(tau, 1.0, c.wall_speed_polar(uw, R1, Nt, dx), 0.0)
+        g.step(steps)
+        u[prec] = g.moments(names=("Ut2",))["Ut2"][:, 0] * math.sin(2.0 * math.pi / Nt) * r_lat
+        g.close()
+    for prec in u:
+        print("\nLADDER precision D2Q21 %s 128x804 CR 0.35 (%d steps): vs FP64 %.2e, vs exact %.3e"
+              % (prec, steps, l2rel(u[prec], u["fp64"]), l2rel(u[prec], ex)))
+    assert l2rel(u["fp64"], ex) < 0.02
+    assert l2rel(u["fp32"], u["fp64"]) < 1e-4
+    assert l2rel(u["fp16"], u["fp64"]) < 2e-2
+    assert l2rel(u["bf16"], u["fp64"]) < 1e-1
+
