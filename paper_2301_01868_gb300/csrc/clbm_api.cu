@@ -478,6 +478,10 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
         dN = sb;
         dr = du = nullptr;
         double* extra = nullptr;
+        struct FreeOnExit {
+            double** p;
+            ~FreeOnExit() { cudaFree(*p); }
+        } guard{&extra};
         if (rho_prev || ut2_prev) {
             CK(cudaMalloc((void**)&extra, 2 * nc * 8));
             if (rho_prev) {
@@ -496,7 +500,6 @@ clbm_status clbm_set_state(clbm_handle g, const double* Np, const double* rho_pr
         g->launches += 2;
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(g->stream));
-        cudaFree(extra);
     } else {
         launch_state_from_fp64(g->Q, g->prec, dN, g->geo, g->stA, g->n1, g->n2, g->ld, g->h, g->ncol,
                                g->stream);

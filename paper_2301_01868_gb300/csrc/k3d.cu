@@ -704,6 +704,10 @@ clbm_status clbm3_set_state(clbm3_handle g, const double* Np, const double* rho,
     const size_t nc = ncells(g);
     const double *dN = Np, *dr = rho, *d2 = u2, *d3 = u3;
     double* extra = nullptr;
+    struct FreeOnExit {
+        double** p;
+        ~FreeOnExit() { cudaFree(*p); }
+    } guard{&extra};
     if (!src_is_device) {
         double* sb = nullptr;
         clbm_status st = staging(g, &sb);
@@ -733,7 +737,6 @@ clbm_status clbm3_set_state(clbm3_handle g, const double* Np, const double* rho,
     }
     CK3(cudaGetLastError());
     CK3(cudaStreamSynchronize(g->stream));
-    if (extra) cudaFree(extra);
     return CLBM_OK;
 }
 
