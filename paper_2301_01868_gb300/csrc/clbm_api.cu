@@ -186,6 +186,11 @@ bool use_tma(const clbm_grid* g) {
     return g->variant != 1;
 }
 
+// General grids run the pipelined form with per-cell tables (kernel 3, the
+// automatic choice) or the per-cell kernel; the TMA tiles of kernel 2 and the
+// pipelined residual read row tables and are for planar / polar grids.
+bool general_grid(const clbm_grid* g) { return g->ncol > 1; }
+
 // Device-side failures recorded by bounded waits since the last check.
 clbm_status check_err(clbm_grid* g) {
     int e = 0;
@@ -413,7 +418,7 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
         clbm_destroy(g);
         return fail(CLBM_ECUDA, "geometry precompute: %s", cudaGetErrorString(ce));
     }
-    if (g->prec != CLBM_FP64 && !general) {
+    if (g->prec != CLBM_FP64) {
         int major = 0;
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, d->device);
         if (major >= 9 && make_tma_maps(g->Q, g->prec, &g->tma, g->phys[0], g->phys[1], g->n1, g->n2,
@@ -599,8 +604,11 @@ clbm_status clbm_step(clbm_handle g, long long n) {
         }
         if (use_tma(g)) {
             const int src = g->stA == g->phys[0] ? 0 : 1;
-            if (launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->variant != 2, g->stream) != 0)
-                return fail(CLBM_ECUDA, "TMA-staged update could not be launched");
+            const int rc = general_grid(g)
+                               ? launch_step_tma_general(g->Q, g->prec, *g->tma, a, src, g->nsm, g->stream)
+                               : launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->variant != 2,
+                                                 g->stream);
+            if (rc != 0) return fail(CLBM_ECUDA, "TMA-staged update could not be launched");
         } else {
             launch_step(g->Q, g->prec, a, g->stream);
         }
@@ -669,8 +677,8 @@ clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
     // the pipelined pass where the update runs pipelined, else one thread
     // per cell loading from global memory
     int nb = -1;
-    if (use_tma(g)) nb = launch_residual_tma(g->Q, g->prec, *g->tma, m, g->stA == g->phys[0] ? 0 : 1,
-                                             g->nsm, g->stream);
+    if (use_tma(g) && !general_grid(g))
+        nb = launch_residual_tma(g->Q, g->prec, *g->tma, m, g->stA == g->phys[0] ? 0 : 1, g->nsm, g->stream);
     if (nb < 0) {
         launch_moments(g->Q, g->prec, m, g->cs.force_iterations, 1, g->stream);
         nb = moments_blocks(g->n1, g->n2);
@@ -819,6 +827,8 @@ clbm_status clbm_set_kernel(clbm_handle g, int variant) {
     if (variant < 0 || variant > 3) return fail(CLBM_EINVAL, "variant must be 0, 1, 2 or 3");
     if (variant >= 2 && !g->tma)
         return fail(CLBM_EINVAL, "the TMA-staged update needs 16/32-bit storage on sm_90 or newer");
+    if (variant == 2 && general_grid(g))
+        return fail(CLBM_EINVAL, "general grids run kernel 1 or 3 (kernel 2 reads row tables)");
     g->variant = variant;
     return CLBM_OK;
 }

@@ -169,6 +169,10 @@ size_t tma_load_maps(const TmaMaps* m, void* out);
 // -1 when it cannot run (FP64 storage, launch failure).
 int launch_residual_tma(int Q, int prec, const TmaMaps& maps, const MomArgs& m, int src, int nsm,
                         cudaStream_t s);
+// The pipelined update of a general grid (per-cell tables read by the
+// consumers, state staged by TMA); the maps as for launch_step_tma.
+int launch_step_tma_general(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
+                            cudaStream_t s);
 int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
                     int pipelined, cudaStream_t s);
 

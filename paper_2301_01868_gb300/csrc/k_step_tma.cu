@@ -292,15 +292,11 @@ struct WsLattice {
 // memory: pull, collide, store straight to global memory (plus, next to a
 // periodic end or a wall, the copies and ghost values it supplies), wall
 // moments.
-template <int Q, typename S, typename C>
-__device__ __forceinline__ void ws_update_cell(const WsLattice<S>& L, const Consts<C>& k, const S* in,
-                                               const C* tab_rows, int i0, int j0, int r, int cc) {
+template <int Q, typename S, typename C, typename TB>
+__device__ __forceinline__ void ws_update_cell_tb(const WsLattice<S>& L, const Consts<C>& k, const S* in,
+                                                  const TB& tb, int i, int j, int r, int cc, int gcols) {
     using G = TileGeom<Q, S>;
-    using T = Tab<Q>;
     constexpr int H = Lat<Q>::H;
-    const int i = i0 + r, j = j0 + cc;
-    if (i >= L.n1 || j >= L.n2) return;
-    const RowTab<Q, C> tb{tab_rows + r * T::S};
     Cell<Q, C> c;
     pull_cell<Q, C>(
         [&](int al, int dr, int dc) -> C {
@@ -316,7 +312,7 @@ __device__ __forceinline__ void ws_update_cell(const WsLattice<S>& L, const Cons
     });
     if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
         const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
-                                C(L.U0_lo), C(L.U0_hi), L.n2 < 2 * GC, 1};
+                                C(L.U0_lo), C(L.U0_hi), L.n2 < 2 * GC, gcols};
         ef.fill(i, j, dst, L.plane, c.rho, c.Ut2);
     }
     if (i < H) {
@@ -331,6 +327,25 @@ __device__ __forceinline__ void ws_update_cell(const WsLattice<S>& L, const Cons
     }
 }
 
+// Planar and polar grids: the row's table block staged with the tile.
+template <int Q, typename S, typename C>
+__device__ __forceinline__ void ws_update_cell(const WsLattice<S>& L, const Consts<C>& k, const S* in,
+                                               const C* tab_rows, int i0, int j0, int r, int cc) {
+    const int i = i0 + r, j = j0 + cc;
+    if (i >= L.n1 || j >= L.n2) return;
+    ws_update_cell_tb<Q, S, C>(L, k, in, RowTab<Q, C>{tab_rows + r * Tab<Q>::S}, i, j, r, cc, 1);
+}
+
+// General grids: the cell's own table planes, read from global memory (one
+// coalesced plane read per entry per warp), the state from the staged tile.
+template <int Q, typename S, typename C>
+__device__ __forceinline__ void ws_update_cell_gen(const WsLattice<S>& L, const Consts<C>& k, const S* in,
+                                                   const C* tab, int i0, int j0, int r, int cc) {
+    const int i = i0 + r, j = j0 + cc;
+    if (i >= L.n1 || j >= L.n2) return;
+    ws_update_cell_tb<Q, S, C>(L, k, in, TabOf<Q, C, true>::at(tab, i, j, L.n1, L.n2), i, j, r, cc, L.n2);
+}
+
 // Issue the TMA boxes of tile (i0, j0) from the 8 load maps of the source
 // buffer, plus the tile's table rows, on barrier bar.
 template <int Q, typename S, typename C>
@@ -339,7 +354,7 @@ __device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0,
     using G = TileGeom<Q, S>;
     constexpr int H = Lat<Q>::H;
     const int nrows = n1 - i0 < G::TR ? n1 - i0 : G::TR;
-    uint32_t bytes = (uint32_t)nrows * Tab<Q>::S * 4;
+    uint32_t bytes = tab ? (uint32_t)nrows * Tab<Q>::S * 4 : 0u;   // no rows: per-cell tables
 #pragma unroll
     for (int al = 0; al < Q; ++al) bytes += G::rows(al) * G::width(al) * (int)sizeof(S);
     mbar_expect(bar, bytes);
@@ -347,7 +362,7 @@ __device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0,
 #pragma unroll
     for (int al = 0; al < Q; ++al)
         tma_load3(in + G::off(al), &ld8[G::shape(al)], j0 + GC - G::col0(al), i0 + H - G::row0(al), al, bar);
-    bulk_load(sm_tab, tab + (size_t)i0 * Tab<Q>::S, (uint32_t)nrows * Tab<Q>::S * 4, bar);
+    if (tab) bulk_load(sm_tab, tab + (size_t)i0 * Tab<Q>::S, (uint32_t)nrows * Tab<Q>::S * 4, bar);
 }
 
 // The pipelined loop shared by the single-lattice and the batched updates
@@ -479,6 +494,33 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
         if (t > 0) w.next();
         return WsTile<Q, S, C>{maps.ld[src], (const C*)a.tab, lat, k, w.band * G::TR, w.col * G::TJ};
     }, WsUpdate<Q, S, C>{});
+}
+
+// General grids: the same pipeline, no table rows staged (the producer's
+// table pointer is null); each consumer reads its cell's table planes.
+template <int Q, typename S, typename C>
+struct WsUpdateGen {
+    const C* tab;
+    __device__ __forceinline__ void operator()(const WsTile<Q, S, C>& t, const S* in, const C*, int r,
+                                               int cc) const {
+        ws_update_cell_gen<Q, S, C>(t.lat, t.k, in, tab, t.i0, t.j0, r, cc);
+    }
+};
+
+template <int Q, typename S, typename C>
+__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+    k_fused_ws_gen(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
+    using G = TileGeom<Q, S>;
+    const int cols = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * cols;
+    const WsLattice<S> lat{(S*)a.dst, a.ghost, a.wall_rho, a.wall_ut2, a.plane, a.ld, a.n1, a.n2,
+                           a.bc_lo, a.bc_hi, a.U0_lo, a.U0_hi};
+    const Consts<C> k = Consts<C>::make(a.k);
+    RowWalk w(cols);
+    ws_pipeline<Q, S, C>(ntiles, a.err, [&](int, int t) {
+        if (t > 0) w.next();
+        return WsTile<Q, S, C>{maps.ld[src], nullptr, lat, k, w.band * G::TR, w.col * G::TJ};
+    }, WsUpdateGen<Q, S, C>{(const C*)a.tab});
 }
 
 // The pipelined update of a batch: work item e = (lattice, i0, j0) over all
@@ -688,6 +730,44 @@ static int run_tma(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cud
     const int grid = tiles < nsm ? tiles : nsm;
     k_fused_tma<Q, S, C><<<grid, G::NT, G::SMEM, s>>>(maps, a, src);
     return 0;
+}
+
+template <int Q, typename S>
+static int run_ws_gen(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cudaStream_t s) {
+    using G = TileGeom<Q, S>;
+    using P = PipeGeom<Q, S>;
+    using C = typename Store<S>::C;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_fused_ws_gen<Q, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 P::SMEM) != cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    const int tiles = ((a.n1 + G::TR - 1) / G::TR) * ((a.n2 + G::TJ - 1) / G::TJ);
+    const int grid = tiles < nsm ? tiles : nsm;
+    k_fused_ws_gen<Q, S, C><<<grid, P::NTHREADS, P::SMEM, s>>>(maps, a, src);
+    return 0;
+}
+
+int launch_step_tma_general(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
+                            cudaStream_t s) {
+    if (Q == 9) {
+        switch (prec) {
+            case 1: return run_ws_gen<9, float>(maps, a, src, nsm, s);
+            case 2: return run_ws_gen<9, __half>(maps, a, src, nsm, s);
+            case 3: return run_ws_gen<9, __nv_bfloat16>(maps, a, src, nsm, s);
+            default: return -1;
+        }
+    }
+    switch (prec) {
+        case 1: return run_ws_gen<21, float>(maps, a, src, nsm, s);
+        case 2: return run_ws_gen<21, __half>(maps, a, src, nsm, s);
+        case 3: return run_ws_gen<21, __nv_bfloat16>(maps, a, src, nsm, s);
+        default: return -1;
+    }
 }
 
 int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
