@@ -192,12 +192,14 @@ clbm_status clbm_set_stream(clbm_handle h, void* stream);
 clbm_status clbm_set_profiling(clbm_handle h, int period);
 clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
 
-/* Kernel of the bulk update: 0 automatic (variant 3 where available, else 1),
- * 1 one thread per cell with direct loads, 2 TMA-staged tiles with a shared
- * output tile, 3 TMA-staged tiles in a warp-specialised pipeline (2 and 3:
- * FP32 / FP16 / BF16 storage and rows of at least 16 bytes; the
- * implicit-force passes always use variant 1).  All run the same arithmetic.
- * CLBM_EINVAL for a variant the grid cannot use. */
+/* Kernel of the bulk update: 0 automatic (variant 3 where available, else 1;
+ * general grids: 1), 1 one thread per cell with direct loads, 2 TMA-staged
+ * tiles with a shared output tile (planar and polar grids), 3 TMA-staged
+ * tiles in a warp-specialised pipeline (general grids: the state staged, the
+ * per-cell tables read by the consumers) (2 and 3: FP32 / FP16 / BF16
+ * storage and rows of at least 16 bytes; the implicit-force passes always
+ * use variant 1).  All run the same arithmetic.  CLBM_EINVAL for a variant
+ * the grid cannot use. */
 clbm_status clbm_set_kernel(clbm_handle h, int variant);
 
 /* Number of kernel launches this grid has issued since creation. */

@@ -181,15 +181,20 @@ StepArgs step_args(const clbm_grid* g, const void* src, void* dst) {
     return a;
 }
 
+// General grids run the per-cell kernel (the automatic choice) or, asked
+// for, the pipelined form with per-cell tables (kernel 3): with the 73 table
+// planes read from global memory by 16 consumer warps per SM, and spilling
+// at the pipeline's 96 registers, that form measured 0.474 ms against the
+// per-cell kernel's 0.419 ms on the 1024 x 4096 wavy channel.  The TMA tiles
+// of kernel 2 and the pipelined residual read row tables: planar and polar
+// grids only.
+bool general_grid(const clbm_grid* g) { return g->ncol > 1; }
+
 bool use_tma(const clbm_grid* g) {
     if (!g->tma || g->cs.force_iterations > 0) return false;
+    if (general_grid(g)) return g->variant == 3;
     return g->variant != 1;
 }
-
-// General grids run the pipelined form with per-cell tables (kernel 3, the
-// automatic choice) or the per-cell kernel; the TMA tiles of kernel 2 and the
-// pipelined residual read row tables and are for planar / polar grids.
-bool general_grid(const clbm_grid* g) { return g->ncol > 1; }
 
 // Device-side failures recorded by bounded waits since the last check.
 clbm_status check_err(clbm_grid* g) {
