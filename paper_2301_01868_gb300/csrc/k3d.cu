@@ -278,7 +278,10 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         jo[q] = wrapm(j - (q - 3), A.n2) * A.n3;
         ko[q] = wrapm(k - (q - 3), A.n3);
     }
-    const size_t own = (size_t)(i - 1 + H) * n23 + jk;
+    // 32-bit element offsets (the grid's 39 planes hold fewer than 2^31
+    // values, which clbm3_create_grid checks)
+    const unsigned pl = (unsigned)A.plane;
+    const unsigned own = (unsigned)(i - 1 + H) * (unsigned)n23 + (unsigned)jk;
 
     // pull (Eq. 12) with the lagged read, moments (Eqs. 7-10), lagged force
     // (Eq. 15), two directions a, b = -a at a time in the two lanes of a pair
@@ -292,10 +295,10 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         const int a = plus3(p), b = opp3(a);
         const int c1 = c1_3(a), c2 = c2_3(a), c3 = c3_3(a);
         // N_a from q - c_a, N_b from q + c_a; the lagged values are the cell's own
-        const size_t ia = (size_t)(i - c1 - 1 + H) * n23 + jo[c2 + 3] + ko[c3 + 3];
-        const size_t ib = (size_t)(i + c1 - 1 + H) * n23 + jo[3 - c2] + ko[3 - c3];
-        const P pp = mkp(C(St3<S>::ld(src + (size_t)a * A.plane + ia)), C(St3<S>::ld(src + (size_t)b * A.plane + ib)));
-        const P lg = mkp(C(St3<S>::ld(src + (size_t)b * A.plane + own)), C(St3<S>::ld(src + (size_t)a * A.plane + own)));
+        const unsigned ia = (unsigned)(i - c1 - 1 + H) * (unsigned)n23 + (unsigned)(jo[c2 + 3] + ko[c3 + 3]);
+        const unsigned ib = (unsigned)(i + c1 - 1 + H) * (unsigned)n23 + (unsigned)(jo[3 - c2] + ko[3 - c3]);
+        const P pp = mkp(C(St3<S>::ld(src + (a * pl + ia))), C(St3<S>::ld(src + (b * pl + ib))));
+        const P lg = mkp(C(St3<S>::ld(src + (b * pl + own))), C(St3<S>::ld(src + (a * pl + own))));
         const V4<C> w0 = ld4(t + Tab3::PA(p)), w1 = ld4(t + Tab3::PA(p) + 4);
         const P d = c1 != 0 ? padd(pp, mkp(w1.z, w1.w)) : pp;
         dd[p] = d;
@@ -402,8 +405,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         const C w = C(w3(a));
         // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
         const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
-        St3<S>::st(dst + (size_t)a * A.plane, S(o.x));
-        St3<S>::st(dst + (size_t)b * A.plane, S(o.y));
+        St3<S>::st(dst + a * pl, S(o.x));
+        St3<S>::st(dst + b * pl, S(o.y));
     }
     // the moments the walls read next (rows within H of a wall)
     if (i <= H) {
@@ -612,8 +615,8 @@ clbm_status clbm3_create_grid(const clbm3_grid_desc* d, clbm3_handle* out) {
     if (d->precision != CLBM_FP64 && d->precision != CLBM_FP32)
         return fail3(CLBM_EINVAL, "precision must be CLBM_FP64 or CLBM_FP32");
     if (d->n1 < 4 || d->n2 < 1 || d->n3 < 1) return fail3(CLBM_EINVAL, "need n1 >= 4 and n2, n3 >= 1");
-    if ((long long)(d->n1 + 2 * H) * d->n2 * d->n3 > (1LL << 31) / 2)
-        return fail3(CLBM_EINVAL, "grid too large");
+    if ((long long)Q * (d->n1 + 2 * H) * d->n2 * d->n3 >= (1LL << 31))
+        return fail3(CLBM_EINVAL, "grid too large: 39 (n1 + 6) n2 n3 must stay below 2^31");
     if (d->kind != CLBM3_CHANNEL && d->kind != CLBM3_ANNULUS) return fail3(CLBM_EINVAL, "bad kind");
     if (!d->edges) return fail3(CLBM_EINVAL, "edges is NULL");
     for (int i = 0; i < d->n1; ++i)
