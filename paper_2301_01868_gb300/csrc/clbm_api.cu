@@ -109,6 +109,8 @@ clbm_status layout_of(const clbm_grid_desc* d, Layout* L, int* ld_out, int* h_ou
                                         : (size_t)(Q == 9 ? Tab<9>::S : Tab<21>::S) * d->n1;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    if ((long long)Q * (d->n1 + 2 * h) * ld >= (1LL << 31))
+        return fail(CLBM_EINVAL, "grid too large: the Q population planes must hold fewer than 2^31 values");
     L->stA = take((size_t)Q * (d->n1 + 2 * h) * ld * sb);
     L->stB = take((size_t)Q * (d->n1 + 2 * h) * ld * sb);
     L->tab = take(tab_entries * cb);

@@ -193,14 +193,16 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>
 }
 
 // Loader of the global buffer: p points at the cell in population plane 0,
-// P is the plane stride and ld the row stride (elements).
+// P is the plane stride and ld the row stride (elements).  Offsets are
+// 32-bit: a grid's Q planes hold fewer than 2^31 values (checked when the
+// grid is created).
 template <typename S>
 struct GlobalLoad {
     const S* p;
-    long long P;
+    int P;
     int ld;
     __device__ __forceinline__ typename Store<S>::C operator()(int al, int dr, int dc) const {
-        return Store<S>::ld(p + al * P + (long long)dr * ld + dc);
+        return Store<S>::ld(p + (al * P + dr * ld + dc));
     }
 };
 

@@ -31,7 +31,7 @@ __device__ __forceinline__ void batch_cell(const BatchGrid& g, int src, int i, i
     const Consts<C> k = Consts<C>::make(g.k);
     const long long off = (long long)(i + H) * g.ld + j + GC;
     Cell<Q, C> c;
-    pull_cell<Q, C>(GlobalLoad<S>{(const S*)g.phys[src] + off, g.plane, g.ld}, tb, k, c);
+    pull_cell<Q, C>(GlobalLoad<S>{(const S*)g.phys[src] + off, (int)g.plane, g.ld}, tb, k, c);
     S* dst = (S*)g.phys[src ^ 1] + off;
     const int dw = wrap_offset(j, g.n2);
     auto put = [&](int al, C v) {
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(128, ITER ? 2 : 4) k_batch_moments(const Batch
             const long long off = (long long)(i + H) * g.ld + j + GC;
             const S* p = (const S*)g.phys[src] + off;
             Cell<Q, C> c;
-            pull_cell<Q, C>(GlobalLoad<S>{p, g.plane, g.ld}, tb, kc, c);
+            pull_cell<Q, C>(GlobalLoad<S>{p, (int)g.plane, g.ld}, tb, kc, c);
             if (ITER) {
                 C out[Q];
                 collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });

@@ -30,7 +30,7 @@ __device__ __forceinline__ void cell_moments(const MomArgs& a, int iters, int i,
     const auto tb = TabOf<Q, C, GEN>::at(a.tab, i, j, a.n1, a.n2);
     const Consts<C> kc = Consts<C>::make(a.k);
     const long long off = (long long)(i + H) * a.ld + j + GC;
-    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld}, tb, kc, c);
+    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, (int)a.plane, a.ld}, tb, kc, c);
     if (ITER) {
         C out[Q];
         collide_emit<Q, C>(tb, c, kc, [&](int al, C x) { out[al] = x; });

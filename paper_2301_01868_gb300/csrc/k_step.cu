@@ -30,12 +30,13 @@ __global__ void __launch_bounds__(128, ITER ? 2 : (GEN ? 3 : 4)) k_fused_step(co
     const int row = i + H;
     const long long off = (long long)row * a.ld + j + GC;
     Cell<Q, C> c;
-    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, a.plane, a.ld}, tb, k, c);
+    const int pl = (int)a.plane;
+    pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, pl, a.ld}, tb, k, c);
     S* dst = (S*)a.dst + off;
     const int dw = wrap_offset(j, a.n2);
     auto put = [&](int al, C v) {
-        Store<S>::st(dst + al * a.plane, v);
-        if (dw != 0) Store<S>::st(dst + al * a.plane + dw, v);
+        Store<S>::st(dst + al * pl, v);
+        if (dw != 0) Store<S>::st(dst + (al * pl + dw), v);
     };
     if (!ITER) {
         collide_emit<Q, C>(tb, c, k, put);

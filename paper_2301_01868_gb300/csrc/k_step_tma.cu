@@ -306,9 +306,10 @@ __device__ __forceinline__ void ws_update_cell_tb(const WsLattice<S>& L, const C
         tb, k, c);
     S* dst = L.dst + (long long)(i + H) * L.ld + j + GC;
     const int dw = wrap_offset(j, L.n2);
+    const int pl = (int)L.plane;   // Q planes < 2^31 values (checked at creation)
     collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
-        Store<S>::st(dst + al * L.plane, v);
-        if (dw != 0) Store<S>::st(dst + al * L.plane + dw, v);
+        Store<S>::st(dst + al * pl, v);
+        if (dw != 0) Store<S>::st(dst + (al * pl + dw), v);
     });
     if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
         const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
