@@ -181,3 +181,43 @@ def test_precision_ladder_on_the_contracted_annulus_at_128():
     assert l2rel(u["fp16"], u["fp64"]) < 2e-2
     assert l2rel(u["bf16"], u["fp64"]) < 2e-1           # 8 mantissa bits: 1.2e-1
 
+
+
+def test_circular_poiseuille_ladder_d2q21_converges():
+    """The fourth flow of Sec. 3: the annulus 1 <= r <= 2 with both walls at
+    rest, driven by a constant contravariant azimuthal force g^2 (the
+    physical acceleration g^2 r sin(dtheta) grows with r; R10, R5), peak
+    speed about 0.01, tau = 0.8, uniform radial grids.  D2Q21 approaches
+    the exact profile (A/8)(r^2 - R1^2)(R2^2 - r^2)/r as N_r grows; D2Q9 at
+    N_r = 32 (6000 steps) stays further away."""
+    c = _clbm()
+    R1, R2, tau, target = 1.0, 2.0, 0.8, 0.01
+    errs = {}
+    for Q, rungs in ((21, (32, 64, 128)), (9, (32,))):
+        T0 = 2.0 / 3.0 if Q == 21 else 1.0 / 3.0
+        nu = T0 * (tau - 0.5)
+        for Nr in rungs:
+            Nt = I.n_theta(Nr, R1, R2)
+            e = I.polar_edges(R1, R2, Nr)
+            dx = (R2 - R1) / Nr
+            M = R1 / dx
+            alpha = math.sin(2.0 * math.pi / Nt)
+            r_lat = 0.5 * (e[:-1] + e[1:]) / dx
+            peak = np.abs(E.Annulus.poiseuille(M, M + Nr, 1.0).u(np.linspace(M, M + Nr, 2001))).max()
+            g2 = nu * target / (alpha * peak)          # A = alpha g2 / nu gives the peak
+            ex = E.Annulus.poiseuille(M, M + Nr, alpha * g2 / nu).u(r_lat)
+            g = c.Grid(Q, Nr, Nt, e, kind=c.POLAR, precision="fp64", bc_lo=c.NOSLIP, bc_hi=c.NOSLIP)
+            g.set_case(tau, 1.0, 0.0, 0.0, (0.0, g2))
+            if Q == 21:
+                steps, res = run_to_steady(g, 1e-10, 1000, 400000)
+            else:
+                steps = 6000
+                g.step(steps)
+                res = float("nan")
+            u = g.moments(names=("Ut2",))["Ut2"][:, 0] * alpha * r_lat
+            errs[(Q, Nr)] = l2rel(u, ex)
+            print("\nLADDER circular Poiseuille D2Q%d fp64 %dx%d: %d steps, residual %.1e, "
+                  "L2 error vs exact %.3e" % (Q, Nr, Nt, steps, res, errs[(Q, Nr)]))
+            g.close()
+    assert errs[(21, 64)] < errs[(21, 32)] / 1.6 and errs[(21, 128)] < errs[(21, 64)] / 1.6
+    assert errs[(21, 32)] < errs[(9, 32)]
