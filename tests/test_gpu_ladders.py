@@ -188,8 +188,9 @@ def test_circular_poiseuille_ladder_d2q21_converges():
     rest, driven by a constant contravariant azimuthal force g^2 (the
     physical acceleration g^2 r sin(dtheta) grows with r; R10, R5), peak
     speed about 0.01, tau = 0.8, uniform radial grids.  D2Q21 approaches
-    the exact profile (A/8)(r^2 - R1^2)(R2^2 - r^2)/r as N_r grows; D2Q9 at
-    N_r = 32 (6000 steps) stays further away."""
+    the exact profile (A/8)(r^2 - R1^2)(R2^2 - r^2)/r at second order as N_r
+    grows (the no-slip walls are second order; circular Couette's first order
+    comes from its moving wall); D2Q9 at N_r = 32 (6000 steps) is 40 % off."""
     c = _clbm()
     R1, R2, tau, target = 1.0, 2.0, 0.8, 0.01
     errs = {}
@@ -219,5 +220,6 @@ def test_circular_poiseuille_ladder_d2q21_converges():
             print("\nLADDER circular Poiseuille D2Q%d fp64 %dx%d: %d steps, residual %.1e, "
                   "L2 error vs exact %.3e" % (Q, Nr, Nt, steps, res, errs[(Q, Nr)]))
             g.close()
-    assert errs[(21, 64)] < errs[(21, 32)] / 1.6 and errs[(21, 128)] < errs[(21, 64)] / 1.6
-    assert errs[(21, 32)] < errs[(9, 32)]
+    # measured 2.33e-3 / 6.36e-4 / 1.67e-4 (second order), D2Q9 4.0e-1
+    assert errs[(21, 64)] < errs[(21, 32)] / 3.0 and errs[(21, 128)] < errs[(21, 64)] / 3.0
+    assert errs[(21, 32)] < errs[(9, 32)] / 10.0
