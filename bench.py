@@ -52,6 +52,8 @@ TABLE_VALUES_PER_CELL = {21: 73, 9: 37}   # per-cell table entries of general gr
 THREE_D_WORKLOADS = {
     "annulus3d_d3q39_fp32_128x804x32": ("fp32", 128, 804, 32, 1.0, 2.0, 0.35, 0.8, 0.01),
     "annulus3d_d3q39_fp64_128x804x32": ("fp64", 128, 804, 32, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "annulus3d_d3q39_f16_128x804x32": ("fp16", 128, 804, 32, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "annulus3d_d3q39_bf16_128x804x32": ("bf16", 128, 804, 32, 1.0, 2.0, 0.35, 0.8, 0.01),
 }
 DEFAULT = "circular_couette_d2q21_fp32_1024x4096"
 METRIC = "D2Q21 curvilinear MLUPS and % HBM roofline; served solves/s, p99 latency"
@@ -460,7 +462,8 @@ def run_3d(args):
     out = {"metric": "D3Q39 curvilinear MLUPS and % HBM roofline", "value": cells * steps / (ms * 1e-3) / 1e6,
            "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp64": "f64", "fp32": "f32"}[prec], "data": "synthetic",
+           "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 compute, f16 storage",
+                     "bf16": "f32 compute, bf16 storage"}[prec], "data": "synthetic",
            "config": {"workload": wl, "lattice": "D3Q39", "n1": n1, "n2": n2, "n3": n3,
                       "geometry": "annulus R2/R1=2 extruded along z, radial CR=%g" % THREE_D_WORKLOADS[wl][6],
                       "tau": tau, "u_wall": THREE_D_WORKLOADS[wl][8], "storage": prec, "chunk": chunk,

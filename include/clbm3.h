@@ -41,7 +41,8 @@ typedef struct clbm3_grid* clbm3_handle;
 typedef enum { CLBM3_CHANNEL = 0, CLBM3_ANNULUS = 1 } clbm3_kind;
 
 typedef struct {
-    int precision;          /* CLBM_FP64 or CLBM_FP32 (compute and storage) */
+    int precision;          /* clbm_precision: FP64, FP32, or FP32 compute with FP16 /
+                               BF16 storage of the deviations (as in clbm.h) */
     int n1, n2, n3;         /* n1 >= 4; n2, n3 >= 1 */
     int kind;               /* clbm3_kind */
     const double* edges;    /* n1 + 1 increasing wall-normal / radial edges (host) */

@@ -195,16 +195,6 @@ __global__ void k3_tables(const double* __restrict__ geo, C* __restrict__ tab, i
 
 // ------------------------------------------------------------- kernels
 
-template <typename S> struct St3;
-template <> struct St3<double> {
-    __device__ static double ld(const double* p) { return *p; }
-    __device__ static void st(double* p, double v) { *p = v; }
-};
-template <> struct St3<float> {
-    __device__ static float ld(const float* p) { return *p; }
-    __device__ static void st(float* p, float v) { *p = v; }
-};
-
 template <typename C>
 __device__ __forceinline__ C* wall_ptr(void* wall, int field, int w, int m, int n23) {
     return (C*)wall + ((size_t)(field * 2 + w) * H + (m - 1)) * n23;
@@ -240,13 +230,13 @@ __global__ void __launch_bounds__(TB) k3_boundary(Args3 A, S* __restrict__ st) {
         const int h = hat3(a);
         C v;
         if (moving) {
-            v = C(St3<S>::ld(src + (size_t)h * A.plane)) +
+            v = Store<S>::ld(src + (size_t)h * A.plane) +
                 coef * C(w3(h)) * (C(c2_3(h)) * (U0 - u2) + C(c3_3(h)) * (C(0) - u3));
         } else {
             const int b = opp3(a);
-            v = C(St3<S>::ld(src + (size_t)b * A.plane)) + C(g[Geo3::REF + b] - g[Geo3::REF + h]);
+            v = Store<S>::ld(src + (size_t)b * A.plane) + C(g[Geo3::REF + b] - g[Geo3::REF + h]);
         }
-        St3<S>::st(dst + (size_t)a * A.plane, v);
+        Store<S>::st(dst + (size_t)a * A.plane, v);
     }
 }
 
@@ -287,7 +277,7 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     // (Eq. 15), two directions a, b = -a at a time in the two lanes of a pair
     using P = typename PairOf<C>::T;
     P dd[NP];
-    const C d0 = C(St3<S>::ld(src + own));
+    const C d0 = Store<S>::ld(src + own);
     P sd = mkp(d0, C(0)), s1 = mkp(C(0), C(0)), s2 = s1, s3 = s1;
     P f1 = mkp(ldt(t + Tab3::F0), C(0)), f2 = mkp(ldt(t + Tab3::F0 + 1), C(0)), f3 = mkp(ldt(t + Tab3::F0 + 2), C(0));
 #pragma unroll
@@ -297,8 +287,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         // N_a from q - c_a, N_b from q + c_a; the lagged values are the cell's own
         const unsigned ia = (unsigned)(i - c1 - 1 + H) * (unsigned)n23 + (unsigned)(jo[c2 + 3] + ko[c3 + 3]);
         const unsigned ib = (unsigned)(i + c1 - 1 + H) * (unsigned)n23 + (unsigned)(jo[3 - c2] + ko[3 - c3]);
-        const P pp = mkp(C(St3<S>::ld(src + (a * pl + ia))), C(St3<S>::ld(src + (b * pl + ib))));
-        const P lg = mkp(C(St3<S>::ld(src + (b * pl + own))), C(St3<S>::ld(src + (a * pl + own))));
+        const P pp = mkp(Store<S>::ld(src + (a * pl + ia)), Store<S>::ld(src + (b * pl + ib)));
+        const P lg = mkp(Store<S>::ld(src + (b * pl + own)), Store<S>::ld(src + (a * pl + own)));
         const V4<C> w0 = ld4(t + Tab3::PA(p)), w1 = ld4(t + Tab3::PA(p) + 4);
         const P d = c1 != 0 ? padd(pp, mkp(w1.z, w1.w)) : pp;
         dd[p] = d;
@@ -391,7 +381,7 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     const C uu = V1 * V1 + V2 * V2 + V3 * V3;
     const C base = C(-0.5) * iT0 * uu * rho * tinv - trP * iT0;
     S* dst = (S*)A.dst + own;
-    St3<S>::st(dst, S(omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base)));
+    Store<S>::st(dst, omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base));
     const P omt2 = mkp(omt, omt), J2 = mkp(J, J);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -405,8 +395,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         const C w = C(w3(a));
         // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
         const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
-        St3<S>::st(dst + a * pl, S(o.x));
-        St3<S>::st(dst + b * pl, S(o.y));
+        Store<S>::st(dst + a * pl, o.x);
+        Store<S>::st(dst + b * pl, o.y);
     }
     // the moments the walls read next (rows within H of a wall)
     if (i <= H) {
@@ -431,7 +421,9 @@ __global__ void k3_from64(const double* __restrict__ Np, const double* __restric
     const int r = blockIdx.y;
     const size_t nc = (size_t)n1 * n23, m = (size_t)r * n23 + jk, own = (size_t)(r + H) * n23 + jk;
     const double* g = geo + (size_t)r * Geo3::S;
-    for (int a = 0; a < Q; ++a) st[(size_t)a * plane + own] = S(Np ? Np[a * nc + m] - g[Geo3::REF + a] : 0.0);
+    using C = typename Store<S>::C;
+    for (int a = 0; a < Q; ++a)
+        Store<S>::st(st + (size_t)a * plane + own, C(Np ? Np[a * nc + m] - g[Geo3::REF + a] : 0.0));
 }
 
 template <typename S>
@@ -442,7 +434,7 @@ __global__ void k3_to64(const S* __restrict__ st, const double* __restrict__ geo
     const int r = blockIdx.y;
     const size_t nc = (size_t)n1 * n23, m = (size_t)r * n23 + jk, own = (size_t)(r + H) * n23 + jk;
     const double* g = geo + (size_t)r * Geo3::S;
-    for (int a = 0; a < Q; ++a) Np[a * nc + m] = double(st[(size_t)a * plane + own]) + g[Geo3::REF + a];
+    for (int a = 0; a < Q; ++a) Np[a * nc + m] = double(Store<S>::ld(st + (size_t)a * plane + own)) + g[Geo3::REF + a];
 }
 
 // Wall moments of rows 1..H and n1-H+1..n1 from cell fields (NULL: rho0, 0).
@@ -471,7 +463,7 @@ __global__ void __launch_bounds__(TB) k3_totals(const S* __restrict__ st, int n1
         const size_t own = (size_t)(r + H) * n23 + jk;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const double s = double(st[(size_t)a * plane + own]);
+            const double s = double(Store<S>::ld(st + (size_t)a * plane + own));
             v[0] += s;
             v[1] += c1_3(a) * s;
             v[2] += c2_3(a) * s;
@@ -510,6 +502,7 @@ __global__ void k3_totals_final(const double* __restrict__ partial, int nb, doub
 // ------------------------------------------------------------------ C ABI
 
 using namespace clbm::d3;
+using clbm::Store;
 
 struct clbm3_grid {
     int prec, n1, n2, n3, kind, bc_lo, bc_hi, device;
@@ -524,7 +517,7 @@ struct clbm3_grid {
     std::vector<double> hedges;
 };
 
-namespace {
+namespace k3api {
 
 clbm_status fail3(clbm_status s, const char* fmt, ...) {
     char buf[512];
@@ -544,7 +537,21 @@ clbm_status fail3(clbm_status s, const char* fmt, ...) {
                          __LINE__);                                                           \
     } while (0)
 
-size_t sbytes(const clbm3_grid* g) { return g->prec == CLBM_FP64 ? 8 : 4; }
+size_t sbytes(const clbm3_grid* g) { return g->prec == CLBM_FP64 ? 8 : g->prec == CLBM_FP32 ? 4 : 2; }
+size_t cbytes(const clbm3_grid* g) { return g->prec == CLBM_FP64 ? 8 : 4; }  // tables, wall moments
+
+template <typename T> struct Tag { using type = T; };
+
+// Call f(Tag<S>{}) for the storage type S of precision prec.
+template <typename F>
+void by_storage(int prec, F&& f) {
+    switch (prec) {
+        case CLBM_FP64: f(Tag<double>{}); break;
+        case CLBM_FP32: f(Tag<float>{}); break;
+        case CLBM_FP32_F16STORE: f(Tag<__half>{}); break;
+        default: f(Tag<__nv_bfloat16>{}); break;
+    }
+}
 int n23(const clbm3_grid* g) { return g->n2 * g->n3; }
 long long plane(const clbm3_grid* g) { return (long long)(g->n1 + 2 * H) * g->n2 * g->n3; }
 size_t ncells(const clbm3_grid* g) { return (size_t)g->n1 * g->n2 * g->n3; }
@@ -578,18 +585,18 @@ Args3 args(const clbm3_grid* g) {
 
 void launch_boundary(const clbm3_grid* g, const Args3& A) {
     dim3 grid((n23(g) + TB - 1) / TB, 2 * H);
-    if (g->prec == CLBM_FP64)
-        k3_boundary<double, double><<<grid, TB, 0, g->stream>>>(A, (double*)A.src);
-    else
-        k3_boundary<float, float><<<grid, TB, 0, g->stream>>>(A, (float*)A.src);
+    by_storage(g->prec, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k3_boundary<S, typename Store<S>::C><<<grid, TB, 0, g->stream>>>(A, (S*)A.src);
+    });
 }
 
 template <bool MOM>
 void launch_cells(const clbm3_grid* g, const Args3& A, double* rho, double* ut) {
-    if (g->prec == CLBM_FP64)
-        k3_step<double, double, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
-    else
-        k3_step<float, float, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
+    by_storage(g->prec, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k3_step<S, typename Store<S>::C, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
+    });
 }
 
 clbm_status staging(clbm3_grid* g, double** out) {
@@ -605,15 +612,17 @@ clbm_status staging(clbm3_grid* g, double** out) {
     return CLBM_OK;
 }
 
-}  // namespace
+}  // namespace k3api
+
+using namespace k3api;
 
 extern "C" {
 
 clbm_status clbm3_create_grid(const clbm3_grid_desc* d, clbm3_handle* out) {
     if (!d || !out) return fail3(CLBM_EINVAL, "NULL argument");
     *out = nullptr;
-    if (d->precision != CLBM_FP64 && d->precision != CLBM_FP32)
-        return fail3(CLBM_EINVAL, "precision must be CLBM_FP64 or CLBM_FP32");
+    if (d->precision < CLBM_FP64 || d->precision > CLBM_FP32_BF16STORE)
+        return fail3(CLBM_EINVAL, "bad precision");
     if (d->n1 < 4 || d->n2 < 1 || d->n3 < 1) return fail3(CLBM_EINVAL, "need n1 >= 4 and n2, n3 >= 1");
     if ((long long)Q * (d->n1 + 2 * H) * d->n2 * d->n3 >= (1LL << 31))
         return fail3(CLBM_EINVAL, "grid too large: 39 (n1 + 6) n2 n3 must stay below 2^31");
@@ -642,7 +651,7 @@ clbm_status clbm3_create_grid(const clbm3_grid_desc* d, clbm3_handle* out) {
     g->dx = d->dx > 0.0 ? d->dx : (d->edges[d->n1] - d->edges[0]) / d->n1;
     g->stream = (cudaStream_t)d->stream;
     g->hedges.assign(d->edges, d->edges + d->n1 + 1);
-    const size_t sb = sbytes(g), cb = sb;  // compute type = storage type
+    const size_t sb = sbytes(g), cb = cbytes(g);
     const size_t nb = (size_t)((n23(g) + TB - 1) / TB) * g->n1;
     bool ok = cudaMalloc((void**)&g->edges, (g->n1 + 1) * 8) == cudaSuccess &&
               cudaMalloc((void**)&g->geo, (size_t)g->n1 * Geo3::S * 8) == cudaSuccess &&
@@ -684,7 +693,7 @@ clbm_status clbm3_set_case(clbm3_handle g, const clbm3_case* c) {
     k3_reference<<<(g->n1 + 63) / 64, 64, 0, g->stream>>>(g->geo, g->n1, c->rho0);
     if (g->prec == CLBM_FP64)
         k3_tables<double><<<(g->n1 + 63) / 64, 64, 0, g->stream>>>(g->geo, (double*)g->tab, g->n1);
-    else
+    else  // FP32 compute for FP32 and 16-bit storage
         k3_tables<float><<<(g->n1 + 63) / 64, 64, 0, g->stream>>>(g->geo, (float*)g->tab, g->n1);
     g->cur = 0;
     CK3(cudaMemsetAsync(g->st[0], 0, (size_t)Q * plane(g) * sbytes(g), g->stream));
@@ -731,13 +740,12 @@ clbm_status clbm3_set_state(clbm3_handle g, const double* Np, const double* rho,
     }
     dim3 cg((n23(g) + TB - 1) / TB, g->n1), wg((n23(g) + TB - 1) / TB, 2 * H);
     g->cur = 0;
-    if (g->prec == CLBM_FP64) {
-        k3_from64<double><<<cg, TB, 0, g->stream>>>(dN, g->geo, (double*)g->st[0], g->n1, n23(g), plane(g));
-        k3_wall_init<double><<<wg, TB, 0, g->stream>>>(g->wall, dr, d2, d3, g->n1, n23(g), g->cs.rho0);
-    } else {
-        k3_from64<float><<<cg, TB, 0, g->stream>>>(dN, g->geo, (float*)g->st[0], g->n1, n23(g), plane(g));
-        k3_wall_init<float><<<wg, TB, 0, g->stream>>>(g->wall, dr, d2, d3, g->n1, n23(g), g->cs.rho0);
-    }
+    by_storage(g->prec, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k3_from64<S><<<cg, TB, 0, g->stream>>>(dN, g->geo, (S*)g->st[0], g->n1, n23(g), plane(g));
+        k3_wall_init<typename Store<S>::C><<<wg, TB, 0, g->stream>>>(g->wall, dr, d2, d3, g->n1, n23(g),
+                                                                    g->cs.rho0);
+    });
     CK3(cudaGetLastError());
     CK3(cudaStreamSynchronize(g->stream));
     return CLBM_OK;
@@ -753,10 +761,10 @@ clbm_status clbm3_get_state(clbm3_handle g, double* Np, int dst_is_device) {
         if (st != CLBM_OK) return st;
     }
     dim3 cg((n23(g) + TB - 1) / TB, g->n1);
-    if (g->prec == CLBM_FP64)
-        k3_to64<double><<<cg, TB, 0, g->stream>>>((const double*)g->st[g->cur], g->geo, dN, g->n1, n23(g), plane(g));
-    else
-        k3_to64<float><<<cg, TB, 0, g->stream>>>((const float*)g->st[g->cur], g->geo, dN, g->n1, n23(g), plane(g));
+    by_storage(g->prec, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k3_to64<S><<<cg, TB, 0, g->stream>>>((const S*)g->st[g->cur], g->geo, dN, g->n1, n23(g), plane(g));
+    });
     CK3(cudaGetLastError());
     if (!dst_is_device)
         CK3(cudaMemcpyAsync(Np, dN, (size_t)Q * ncells(g) * 8, cudaMemcpyDeviceToHost, g->stream));
@@ -811,10 +819,10 @@ clbm_status clbm3_totals(clbm3_handle g, double out[4]) {
     CK3(cudaSetDevice(g->device));
     dim3 cg((n23(g) + TB - 1) / TB, g->n1);
     const int nb = (int)(cg.x * cg.y);
-    if (g->prec == CLBM_FP64)
-        k3_totals<double><<<cg, TB, 0, g->stream>>>((const double*)g->st[g->cur], g->n1, n23(g), plane(g), g->partial);
-    else
-        k3_totals<float><<<cg, TB, 0, g->stream>>>((const float*)g->st[g->cur], g->n1, n23(g), plane(g), g->partial);
+    by_storage(g->prec, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k3_totals<S><<<cg, TB, 0, g->stream>>>((const S*)g->st[g->cur], g->n1, n23(g), plane(g), g->partial);
+    });
     k3_totals_final<<<4, 256, 0, g->stream>>>(g->partial, nb, g->red);
     CK3(cudaGetLastError());
     double v[4];

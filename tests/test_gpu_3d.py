@@ -111,6 +111,14 @@ def test_fp32_channel_velocity_matches_oracle():
     assert rel(g.moments()["Ut"], o.moments()["Ut"]) <= 1e-5
 
 
+@pytest.mark.parametrize("prec,tol", [(2, 3e-3), (3, 3e-2)])
+def test_16bit_storage_channel_velocity_near_oracle(prec, tol):
+    """FP32 compute with FP16 / BF16 storage of the deviations."""
+    case = stretched_channel(bc=(1, 0), U0=(0.02, 0.0), g=(0.0, 1e-6, 2e-6))
+    o, g = run_pair(case, 200, prec=prec, amp=0.0)
+    assert rel(g.moments()["Ut"], o.moments()["Ut"]) <= tol
+
+
 def test_totals_conserve_mass_and_match_oracle():
     case = stretched_channel(bc=(0, 0), g=(0.0, 0.0, 0.0))
     o, g = run_pair(case, 0)
