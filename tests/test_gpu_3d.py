@@ -151,7 +151,7 @@ def test_grid_rejects_bad_descriptions():
     with pytest.raises(c.ClbmError):
         c.Grid3(6, 4, 4, np.array([0, 1, 2, 2, 3, 4, 5.0]))
     with pytest.raises(c.ClbmError):
-        c.Grid3(6, 4, 4, np.arange(7.0), precision=2)
+        c.Grid3(6, 4, 4, np.arange(7.0), precision=4)
     g = c.Grid3(6, 4, 4, np.arange(7.0))
     with pytest.raises(c.ClbmError):
         g.step(1)                 # no case yet
