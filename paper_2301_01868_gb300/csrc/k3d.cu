@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     const C uu = V1 * V1 + V2 * V2 + V3 * V3;
     const C base = C(-0.5) * iT0 * uu * rho * tinv - trP * iT0;
     S* dst = (S*)A.dst + own;
-    Store<S>::st(dst, omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base));
+    const uint64_t pol = l2_evict_first();   // read only by the next launch
+    StHint<S>::st(dst, omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base), pol);
     const P omt2 = mkp(omt, omt), J2 = mkp(J, J);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -395,8 +396,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         const C w = C(w3(a));
         // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
         const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
-        Store<S>::st(dst + a * pl, o.x);
-        Store<S>::st(dst + b * pl, o.y);
+        StHint<S>::st(dst + a * pl, o.x, pol);
+        StHint<S>::st(dst + b * pl, o.y, pol);
     }
     // the moments the walls read next (rows within H of a wall)
     if (i <= H) {
