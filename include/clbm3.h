@@ -77,6 +77,24 @@ clbm_status clbm3_set_state(clbm3_handle h, const double* Np, const double* rho_
                             const double* ut2_prev, const double* ut3_prev, int src_is_device);
 clbm_status clbm3_get_state(clbm3_handle h, double* Np, int dst_is_device);
 
+/* Start from the local equilibrium of given fields: N'(q,-1) = J f^eq(rho,
+ * U, Ut = U; g^{ij}(q)) (Eq. 19, formed in FP64 on the device), the walls'
+ * last-collision moments (rho, U^2, U^3), t = 0.  rho [n1][n2][n3] and U
+ * [3][n1][n2][n3] (contravariant) FP64, host or device; NULL: rho0 / 0.
+ * Requires clbm3_set_case.  Synchronises. */
+clbm_status clbm3_set_equilibrium(clbm3_handle h, const double* rho, const double* U, int src_is_device);
+
+/* Checkpoint / resume: clbm3_checkpoint copies the case, the time, the raw
+ * current state buffer (storage type, ghost rows included) and the wall
+ * moments into buf (host memory of clbm3_checkpoint_bytes bytes,
+ * caller-owned); clbm3_restore loads it into a grid with the same
+ * description (no case needed first) and stepping then continues bit for
+ * bit.  CLBM_EINVAL if precision, sizes or kind differ.  The paper has no
+ * counterpart.  Both synchronise. */
+clbm_status clbm3_checkpoint_bytes(clbm3_handle h, size_t* bytes);
+clbm_status clbm3_checkpoint(clbm3_handle h, void* buf);
+clbm_status clbm3_restore(clbm3_handle h, const void* buf);
+
 /* Advance n >= 0 time steps (Sec. 2: advection Eq. 12, moments Eqs. 7-10,
  * lagged force Eq. 15, Ut Eq. 18, f^eq Eq. 19, dPi Eq. 16, dN Eq. 17, BGK
  * Eqs. 6, 11; App. B walls): two launches per step (ghost rows, update),

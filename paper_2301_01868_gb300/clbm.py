@@ -107,6 +107,10 @@ def lib():
             "clbm3_moments": [h, vp, vp, C.c_int],
             "clbm3_totals": [h, dp],
             "clbm3_time": [h, C.POINTER(ll)],
+            "clbm3_set_equilibrium": [h, vp, vp, C.c_int],
+            "clbm3_checkpoint_bytes": [h, C.POINTER(C.c_size_t)],
+            "clbm3_checkpoint": [h, vp],
+            "clbm3_restore": [h, vp],
             "clbm3_destroy": [h],
         }
         for name, args in sig.items():
@@ -499,6 +503,32 @@ class Grid3:
 
     def step(self, n=1):
         _check(lib().clbm3_step(self._h, int(n)))
+
+    def set_equilibrium(self, rho=None, U=None):
+        """Start from J f^eq(rho, U, Ut = U) (Eq. 19): rho (n1, n2, n3) and
+        contravariant U (3, n1, n2, n3), float64 numpy (None: rho0 / 0)."""
+        arrs = [None if x is None else np.ascontiguousarray(x, dtype=np.float64) for x in (rho, U)]
+        if arrs[0] is not None and arrs[0].shape != self.shape:
+            raise ValueError("rho must be (n1, n2, n3)")
+        if arrs[1] is not None and arrs[1].shape != (3,) + self.shape:
+            raise ValueError("U must be (3, n1, n2, n3)")
+        _check(lib().clbm3_set_equilibrium(self._h, _ptr(arrs[0]), _ptr(arrs[1]), 0))
+
+    def checkpoint(self):
+        """Case, time, raw state and wall moments as bytes (restore() resumes bit for bit)."""
+        n = C.c_size_t()
+        _check(lib().clbm3_checkpoint_bytes(self._h, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().clbm3_checkpoint(self._h, buf.ctypes.data))
+        return buf.tobytes()
+
+    def restore(self, blob):
+        buf = np.frombuffer(blob, dtype=np.uint8)
+        n = C.c_size_t()
+        _check(lib().clbm3_checkpoint_bytes(self._h, C.byref(n)))
+        if buf.size != n.value:
+            raise ClbmError(1, "checkpoint is %d bytes, this grid's are %d" % (buf.size, n.value))
+        _check(lib().clbm3_restore(self._h, buf.ctypes.data))
 
     def moments(self):
         """dict: rho (n1, n2, n3) and Ut (3, n1, n2, n3), float64 numpy."""

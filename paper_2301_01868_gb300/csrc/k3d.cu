@@ -427,6 +427,44 @@ __global__ void k3_from64(const double* __restrict__ Np, const double* __restric
         Store<S>::st(st + (size_t)a * plane + own, C(Np ? Np[a * nc + m] - g[Geo3::REF + a] : 0.0));
 }
 
+// Equilibrium start N(q, 0) = J f^eq(rho, U, Ut = U; g^{ij}(q)) in FP64 (Eq.
+// 19 in three coordinates: second moment T0 g^{ij} + Ut^i Ut^j, third built
+// from Ut, U and g^{ij}; Ut = U with no force known yet), written as FP64
+// N' ([a][cell]) for k3_from64.  Absent fields are rho0 and 0.
+__global__ void k3_equilibrium(const double* __restrict__ rho, const double* __restrict__ U,
+                               const double* __restrict__ geo, double* __restrict__ Np, int n1, int n23,
+                               double rho0) {
+    const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (jk >= n23) return;
+    const int r = blockIdx.y;
+    const size_t nc = (size_t)n1 * n23, m = (size_t)r * n23 + jk;
+    const double* g = geo + (size_t)r * Geo3::S;
+    const double R = rho ? rho[m] : rho0;
+    const double u[3] = {U ? U[m] : 0.0, U ? U[nc + m] : 0.0, U ? U[2 * nc + m] : 0.0};
+    const int P[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    double e[3][3];   // g^{ij} - delta^{ij}
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) e[p][q] = g[Geo3::GI + P[p][q]] - (p == q ? 1.0 : 0.0);
+    for (int a = 0; a < Q; ++a) {
+        const double c[3] = {(double)c1_3(a), (double)c2_3(a), (double)c3_3(a)};
+        double h1 = 0.0, h2 = 0.0, h3 = 0.0;
+        for (int p = 0; p < 3; ++p) h1 += c[p] * u[p];
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) {
+                const double A = u[p] * u[q] + T0 * e[p][q];
+                h2 += (c[p] * c[q] - (p == q ? T0 : 0.0)) * A;
+                for (int k = 0; k < 3; ++k) {
+                    // C^{pqk} = Ut Ut Ut + T0 ((g - delta)^{pq} U^k + cyclic), Ut = U
+                    const double C3 = u[p] * u[q] * u[k] + T0 * (e[p][q] * u[k] + e[q][k] * u[p] + e[k][p] * u[q]);
+                    const double H3 = c[p] * c[q] * c[k] - T0 * (c[p] * (q == k) + c[q] * (k == p) + c[k] * (p == q));
+                    h3 += H3 * C3;
+                }
+            }
+        const double Pa = 1.0 + h1 / T0 + h2 / (2.0 * T0 * T0) + h3 / (6.0 * T0 * T0 * T0);
+        Np[(size_t)a * nc + m] = g[Geo3::J] * w3(a) * R * Pa;
+    }
+}
+
 template <typename S>
 __global__ void k3_to64(const S* __restrict__ st, const double* __restrict__ geo, double* __restrict__ Np, int n1,
                         int n23, long long plane) {
@@ -613,6 +651,30 @@ clbm_status staging(clbm3_grid* g, double** out) {
     return CLBM_OK;
 }
 
+// Checkpoint header: the grid's identity, case and time; the raw state
+// buffer (ghost rows included, in the storage type) and the wall moments
+// follow it.
+struct Ckpt3 {
+    char magic[8];
+    int prec, n1, n2, n3, kind;
+    long long t;
+    clbm3_case cs;
+};
+
+Ckpt3 ckpt_header(const clbm3_grid* g) {
+    Ckpt3 h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "CLBM3CK1", 8);
+    h.prec = g->prec;
+    h.n1 = g->n1;
+    h.n2 = g->n2;
+    h.n3 = g->n3;
+    h.kind = g->kind;
+    h.t = g->t;
+    h.cs = g->cs;
+    return h;
+}
+
 }  // namespace k3api
 
 using namespace k3api;
@@ -749,6 +811,85 @@ clbm_status clbm3_set_state(clbm3_handle g, const double* Np, const double* rho,
     });
     CK3(cudaGetLastError());
     CK3(cudaStreamSynchronize(g->stream));
+    return CLBM_OK;
+}
+
+clbm_status clbm3_set_equilibrium(clbm3_handle g, const double* rho, const double* U, int src_is_device) {
+    if (!g) return fail3(CLBM_EINVAL, "handle is NULL");
+    if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
+    CK3(cudaSetDevice(g->device));
+    const size_t nc = ncells(g);
+    double* sb = nullptr;
+    clbm_status st = staging(g, &sb);
+    if (st != CLBM_OK) return st;
+    const double *dr = rho, *du = U;
+    double* extra = nullptr;
+    struct FreeOnExit {
+        double** p;
+        ~FreeOnExit() { cudaFree(*p); }
+    } guard{&extra};
+    if (!src_is_device && (rho || U)) {
+        CK3(cudaMalloc((void**)&extra, 4 * nc * 8));
+        if (rho) CK3(cudaMemcpyAsync(extra, rho, nc * 8, cudaMemcpyHostToDevice, g->stream));
+        if (U) CK3(cudaMemcpyAsync(extra + nc, U, 3 * nc * 8, cudaMemcpyHostToDevice, g->stream));
+        dr = rho ? extra : nullptr;
+        du = U ? extra + nc : nullptr;
+    }
+    dim3 cg((n23(g) + TB - 1) / TB, g->n1), wg((n23(g) + TB - 1) / TB, 2 * H);
+    k3_equilibrium<<<cg, TB, 0, g->stream>>>(dr, du, g->geo, sb, g->n1, n23(g), g->cs.rho0);
+    g->cur = 0;
+    by_storage(g->prec, [&](auto tag) {
+        using S = typename decltype(tag)::type;
+        k3_from64<S><<<cg, TB, 0, g->stream>>>(sb, g->geo, (S*)g->st[0], g->n1, n23(g), plane(g));
+        k3_wall_init<typename Store<S>::C><<<wg, TB, 0, g->stream>>>(g->wall, dr, du ? du + nc : nullptr,
+                                                                    du ? du + 2 * nc : nullptr, g->n1,
+                                                                    n23(g), g->cs.rho0);
+    });
+    CK3(cudaGetLastError());
+    CK3(cudaStreamSynchronize(g->stream));
+    g->t = 0;
+    return CLBM_OK;
+}
+
+clbm_status clbm3_checkpoint_bytes(clbm3_handle g, size_t* bytes) {
+    if (!g || !bytes) return fail3(CLBM_EINVAL, "NULL argument");
+    *bytes = sizeof(Ckpt3) + (size_t)Q * plane(g) * sbytes(g) + (size_t)3 * 2 * H * n23(g) * cbytes(g);
+    return CLBM_OK;
+}
+
+clbm_status clbm3_checkpoint(clbm3_handle g, void* buf) {
+    if (!g || !buf) return fail3(CLBM_EINVAL, "NULL argument");
+    if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
+    CK3(cudaSetDevice(g->device));
+    Ckpt3 h = ckpt_header(g);
+    char* p = (char*)buf;
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t sbb = (size_t)Q * plane(g) * sbytes(g), wb = (size_t)3 * 2 * H * n23(g) * cbytes(g);
+    CK3(cudaMemcpyAsync(p, g->st[g->cur], sbb, cudaMemcpyDeviceToHost, g->stream));
+    CK3(cudaMemcpyAsync(p + sbb, g->wall, wb, cudaMemcpyDeviceToHost, g->stream));
+    CK3(cudaStreamSynchronize(g->stream));
+    return CLBM_OK;
+}
+
+clbm_status clbm3_restore(clbm3_handle g, const void* buf) {
+    if (!g || !buf) return fail3(CLBM_EINVAL, "NULL argument");
+    CK3(cudaSetDevice(g->device));
+    Ckpt3 h, mine = ckpt_header(g);
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.magic, mine.magic, 8) != 0 || h.prec != mine.prec || h.n1 != mine.n1 || h.n2 != mine.n2 ||
+        h.n3 != mine.n3 || h.kind != mine.kind)
+        return fail3(CLBM_EINVAL, "checkpoint does not match this grid (precision, size or kind)");
+    if (!(h.cs.tau > 0.5) || !(h.cs.rho0 > 0.0)) return fail3(CLBM_EINVAL, "checkpoint holds a bad case");
+    clbm_status st = clbm3_set_case(g, &h.cs);     // tables of the saved case
+    if (st != CLBM_OK) return st;
+    const char* p = (const char*)buf + sizeof(h);
+    const size_t sbb = (size_t)Q * plane(g) * sbytes(g), wb = (size_t)3 * 2 * H * n23(g) * cbytes(g);
+    g->cur = 0;
+    CK3(cudaMemcpyAsync(g->st[0], p, sbb, cudaMemcpyHostToDevice, g->stream));
+    CK3(cudaMemcpyAsync(g->wall, p + sbb, wb, cudaMemcpyHostToDevice, g->stream));
+    CK3(cudaStreamSynchronize(g->stream));
+    g->t = h.t;
     return CLBM_OK;
 }
 

@@ -188,3 +188,53 @@ def test_circular_couette_converges_in_three_dimensions():
         g.close()
     assert errs[1] < errs[0] / 1.6 and errs[2] < errs[1] / 1.6
     assert errs[1] < 0.05
+
+
+def test_3d_equilibrium_start_matches_oracle_feq():
+    """J f^eq of given fields (Eq. 19) against the 3-D oracle's f^eq, cell by
+    cell; then 40 steps from that start against the oracle (the walls read
+    the start's moments)."""
+    e = I.polar_edges(1.0, 2.0, 6, 0.35)
+    case = Case3(6, 30, 3, 1, edges=e, step3=0.2, bc=(1, 0), U0=(0.04, 0.0))
+    o = case.oracle()
+    g = case.gpu(0)
+    sh = (6, 30, 3)
+    rho = 1.0 + I.smooth_field((6, 30, 3), seed=21, amplitude=0.02)
+    U = I.smooth_field((18, 30, 3), seed=22, amplitude=0.01).reshape((3,) + sh)
+    g.set_equilibrium(rho, U)
+    N = g.state()
+    ref = np.empty_like(N)
+    for i in range(6):
+        geo = o.row_geometry(i + 1)
+        for j in range(30):
+            for k in range(3):
+                u = U[:, i, j, k]
+                for a in range(39):
+                    ref[a, i, j, k] = geo["J"] * o.feq(a, rho[i, j, k], u, u, geo["ginv"])
+    assert np.abs(N - ref).max() <= 1e-14 * np.abs(ref).max()
+    o.set_state(ref, rho, U[1], U[2])
+    o.step(40)
+    g.step(40)
+    assert rel(g.state(), o.state()) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_3d_restore_continues_bit_for_bit(prec):
+    case = stretched_channel(n1=8, n2=12, n3=10, bc=(1, 0), U0=(0.02, 0.0), g=(0.0, 1e-6, 1e-6))
+    a = case.gpu(prec)
+    a.step(30)
+    blob = a.checkpoint()
+    a.step(40)
+    sa = a.state()
+    c = _clbm()
+    b = c.Grid3(case.n1, case.n2, case.n3, case.edges, kind=case.kind, step2=case.step2, step3=case.step3,
+                precision=prec, bc_lo=1, bc_hi=0)
+    b.restore(blob)
+    assert b.t == 30
+    b.step(40)
+    assert np.array_equal(b.state(), sa)
+    other = c.Grid3(case.n1, case.n2, case.n3 + 1, np.asarray(case.edges), kind=case.kind,
+                    step2=case.step2, step3=case.step3, precision=prec)
+    with pytest.raises(c.ClbmError):
+        other.restore(blob)
+
