@@ -78,13 +78,36 @@ struct RowTab {
     __device__ __forceinline__ V4<C> pd(int q) const { return ld4(p + Tab<Q>::pd(q)); }
 };
 
+// A sum of products v * k whose coefficients k are lattice constants
+// (compile-time after unrolling), accumulated in the order of the terms.  A
+// term with k = 0 is left out: IEEE rules forbid a compiler to drop a
+// product with a literal zero (it would be NaN for an infinite v), but adding
+// an exact zero leaves the sum unchanged, so leaving it out saves the
+// instruction and keeps every rounding.
+template <typename C>
+struct KSum {
+    C s = C(0);
+    bool any = false;
+    __device__ __forceinline__ KSum() {}
+    __device__ __forceinline__ explicit KSum(C first) : s(first), any(true) {}
+    __device__ __forceinline__ void add(C v, double k) {
+        if (k != 0.0) {
+            s = any ? fma(v, C(k), s) : v * C(k);
+            any = true;
+        }
+    }
+};
+
 // Rest polynomial of Eq. 19 at U = Ut = 0 in the compute type:
 // 1 + [c.(g - 1).c / T0 - tr(g - 1)] / 2 for direction a.
 template <int Q, typename C>
 __device__ __forceinline__ C rest_poly_c(int a, C gi11, C gi12, C gi22) {
-    const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
-    const C q = c1 * c1 * (gi11 - C(1)) + C(2) * c1 * c2 * gi12 + c2 * c2 * (gi22 - C(1));
-    return C(1) + C(0.5) * (q * C(1.0 / Lat<Q>::T0) - (gi11 - C(1)) - (gi22 - C(1)));
+    const double c1 = c1_of(a), c2 = c2_of(a);
+    KSum<C> q;
+    q.add(gi11 - C(1), c1 * c1);
+    q.add(gi12, 2.0 * c1 * c2);
+    q.add(gi22 - C(1), c2 * c2);
+    return C(1) + C(0.5) * (q.s * C(1.0 / Lat<Q>::T0) - (gi11 - C(1)) - (gi22 - C(1)));
 }
 
 // CellTab: per-cell tables of general grids, one plane of n1 n2 values per
@@ -114,10 +137,15 @@ struct CellTab {
     __device__ __forceinline__ C p0(int q) const { return rest_poly_c<Q, C>(Lat<Q>::plus(q), gi11, gi12, gi22); }
     __device__ __forceinline__ V4<C> pb(int q) const {
         const int a = Lat<Q>::plus(q);
-        const C w = C(Lat<Q>::w(a)), c1 = C(c1_of(a)), c2 = C(c2_of(a));
+        const double w = Lat<Q>::w(a), c1 = c1_of(a), c2 = c2_of(a);
         const V4<C> A = pa(q);
         const C D1 = A.x + A.y, D2 = A.z + A.w;
-        return {C(2) * w * c1 * D1, C(2) * w * c2 * D2, w * (c1 * D2 + c2 * D1), p0(q)};
+        KSum<C> e11, e22, e12;
+        e11.add(D1, 2.0 * w * c1);
+        e22.add(D2, 2.0 * w * c2);
+        e12.add(D2, w * c1);
+        e12.add(D1, w * c2);
+        return {e11.s, e22.s, e12.s, p0(q)};
     }
 };
 
@@ -265,12 +293,20 @@ __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const 
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q);
-        const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
-        O[q] = K11 * c1 + K12 * c2 + K111 * (c1 * c1 * c1) + K112 * (c1 * c1 * c2) +
-               K122 * (c1 * c2 * c2) + K222 * (c2 * c2 * c2);
+        const double c1 = c1_of(a), c2 = c2_of(a);
+        KSum<C> o;
+        o.add(K11, c1);
+        o.add(K12, c2);
+        o.add(K111, c1 * c1 * c1);
+        o.add(K112, c1 * c1 * c2);
+        o.add(K122, c1 * c2 * c2);
+        o.add(K222, c2 * c2 * c2);
+        O[q] = o.s;
+        // the weights vanish exactly with the velocity components they carry
+        // (E11 = 2 w c1 D1, E22 = 2 w c2 D2)
         const V4<C> B = tb.pb(q);
-        S11 += B.x * O[q];
-        S22 += B.y * O[q];
+        if (c1 != 0.0) S11 += B.x * O[q];
+        if (c2 != 0.0) S22 += B.y * O[q];
         S12 += B.z * O[q];
     }
     const C pr = k.pref * c.rho;
@@ -292,9 +328,14 @@ __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const 
 #pragma unroll
     for (int q = 0; q < L::NP; ++q) {
         const int a = L::plus(q), b = opp_of(a);
-        const C c1 = C(c1_of(a)), c2 = C(c2_of(a));
-        const C X = drt * tb.p0(q) + base + Ea * (c1 * c1) + Eb * (c1 * c2) + Ec * (c2 * c2);
-        const C Y = rt * O[q] + Fa * c1 + Fb * c2;
+        const double c1 = c1_of(a), c2 = c2_of(a);
+        KSum<C> x(drt * tb.p0(q) + base), y(rt * O[q]);
+        x.add(Ea, c1 * c1);
+        x.add(Eb, c1 * c2);
+        x.add(Ec, c2 * c2);
+        y.add(Fa, c1);
+        y.add(Fb, c2);
+        const C X = x.s, Y = y.s;
         const C w = C(L::w(a));
         // (N'_a, N'_b) = (d_a, d_b) (1 - 1/tau) + J w (X + Y, X - Y)
         const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(mkp(c.d[a], c.d[b]), omt2));

@@ -352,18 +352,31 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = plus3(p);
-        const C x = C(c1_3(a)), y = C(c2_3(a)), z = C(c3_3(a));
-        const C o = K1 * x + K2 * y + K3 * z + k111 * (x * x * x) + k222 * (y * y * y) + k333 * (z * z * z) +
-                    k112 * (x * x * y) + k113 * (x * x * z) + k122 * (x * y * y) + k133 * (x * z * z) +
-                    k223 * (y * y * z) + k233 * (y * z * z) + k123 * (x * y * z);
+        const double x = c1_3(a), y = c2_3(a), z = c3_3(a);
+        KSum<C> os;
+        os.add(K1, x);
+        os.add(K2, y);
+        os.add(K3, z);
+        os.add(k111, x * x * x);
+        os.add(k222, y * y * y);
+        os.add(k333, z * z * z);
+        os.add(k112, x * x * y);
+        os.add(k113, x * x * z);
+        os.add(k122, x * y * y);
+        os.add(k133, x * z * z);
+        os.add(k223, y * y * z);
+        os.add(k233, y * z * z);
+        os.add(k123, x * y * z);
+        const C o = os.s;
         O[p] = o;
+        // E_kl = w (c^k D^l + c^l D^k) vanishes exactly where c^k = c^l = 0
         const V4<C> e0 = ld4(t + Tab3::E(p)), e1 = ld4(t + Tab3::E(p) + 4);
-        P11 += e0.x * o;
-        P22 += e0.y * o;
-        P33 += e0.z * o;
-        P12 += e0.w * o;
-        P13 += e1.x * o;
-        P23 += e1.y * o;
+        if (x != 0.0) P11 += e0.x * o;
+        if (y != 0.0) P22 += e0.y * o;
+        if (z != 0.0) P33 += e0.z * o;
+        if (x != 0.0 || y != 0.0) P12 += e0.w * o;
+        if (x != 0.0 || z != 0.0) P13 += e1.x * o;
+        if (y != 0.0 || z != 0.0) P23 += e1.y * o;
     }
     const C pr = C(A.pref) * rho;
     P11 *= pr;
@@ -387,12 +400,23 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = plus3(p), b = opp3(a);
-        const C x = C(c1_3(a)), y = C(c2_3(a)), z = C(c3_3(a));
-        const C cu = x * V1 + y * V2 + z * V3;
-        const C cPc = x * x * P11 + y * y * P22 + z * z * P33 + C(2) * (x * y * P12 + x * z * P13 + y * z * P23);
-        const C X = drho * ldt(t + Tab3::P0 + a) * tinv + rho * tinv * (cu * cu) * i2T02 + cPc * (iT0 * iT0) +
-                    base;
-        const C Y = rho * tinv * O[p] + (x * F1 + y * F2 + z * F3) * iT0;
+        const double x = c1_3(a), y = c2_3(a), z = c3_3(a);
+        KSum<C> cu, cPc, cF;
+        cu.add(V1, x);
+        cu.add(V2, y);
+        cu.add(V3, z);
+        cPc.add(P11, x * x);
+        cPc.add(P22, y * y);
+        cPc.add(P33, z * z);
+        cPc.add(P12, 2.0 * x * y);
+        cPc.add(P13, 2.0 * x * z);
+        cPc.add(P23, 2.0 * y * z);
+        cF.add(F1, x);
+        cF.add(F2, y);
+        cF.add(F3, z);
+        const C X = drho * ldt(t + Tab3::P0 + a) * tinv + rho * tinv * (cu.s * cu.s) * i2T02 +
+                    cPc.s * (iT0 * iT0) + base;
+        const C Y = rho * tinv * O[p] + cF.s * iT0;
         const C w = C(w3(a));
         // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
         const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
