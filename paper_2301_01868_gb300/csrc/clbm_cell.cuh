@@ -168,15 +168,19 @@ template <int Q, typename C> struct TabOf<Q, C, true> {
 //   F^k = -1/(2J) sum_b a^k_b [N'_b(q, t-1) + N_{opp b}(q, t)] + rho g^k.
 // ld(alpha, dr, dc) returns the stored value of population alpha at the cell
 // offset by (dr, dc) rows / columns; dr and dc are compile-time after unrolling.
-template <int Q, typename C, typename LD, typename TB>
+// SC: the values ld returns are SC times the deviations (a power of two, so
+// every sum is exactly SC times the unscaled one); c.d and the lagged sums
+// keep the scale, the moments and the force are unscaled.
+template <int Q, typename C, int SC = 1, typename LD, typename TB>
 __device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>& k, Cell<Q, C>& c) {
     using L = Lat<Q>;
     using T = Tab<Q>;
     using P = typename PairOf<C>::T;
     // two-lane sums: lane x collects direction a of each pair, lane y b
-    P sd = mkp(tb.s(T::D0), C(0));
-    P s1 = mkp(tb.s(T::M1), C(0)), s2 = mkp(tb.s(T::M2), C(0));
-    P f1 = mkp(tb.s(T::F01), C(0)), f2 = mkp(tb.s(T::F02), C(0));
+    // the rest parts of the sums (table constants) join at the same scale
+    P sd = mkp(tb.s(T::D0) * C(SC), C(0));
+    P s1 = mkp(tb.s(T::M1) * C(SC), C(0)), s2 = mkp(tb.s(T::M2) * C(SC), C(0));
+    P f1 = mkp(tb.s(T::F01) * C(SC), C(0)), f2 = mkp(tb.s(T::F02) * C(SC), C(0));
     P ls = mkp(C(0), C(0)), ls1 = mkp(C(0), C(0)), ls2 = mkp(C(0), C(0));
     c.d[0] = ld(0, 0, 0);
 #pragma unroll
@@ -199,7 +203,7 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>
         if (c2 != 0) ls2 = pfma(mkp(C(-c2), C(c2)), lg, ls2);
         if (c1 != 0 || TB::ALL_OFFSETS) {
             const V4<C> D = tb.pd(q);
-            const P dd = padd(pp, mkp(D.x, D.y));
+            const P dd = SC == 1 ? padd(pp, mkp(D.x, D.y)) : pfma(mkp(D.x, D.y), mkp(C(SC), C(SC)), pp);
             c.d[a] = dd.x;
             c.d[b] = dd.y;
         } else {
@@ -210,7 +214,7 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>
     c.ls = c.d[0] + (ls.x + ls.y);
     c.ls1 = ls1.x + ls1.y;
     c.ls2 = ls2.x + ls2.y;
-    const C invJ = tb.s(T::INVJ);
+    const C invJ = tb.s(T::INVJ) * C(1.0 / SC);
     c.drho = (c.d[0] + sd.x + sd.y) * invJ;
     c.rho = k.rho0 + c.drho;
     c.irho = C(1) / c.rho;
@@ -258,8 +262,9 @@ __device__ __forceinline__ void force_again(const TB& tb, const C (&out)[Q], con
 
 // Ut (Eq. 18), equilibrium coefficients (Eq. 19), odd parts, the momentum-flux
 // correction (Eq. 16, symmetric part), source (Eq. 17) and BGK (Eqs. 6, 11).
-// emit(alpha, value) receives every new post-collision deviation.
-template <int Q, typename C, typename TB, typename Emit>
+// emit(alpha, value) receives every new post-collision deviation, times SC
+// when pull_cell ran with that scale.
+template <int Q, typename C, int SC = 1, typename TB, typename Emit>
 __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const Consts<C>& k,
                                              Emit&& emit) {
     using L = Lat<Q>;
@@ -314,7 +319,7 @@ __device__ __forceinline__ void collide_emit(const TB& tb, Cell<Q, C>& c, const 
     S22 *= pr;
     S12 *= pr;
     const C trS = S11 + S22;
-    const C J = tb.s(T::J);
+    const C J = tb.s(T::J) * C(SC);
     const C omt = k.omt;
     const C drt = c.drho * k.tau_inv, rt = c.rho * k.tau_inv;
     const C Fa = c.F1 * iT0, Fb = c.F2 * iT0;

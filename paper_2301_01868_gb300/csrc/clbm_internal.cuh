@@ -29,28 +29,39 @@
 
 namespace clbm {
 
-// Storage conversions.  FP16 keeps deviations scaled by 2^12 (out of the
-// subnormal range; scaling by a power of two is exact).  ld reads global
+// Storage conversions.  FP16 keeps deviations scaled by SCALE = 2^12 (out of
+// the subnormal range; scaling by a power of two is exact).  ld reads global
 // memory through the read-only path, lds any address, rt rounds a value the
-// way a store and a load would.
+// way a store and a load would; ldr (global, read-only path) and ldsr (any
+// address) read the stored value as it is (SCALE times the deviation), for
+// an update that carries the scale through its arithmetic instead.
 constexpr float F16_SCALE = 4096.0f;
 template <typename S> struct Store;
 template <> struct Store<double> {
     using C = double;
+    static constexpr int SCALE = 1;
     __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
     __device__ static __forceinline__ double lds(const double* p) { return *p; }
+    __device__ static __forceinline__ double ldsr(const double* p) { return *p; }
+    __device__ static __forceinline__ double ldr(const double* p) { return __ldg(p); }
     __device__ static __forceinline__ void st(double* p, double v) { *p = v; }
     __device__ static __forceinline__ double rt(double v) { return v; }
 };
 template <> struct Store<float> {
     using C = float;
+    static constexpr int SCALE = 1;
     __device__ static __forceinline__ float ld(const float* p) { return __ldg(p); }
     __device__ static __forceinline__ float lds(const float* p) { return *p; }
+    __device__ static __forceinline__ float ldsr(const float* p) { return *p; }
+    __device__ static __forceinline__ float ldr(const float* p) { return __ldg(p); }
     __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
     __device__ static __forceinline__ float rt(float v) { return v; }
 };
 template <> struct Store<__half> {
     using C = float;
+    static constexpr int SCALE = 4096;   // F16_SCALE
+    __device__ static __forceinline__ float ldsr(const __half* p) { return __half2float(*p); }
+    __device__ static __forceinline__ float ldr(const __half* p) { return __half2float(__ldg(p)); }
     __device__ static __forceinline__ float ld(const __half* p) {
         return __half2float(__ldg(p)) * (1.0f / F16_SCALE);
     }
@@ -64,6 +75,9 @@ template <> struct Store<__half> {
 };
 template <> struct Store<__nv_bfloat16> {
     using C = float;
+    static constexpr int SCALE = 1;
+    __device__ static __forceinline__ float ldsr(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ float ldr(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     __device__ static __forceinline__ float lds(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
@@ -80,22 +94,27 @@ __device__ __forceinline__ uint64_t l2_evict_first() {
 }
 template <typename S> struct StHint;
 template <> struct StHint<double> {
+    __device__ static __forceinline__ void str(double* p, double v, uint64_t pol) { st(p, v, pol); }
     __device__ static __forceinline__ void st(double* p, double v, uint64_t pol) {
         asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
     }
 };
 template <> struct StHint<float> {
+    __device__ static __forceinline__ void str(float* p, float v, uint64_t pol) { st(p, v, pol); }
     __device__ static __forceinline__ void st(float* p, float v, uint64_t pol) {
         asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
     }
 };
 template <> struct StHint<__half> {
-    __device__ static __forceinline__ void st(__half* p, float v, uint64_t pol) {
-        const unsigned short b = __half_as_ushort(__float2half_rn(v * F16_SCALE));
+    // str stores a value already scaled by Store<__half>::SCALE
+    __device__ static __forceinline__ void str(__half* p, float v, uint64_t pol) {
+        const unsigned short b = __half_as_ushort(__float2half_rn(v));
         asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(b), "l"(pol) : "memory");
     }
+    __device__ static __forceinline__ void st(__half* p, float v, uint64_t pol) { str(p, v * F16_SCALE, pol); }
 };
 template <> struct StHint<__nv_bfloat16> {
+    __device__ static __forceinline__ void str(__nv_bfloat16* p, float v, uint64_t pol) { st(p, v, pol); }
     __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, uint64_t pol) {
         const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
         asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(b), "l"(pol) : "memory");

@@ -274,12 +274,16 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     const unsigned own = (unsigned)(i - 1 + H) * (unsigned)n23 + (unsigned)jk;
 
     // pull (Eq. 12) with the lagged read, moments (Eqs. 7-10), lagged force
-    // (Eq. 15), two directions a, b = -a at a time in the two lanes of a pair
+    // (Eq. 15), two directions a, b = -a at a time in the two lanes of a pair.
+    // The arithmetic carries the storage scale SC (values as stored, a power
+    // of two: exactly SC times the unscaled sums) up to the moments.
     using P = typename PairOf<C>::T;
+    constexpr int SC = Store<S>::SCALE;
     P dd[NP];
-    const C d0 = Store<S>::ld(src + own);
+    const C d0 = Store<S>::ldr(src + own);
     P sd = mkp(d0, C(0)), s1 = mkp(C(0), C(0)), s2 = s1, s3 = s1;
-    P f1 = mkp(ldt(t + Tab3::F0), C(0)), f2 = mkp(ldt(t + Tab3::F0 + 1), C(0)), f3 = mkp(ldt(t + Tab3::F0 + 2), C(0));
+    P f1 = mkp(ldt(t + Tab3::F0) * C(SC), C(0)), f2 = mkp(ldt(t + Tab3::F0 + 1) * C(SC), C(0)),
+      f3 = mkp(ldt(t + Tab3::F0 + 2) * C(SC), C(0));
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = plus3(p), b = opp3(a);
@@ -287,10 +291,12 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         // N_a from q - c_a, N_b from q + c_a; the lagged values are the cell's own
         const unsigned ia = (unsigned)(i - c1 - 1 + H) * (unsigned)n23 + (unsigned)(jo[c2 + 3] + ko[c3 + 3]);
         const unsigned ib = (unsigned)(i + c1 - 1 + H) * (unsigned)n23 + (unsigned)(jo[3 - c2] + ko[3 - c3]);
-        const P pp = mkp(Store<S>::ld(src + (a * pl + ia)), Store<S>::ld(src + (b * pl + ib)));
-        const P lg = mkp(Store<S>::ld(src + (b * pl + own)), Store<S>::ld(src + (a * pl + own)));
+        const P pp = mkp(Store<S>::ldr(src + (a * pl + ia)), Store<S>::ldr(src + (b * pl + ib)));
+        const P lg = mkp(Store<S>::ldr(src + (b * pl + own)), Store<S>::ldr(src + (a * pl + own)));
         const V4<C> w0 = ld4(t + Tab3::PA(p)), w1 = ld4(t + Tab3::PA(p) + 4);
-        const P d = c1 != 0 ? padd(pp, mkp(w1.z, w1.w)) : pp;
+        const P d = c1 == 0 ? pp
+                    : SC == 1 ? padd(pp, mkp(w1.z, w1.w))
+                              : pfma(mkp(w1.z, w1.w), mkp(C(SC), C(SC)), pp);
         dd[p] = d;
         sd = padd(sd, d);
         if (c1) s1 = pfma(mkp(C(c1), C(-c1)), d, s1);
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         f2 = pfma(mkp(w0.z, w0.w), tt, f2);
         f3 = pfma(mkp(w1.x, w1.y), tt, f3);
     }
-    const C invJ = ldt(t + Tab3::INVJ), J = ldt(t + Tab3::J);
+    const C invJ = ldt(t + Tab3::INVJ) * C(1.0 / SC), J = ldt(t + Tab3::J) * C(SC);
     const C drho = (sd.x + sd.y) * invJ, rho = C(A.rho0) + drho, irho = C(1) / rho;
     const C U1 = (s1.x + s1.y) * invJ * irho, U2 = (s2.x + s2.y) * invJ * irho, U3 = (s3.x + s3.y) * invJ * irho;
     const C F1 = C(-0.5) * invJ * (f1.x + f1.y) + rho * C(A.g1);
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     const C base = C(-0.5) * iT0 * uu * rho * tinv - trP * iT0;
     S* dst = (S*)A.dst + own;
     const uint64_t pol = l2_evict_first();   // read only by the next launch
-    StHint<S>::st(dst, omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base), pol);
+    StHint<S>::str(dst, omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base), pol);
     const P omt2 = mkp(omt, omt), J2 = mkp(J, J);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -420,8 +426,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
         const C w = C(w3(a));
         // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
         const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
-        StHint<S>::st(dst + a * pl, o.x, pol);
-        StHint<S>::st(dst + b * pl, o.y, pol);
+        StHint<S>::str(dst + a * pl, o.x, pol);
+        StHint<S>::str(dst + b * pl, o.y, pol);
     }
     // the moments the walls read next (rows within H of a wall)
     if (i <= H) {

@@ -297,20 +297,22 @@ __device__ __forceinline__ void ws_update_cell_tb(const WsLattice<S>& L, const C
                                                   const TB& tb, int i, int j, int r, int cc, int gcols) {
     using G = TileGeom<Q, S>;
     constexpr int H = Lat<Q>::H;
+    // the cell's arithmetic carries the storage scale (values as stored)
+    constexpr int SC = Store<S>::SCALE;
     Cell<Q, C> c;
-    pull_cell<Q, C>(
+    pull_cell<Q, C, SC>(
         [&](int al, int dr, int dc) -> C {
-            return C(Store<S>::lds(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) + cc +
-                                   G::col0(al) + dc));
+            return C(Store<S>::ldsr(in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) + cc +
+                                    G::col0(al) + dc));
         },
         tb, k, c);
     S* dst = L.dst + (long long)(i + H) * L.ld + j + GC;
     const int dw = wrap_offset(j, L.n2);
     const int pl = (int)L.plane;   // Q planes < 2^31 values (checked at creation)
     const uint64_t pol = l2_evict_first();
-    collide_emit<Q, C>(tb, c, k, [&](int al, C v) {
-        StHint<S>::st(dst + al * pl, v, pol);
-        if (dw != 0) StHint<S>::st(dst + (al * pl + dw), v, pol);
+    collide_emit<Q, C, SC>(tb, c, k, [&](int al, C v) {
+        StHint<S>::str(dst + al * pl, v, pol);
+        if (dw != 0) StHint<S>::str(dst + (al * pl + dw), v, pol);
     });
     if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
         const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
