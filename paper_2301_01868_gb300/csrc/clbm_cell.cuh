@@ -192,8 +192,13 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>
         const P pp = mkp(ld(a, -c1, -c2), ld(b, c1, c2));
         const P lg = mkp(ld(b, 0, 0), ld(a, 0, 0));        // (lagged b, lagged a)
         sd = padd(sd, pp);
-        if (c1 != 0) s1 = pfma(mkp(C(c1), C(-c1)), pp, s1);
-        if (c2 != 0) s2 = pfma(mkp(C(c2), C(-c2)), pp, s2);
+        // momentum: c_b = -c_a, so the pair adds c_a (N_a - N_b); scalar
+        // instructions here leave the FMA pipe's packed slots to the sums above
+        if (c1 != 0 || c2 != 0) {
+            const C df = pp.x - pp.y;
+            if (c1 != 0) s1.x = fma(C(c1), df, s1.x);
+            if (c2 != 0) s2.x = fma(C(c2), df, s2.x);
+        }
         // (N'_b + N_a, N'_a + N_b): the two sums the contractions of a and b weigh
         const P t = padd(lg, pp);
         f1 = pfma(mkp(A.x, A.y), t, f1);

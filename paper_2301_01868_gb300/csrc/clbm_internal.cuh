@@ -84,41 +84,16 @@ template <> struct Store<__nv_bfloat16> {
     __device__ static __forceinline__ float rt(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
-// Stores of the update's output with an L2 evict-first policy: what a
-// launch writes is read only by the next launch, so it gives way first to
-// the rows this launch reads again (the halo rows of the next bands).
-__device__ __forceinline__ uint64_t l2_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-template <typename S> struct StHint;
-template <> struct StHint<double> {
-    __device__ static __forceinline__ void str(double* p, double v, uint64_t pol) { st(p, v, pol); }
-    __device__ static __forceinline__ void st(double* p, double v, uint64_t pol) {
-        asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
-    }
-};
-template <> struct StHint<float> {
-    __device__ static __forceinline__ void str(float* p, float v, uint64_t pol) { st(p, v, pol); }
-    __device__ static __forceinline__ void st(float* p, float v, uint64_t pol) {
-        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
-    }
-};
-template <> struct StHint<__half> {
-    // str stores a value already scaled by Store<__half>::SCALE
-    __device__ static __forceinline__ void str(__half* p, float v, uint64_t pol) {
-        const unsigned short b = __half_as_ushort(__float2half_rn(v));
-        asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(b), "l"(pol) : "memory");
-    }
-    __device__ static __forceinline__ void st(__half* p, float v, uint64_t pol) { str(p, v * F16_SCALE, pol); }
-};
-template <> struct StHint<__nv_bfloat16> {
-    __device__ static __forceinline__ void str(__nv_bfloat16* p, float v, uint64_t pol) { st(p, v, pol); }
-    __device__ static __forceinline__ void st(__nv_bfloat16* p, float v, uint64_t pol) {
-        const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-        asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(b), "l"(pol) : "memory");
-    }
+// Stores of the update's output with the streaming cache hint (st.global.cs:
+// evict-first): what a launch writes is read only by the next launch, so it
+// gives way first to the rows this launch reads again (the halo rows of the
+// next bands).  str stores a value already in the storage scale
+// (Store<S>::SCALE times the deviation), st a deviation.
+template <typename S>
+struct StStream {
+    using C = typename Store<S>::C;
+    __device__ static __forceinline__ void str(S* p, C v) { __stcs(p, S(v)); }
+    __device__ static __forceinline__ void st(S* p, C v) { str(p, v * C(Store<S>::SCALE)); }
 };
 
 constexpr int GC = 8;  // ghost columns on each side (>= widest |c^2| = 3; 16-byte TMA origins)

@@ -400,34 +400,35 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
     const C uu = V1 * V1 + V2 * V2 + V3 * V3;
     const C base = C(-0.5) * iT0 * uu * rho * tinv - trP * iT0;
     S* dst = (S*)A.dst + own;
-    const uint64_t pol = l2_evict_first();   // read only by the next launch
-    StHint<S>::str(dst, omt * d0 + J * C(w3(0)) * (drho * ldt(t + Tab3::P0) * tinv + base), pol);
+    // the even part of the bracket is quadratic in c: c.M.c with
+    // M = rho (Ut Ut) / (2 T0^2 tau) + dPi / T0^2, formed once per cell
+    const C P0 = ldt(t + Tab3::P0);
+    const C drt = drho * tinv, rt = rho * tinv, A1 = rt * i2T02, iT02 = iT0 * iT0;
+    const C M11 = A1 * V1 * V1 + P11 * iT02, M22 = A1 * V2 * V2 + P22 * iT02, M33 = A1 * V3 * V3 + P33 * iT02;
+    const C M12 = A1 * V1 * V2 + P12 * iT02, M13 = A1 * V1 * V3 + P13 * iT02, M23 = A1 * V2 * V3 + P23 * iT02;
+    const C Fa = F1 * iT0, Fb = F2 * iT0, Fc = F3 * iT0;
+    StStream<S>::str(dst, omt * d0 + J * C(w3(0)) * (drt * P0 + base));   // read only by the next launch
     const P omt2 = mkp(omt, omt), J2 = mkp(J, J);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = plus3(p), b = opp3(a);
         const double x = c1_3(a), y = c2_3(a), z = c3_3(a);
-        KSum<C> cu, cPc, cF;
-        cu.add(V1, x);
-        cu.add(V2, y);
-        cu.add(V3, z);
-        cPc.add(P11, x * x);
-        cPc.add(P22, y * y);
-        cPc.add(P33, z * z);
-        cPc.add(P12, 2.0 * x * y);
-        cPc.add(P13, 2.0 * x * z);
-        cPc.add(P23, 2.0 * y * z);
-        cF.add(F1, x);
-        cF.add(F2, y);
-        cF.add(F3, z);
-        const C X = drho * ldt(t + Tab3::P0 + a) * tinv + rho * tinv * (cu.s * cu.s) * i2T02 +
-                    cPc.s * (iT0 * iT0) + base;
-        const C Y = rho * tinv * O[p] + cF.s * iT0;
+        KSum<C> xs(drt * ldt(t + Tab3::P0 + a) + base), ys(rt * O[p]);
+        xs.add(M11, x * x);
+        xs.add(M22, y * y);
+        xs.add(M33, z * z);
+        xs.add(M12, 2.0 * x * y);
+        xs.add(M13, 2.0 * x * z);
+        xs.add(M23, 2.0 * y * z);
+        ys.add(Fa, x);
+        ys.add(Fb, y);
+        ys.add(Fc, z);
+        const C X = xs.s, Y = ys.s;
         const C w = C(w3(a));
         // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
         const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
-        StHint<S>::str(dst + a * pl, o.x, pol);
-        StHint<S>::str(dst + b * pl, o.y, pol);
+        StStream<S>::str(dst + a * pl, o.x);
+        StStream<S>::str(dst + b * pl, o.y);
     }
     // the moments the walls read next (rows within H of a wall)
     if (i <= H) {

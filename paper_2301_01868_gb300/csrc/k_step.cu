@@ -34,10 +34,9 @@ __global__ void __launch_bounds__(128, ITER ? 2 : (GEN ? 3 : 4)) k_fused_step(co
     pull_cell<Q, C>(GlobalLoad<S>{(const S*)a.src + off, pl, a.ld}, tb, k, c);
     S* dst = (S*)a.dst + off;
     const int dw = wrap_offset(j, a.n2);
-    const uint64_t pol = l2_evict_first();
     auto put = [&](int al, C v) {
-        StHint<S>::st(dst + al * pl, v, pol);
-        if (dw != 0) StHint<S>::st(dst + (al * pl + dw), v, pol);
+        StStream<S>::st(dst + al * pl, v);
+        if (dw != 0) StStream<S>::st(dst + (al * pl + dw), v);
     };
     if (!ITER) {
         collide_emit<Q, C>(tb, c, k, put);

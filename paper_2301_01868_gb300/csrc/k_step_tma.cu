@@ -309,10 +309,9 @@ __device__ __forceinline__ void ws_update_cell_tb(const WsLattice<S>& L, const C
     S* dst = L.dst + (long long)(i + H) * L.ld + j + GC;
     const int dw = wrap_offset(j, L.n2);
     const int pl = (int)L.plane;   // Q planes < 2^31 values (checked at creation)
-    const uint64_t pol = l2_evict_first();
     collide_emit<Q, C, SC>(tb, c, k, [&](int al, C v) {
-        StHint<S>::str(dst + al * pl, v, pol);
-        if (dw != 0) StHint<S>::str(dst + (al * pl + dw), v, pol);
+        StStream<S>::str(dst + al * pl, v);
+        if (dw != 0) StStream<S>::str(dst + (al * pl + dw), v);
     });
     if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
         const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
