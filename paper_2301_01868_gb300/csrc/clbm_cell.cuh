@@ -192,9 +192,15 @@ __device__ __forceinline__ void pull_cell(LD&& ld, const TB& tb, const Consts<C>
         const P pp = mkp(ld(a, -c1, -c2), ld(b, c1, c2));
         const P lg = mkp(ld(b, 0, 0), ld(a, 0, 0));        // (lagged b, lagged a)
         sd = padd(sd, pp);
-        // momentum: c_b = -c_a, so the pair adds c_a (N_a - N_b); scalar
-        // instructions here leave the FMA pipe's packed slots to the sums above
-        if (c1 != 0 || c2 != 0) {
+        // momentum: c_b = -c_a, so the pair adds c_a (N_a - N_b).  With row
+        // tables (the pipelined update, FMA-pipe bound) the scalar form is
+        // faster: fewer lane operations than the packed one with its
+        // constant pairs; with per-cell tables (general grids, bound by the
+        // table loads) the packed form measured faster
+        if (TB::ALL_OFFSETS) {
+            if (c1 != 0) s1 = pfma(mkp(C(c1), C(-c1)), pp, s1);
+            if (c2 != 0) s2 = pfma(mkp(C(c2), C(-c2)), pp, s2);
+        } else if (c1 != 0 || c2 != 0) {
             const C df = pp.x - pp.y;
             if (c1 != 0) s1.x = fma(C(c1), df, s1.x);
             if (c2 != 0) s2.x = fma(C(c2), df, s2.x);

@@ -245,9 +245,11 @@ __device__ __forceinline__ C ldt(const C* p) { return *p; }
 
 // One cell (i, j, k) of the update; MOM: write rho and Ut instead.  A block
 // covers 128 cells of one row, so the row's table is staged in shared
-// memory once per block and every coefficient is a shared-memory read.
+// memory once per block and every coefficient is a shared-memory read.  Six
+// blocks per SM (FP32 compute: 80 registers, a few bytes spilled) measured
+// 8 % faster than four (128 registers, no spills); seven and eight spill more.
 template <typename S, typename C, bool MOM>
-__global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 6 : 2)
     k3_step(Args3 A, double* __restrict__ mrho, double* __restrict__ mut) {
     __shared__ __align__(16) C ts[Tab3::S];
     const int n23 = A.n2 * A.n3;
