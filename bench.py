@@ -277,6 +277,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(GENERAL_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-inputs", choices=("state", "state_serial", "fields"), default="state",
+                    help="what the e2e leg uploads each step: the FP64 state with the copies overlapping "
+                         "the previous step (default), the same copies in series, or the macroscopic fields")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one thread per cell, 2 TMA-staged tiles, "
                          "3 TMA-staged warp-specialised pipeline")
@@ -340,7 +343,9 @@ def main():
         bench_step()
     clocks = Clocks(smi_index(local))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g.set_profiling(True, period=10)   # every 10th launch: the events cost ~2 us each
+    # graph replays of 10 back-to-back update launches are timed as a whole
+    # (plain launches: every 10th, the events cost ~2 us each)
+    g.set_profiling(True, period=10)
     launches0 = g.launch_count()
     barrier()
     clocks.start()
@@ -372,7 +377,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(g, args, torch, stream, world, dist, cells, Q, "state")
+        e2e = run_e2e(g, args, torch, stream, world, dist, cells, Q, args.e2e_inputs)
 
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -584,50 +589,95 @@ def run_e2e(g, args, torch, stream, world, dist, cells, Q, inputs="state"):
     """Same metric through the public API with host buffers.  Every step
     uploads that step's inputs from pinned host memory, advances `chunk` time
     steps and reads the moments rho, Ut^1, Ut^2 back into pinned host memory.
-    inputs "state": the full FP64 N' (clbm_set_state, Q values per cell);
+    inputs "state" (the default): the full FP64 N' (clbm_set_state, Q values
+    per cell), pipelined -- a copy stream uploads step k+1's input into a
+    second device buffer and downloads step k-1's moments while step k
+    computes, so each step's copies stay inside the timed region but overlap
+    the update; "state_serial": the same copies one after another with the
+    compute (host buffers passed to clbm_set_state / clbm_moments);
     "fields": the macroscopic start rho, U^1, U^2 (clbm_set_equilibrium, 3
     FP64 values per cell; fewer bytes, but the FP64 equilibrium on the device
-    costs more than the saved transfer: 21,061 against 25,403 MLUPS on the
-    1024 x 4096 annulus)."""
+    costs more than the saved transfer: 21,061 against 25,403 MLUPS serially
+    on the 1024 x 4096 annulus)."""
     n1, n2 = g.n1, g.n2
     names = ("rho", "Ut1", "Ut2")
-    pinned = {k: torch.empty((n1, n2), dtype=torch.float64, pin_memory=True).numpy() for k in names}
     if inputs == "state":
         host_state = torch.empty((Q, n1, n2), dtype=torch.float64, pin_memory=True)
         host_state.copy_(g.state(device=True).cpu())
-        state_np = host_state.numpy()
+        dev_in = [torch.empty((Q, n1, n2), dtype=torch.float64, device=g.device) for _ in range(2)]
+        dev_out = [{k: torch.empty((n1, n2), dtype=torch.float64, device=g.device) for k in names}
+                   for _ in range(2)]
+        host_out = [{k: torch.empty((n1, n2), dtype=torch.float64, pin_memory=True) for k in names}
+                    for _ in range(2)]
+        cs = torch.cuda.Stream(device=g.device)
+        up_ev = [torch.cuda.Event() for _ in range(2)]
+        dl_ev = [torch.cuda.Event() for _ in range(2)]
+        dl_pending = [False, False]
 
-        def upload():
-            g.set_state(state_np)
+        def upload(k):
+            with torch.cuda.stream(cs):
+                dev_in[k % 2].copy_(host_state, non_blocking=True)
+                up_ev[k % 2].record(cs)
+
+        def run(nsteps):
+            upload(0)
+            for k in range(nsteps):
+                b = k % 2
+                stream.wait_event(up_ev[b])
+                g.set_state(dev_in[b])                  # converts on the grid's stream; synchronises it
+                if k + 1 < nsteps:
+                    upload(k + 1)                       # overlaps this step's update
+                g.step(args.chunk)
+                if dl_pending[b]:
+                    stream.wait_event(dl_ev[b])         # step k-2's download has read this buffer
+                g.moments(device=True, names=names, out=dev_out[b])   # synchronises the grid's stream
+                with torch.cuda.stream(cs):
+                    for nm in names:
+                        host_out[b][nm].copy_(dev_out[b][nm], non_blocking=True)
+                    dl_ev[b].record(cs)
+                dl_pending[b] = True
+            cs.synchronize()
         h2d = Q * cells * 8
     else:
-        m = g.moments(names=("rho", "U1", "U2"))
-        fields = []
-        for k in ("rho", "U1", "U2"):
-            f = torch.empty((n1, n2), dtype=torch.float64, pin_memory=True).numpy()
-            f[...] = m[k]
-            fields.append(f)
+        pinned = {k: torch.empty((n1, n2), dtype=torch.float64, pin_memory=True).numpy() for k in names}
+        if inputs == "state_serial":
+            host_state = torch.empty((Q, n1, n2), dtype=torch.float64, pin_memory=True)
+            host_state.copy_(g.state(device=True).cpu())
+            state_np = host_state.numpy()
 
-        def upload():
-            g.set_equilibrium(*fields)
-        h2d = 3 * cells * 8
+            def upload():
+                g.set_state(state_np)
+            h2d = Q * cells * 8
+        else:
+            m = g.moments(names=("rho", "U1", "U2"))
+            fields = []
+            for k in ("rho", "U1", "U2"):
+                f = torch.empty((n1, n2), dtype=torch.float64, pin_memory=True).numpy()
+                f[...] = m[k]
+                fields.append(f)
 
-    def one():
-        upload()
-        g.step(args.chunk)
-        return g.moments(names=names, out=pinned)
+            def upload():
+                g.set_equilibrium(*fields)
+            h2d = 3 * cells * 8
 
-    one()
+        def run(nsteps):
+            for _ in range(nsteps):
+                upload()
+                g.step(args.chunk)
+                g.moments(names=names, out=pinned)
+
+    run(1)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        one()
+    run(args.steps)
     torch.cuda.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-    what = ("macroscopic start (FP64 rho, U^1, U^2 through clbm_set_equilibrium)" if inputs == "fields"
-            else "state upload (FP64 N' through clbm_set_state)")
+    what = {"state": "state upload (FP64 N' through clbm_set_state from a device buffer that a copy stream "
+                     "fills from pinned host memory while the previous step computes)",
+            "state_serial": "state upload (FP64 N' from pinned host memory through clbm_set_state)",
+            "fields": "macroscopic start (FP64 rho, U^1, U^2 through clbm_set_equilibrium)"}[inputs]
     return {"value": cells * args.chunk * args.steps * world / dt / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 3 * cells * 8,
             "note": "per step: %s, %d time steps, moments download (FP64 rho, Ut^1, Ut^2)"

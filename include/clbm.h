@@ -146,7 +146,11 @@ clbm_status clbm_get_state(clbm_handle h, double* Np, int dst_is_device);
 /* Advance n time steps: one launch of the fused stream-collide-force update
  * per step, which also writes the ghost rows (App. B) and periodic ghost
  * columns of the buffer it fills; the ghosts are rebuilt once first when the
- * state or case was set since.  Asynchronous on the grid's stream. */
+ * state or case was set since.  Asynchronous on the grid's stream.  Runs of
+ * more than 21 steps replay a CUDA graph of 10 launches (captured on first
+ * use and again whenever the case, kernel or buffers it was captured with
+ * change; the same launches, so the results are identical bit for bit);
+ * if a capture fails the grid keeps to plain launches. */
 clbm_status clbm_step(clbm_handle h, long long n);
 
 /* Moments of the current state, i.e. of the post-advection populations
@@ -186,7 +190,9 @@ clbm_status clbm_set_stream(clbm_handle h, void* stream);
 
 /* period > 0: clbm_step records a CUDA event pair around every period-th
  * launch of the fused update (1: every launch; a larger period keeps the
- * events' own cost out of the timed stream); period 0 switches it off.
+ * events' own cost out of the timed stream); a graph replay is recorded as a
+ * whole, one pair around its 10 back-to-back launches, whatever the period;
+ * period 0 switches it off.
  * clbm_kernel_time returns the recorded launches' summed duration (ms) and
  * their count since the last reset, and resets.  Synchronises. */
 clbm_status clbm_set_profiling(clbm_handle h, int period);

@@ -75,6 +75,7 @@ struct clbm_grid {
     long long prof_count;   // update launches since profiling was switched on
     std::vector<cudaEvent_t> ev;
     size_t ev_used;
+    long long ev_launches;  // update launches the recorded event pairs span
     std::vector<double> edges;
     double step2;
     double* stage;          // lazily allocated FP64 staging buffer for host transfers
@@ -86,6 +87,16 @@ struct clbm_grid {
     int nsm;                // SM count of the device
     int variant;            // 0 auto, 1 per-cell loads, 2 TMA-staged tiles
     int* err;               // device error word of bounded waits
+    // CUDA graph of GRAPH_STEPS update launches (an even count, so the two
+    // state buffers end where they started), replayed by clbm_step; the key
+    // is what the launches take, and a change of it rebuilds the graph
+    cudaGraph_t graph;       // kept while gexec lives: its nodes address gexec's
+    cudaGraphExec_t gexec;
+    cudaGraphNode_t gev[2];  // event-record nodes before the first and after the last launch
+    cudaEvent_t gdummy[2];   // their events while profiling is off
+    StepArgs gargs;          // arguments of the first captured launch
+    int gpath[4];            // use_tma, general, variant, nsm at capture
+    bool graphs_off;         // capture failed once: plain launches from then on
 };
 
 namespace {
@@ -156,7 +167,7 @@ StepScalars scalars(const clbm_case& c) {
 }
 
 StepArgs step_args(const clbm_grid* g, const void* src, void* dst) {
-    StepArgs a;
+    StepArgs a{};   // zeroed padding: graph keys compare these bytes
     a.k = scalars(g->cs);
     a.src = src;
     a.dst = dst;
@@ -588,6 +599,160 @@ clbm_status clbm_get_state(clbm_handle g, double* Np, int dst_is_device) {
     return CLBM_OK;
 }
 
+// One launch of the fused update from stA into stB (no bookkeeping).
+static clbm_status launch_update(clbm_grid* g, const StepArgs& a) {
+    if (use_tma(g)) {
+        const int src = a.src == g->phys[0] ? 0 : 1;
+        const int rc = general_grid(g)
+                           ? launch_step_tma_general(g->Q, g->prec, *g->tma, a, src, g->nsm, g->stream)
+                           : launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->variant != 2, g->stream);
+        if (rc != 0) return fail(CLBM_ECUDA, "TMA-staged update could not be launched");
+    } else {
+        launch_step(g->Q, g->prec, a, g->stream);
+    }
+    return CLBM_OK;
+}
+
+// One time step with plain launches (and the sampled profiling events).
+static clbm_status step_plain(clbm_grid* g) {
+    const StepArgs a = step_args(g, g->stA, g->stB);
+    const bool timed = g->profiling && g->prof_count++ % g->prof_period == 0;
+    if (timed) {
+        if (g->ev_used + 2 > g->ev.size()) {
+            for (int k = 0; k < 256; ++k) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                g->ev.push_back(e);
+            }
+        }
+        CK(cudaEventRecord(g->ev[g->ev_used], g->stream));
+    }
+    const clbm_status st = launch_update(g, a);
+    if (st != CLBM_OK) return st;
+    if (timed) {
+        CK(cudaEventRecord(g->ev[g->ev_used + 1], g->stream));
+        g->ev_used += 2;
+        g->ev_launches += 1;
+    }
+    g->launches += 1;
+    std::swap(g->stA, g->stB);
+    g->t++;
+    return CLBM_OK;
+}
+
+constexpr int GRAPH_STEPS = 10;
+
+// Capture GRAPH_STEPS launches from the current stA into a graph; false (and
+// plain launches from then on) if the capture or the instantiation fails.
+static bool capture_graph(clbm_grid* g) {
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->gexec = nullptr;
+    g->graph = nullptr;
+    // (the legacy default stream cannot be captured: such grids keep to
+    // plain launches)
+    if ((!g->gdummy[0] && (cudaEventCreate(&g->gdummy[0]) != cudaSuccess ||
+                           cudaEventCreate(&g->gdummy[1]) != cudaSuccess)) ||
+        cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        g->graphs_off = true;
+        return false;
+    }
+    cudaGraph_t graph = nullptr;
+    void* a = g->stA;
+    void* b = g->stB;
+    bool ok = true;
+    ok = cudaEventRecordWithFlags(g->gdummy[0], g->stream, cudaEventRecordExternal) == cudaSuccess;
+    for (int k = 0; k < GRAPH_STEPS && ok; ++k) {
+        ok = launch_update(g, step_args(g, a, b)) == CLBM_OK;
+        std::swap(a, b);
+    }
+    if (ok) ok = cudaEventRecordWithFlags(g->gdummy[1], g->stream, cudaEventRecordExternal) == cudaSuccess;
+    const bool ended = cudaStreamEndCapture(g->stream, &graph) == cudaSuccess;
+    ok = ok && ended && graph;
+    if (ok) {
+        // the two event-record nodes, to be pointed at the profiling events
+        size_t nn = 0;
+        ok = cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess;
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (ok) ok = cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess;
+        g->gev[0] = g->gev[1] = nullptr;
+        for (size_t k = 0; ok && k < nn; ++k) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nodes[k], &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t e;
+            if (cudaGraphEventRecordNodeGetEvent(nodes[k], &e) != cudaSuccess) continue;
+            if (e == g->gdummy[0]) g->gev[0] = nodes[k];
+            if (e == g->gdummy[1]) g->gev[1] = nodes[k];
+        }
+        ok = ok && g->gev[0] && g->gev[1] &&
+             cudaGraphInstantiate(&g->gexec, graph, 0) == cudaSuccess;
+    }
+    cudaGetLastError();   // a failed capture leaves its error behind; plain launches report their own
+    if (!ok) {
+        if (g->gexec) cudaGraphExecDestroy(g->gexec);
+        if (graph) cudaGraphDestroy(graph);
+        g->gexec = nullptr;
+        g->graphs_off = true;
+        return false;
+    }
+    g->graph = graph;
+    g->gargs = step_args(g, g->stA, g->stB);
+    g->gpath[0] = use_tma(g);
+    g->gpath[1] = general_grid(g);
+    g->gpath[2] = g->variant;
+    g->gpath[3] = g->nsm;
+    return true;
+}
+
+// Whether the graph replays exactly what plain launches from stA would do.
+static bool graph_matches(const clbm_grid* g) {
+    if (!g->gexec) return false;
+    const StepArgs a = step_args(g, g->stA, g->stB);
+    return memcmp(&a, &g->gargs, sizeof a) == 0 && g->gpath[0] == (int)use_tma(g) &&
+           g->gpath[1] == (int)general_grid(g) && g->gpath[2] == g->variant && g->gpath[3] == g->nsm;
+}
+
+// One replay of the graph: GRAPH_STEPS time steps.
+static clbm_status step_graph(clbm_grid* g) {
+    cudaEvent_t e0 = g->gdummy[0], e1 = g->gdummy[1];
+    if (g->profiling) {
+        // a replay is timed as a whole: its GRAPH_STEPS back-to-back launches
+        if (g->ev_used + 2 > g->ev.size()) {
+            for (int k = 0; k < 256; ++k) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                g->ev.push_back(e);
+            }
+        }
+        e0 = g->ev[g->ev_used];
+        e1 = g->ev[g->ev_used + 1];
+        g->ev_used += 2;
+        g->ev_launches += GRAPH_STEPS;
+        g->prof_count += GRAPH_STEPS;
+    }
+    if (cudaGraphExecEventRecordNodeSetEvent(g->gexec, g->gev[0], e0) != cudaSuccess ||
+        cudaGraphExecEventRecordNodeSetEvent(g->gexec, g->gev[1], e1) != cudaSuccess) {
+        // not expected; keep to plain launches rather than fail the step
+        cudaGetLastError();
+        if (g->profiling) {
+            g->ev_used -= 2;
+            g->ev_launches -= GRAPH_STEPS;
+            g->prof_count -= GRAPH_STEPS;
+        }
+        g->graphs_off = true;
+        for (int k = 0; k < GRAPH_STEPS; ++k) {
+            const clbm_status st = step_plain(g);
+            if (st != CLBM_OK) return st;
+        }
+        return CLBM_OK;
+    }
+    CK(cudaGraphLaunch(g->gexec, g->stream));
+    g->launches += GRAPH_STEPS;
+    g->t += GRAPH_STEPS;
+    return CLBM_OK;
+}
+
 clbm_status clbm_step(clbm_handle g, long long n) {
     Range nvtx_range("clbm_step");
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
@@ -596,38 +761,33 @@ clbm_status clbm_step(clbm_handle g, long long n) {
     clbm_status st = select(g);
     if (st != CLBM_OK) return st;
     fill_ghosts(g);
-    for (long long s = 0; s < n; ++s) {
-        StepArgs a = step_args(g, g->stA, g->stB);
-        const bool timed = g->profiling && g->prof_count++ % g->prof_period == 0;
-        if (timed) {
-            if (g->ev_used + 2 > g->ev.size()) {
-                for (int k = 0; k < 256; ++k) {
-                    cudaEvent_t e;
-                    CK(cudaEventCreate(&e));
-                    g->ev.push_back(e);
-                }
+    long long s = 0;
+    // long runs replay a captured graph of GRAPH_STEPS launches: one host call
+    // per replay instead of one per launch, so the device never waits on the
+    // host.  Before a capture two plain launches set the kernels up
+    // (attributes) and bring the buffers back to the parity they started
+    // from, so that runs of an even number of steps replay from their start
+    if (!g->graphs_off && n >= 2 * GRAPH_STEPS + 2) {
+        if (!graph_matches(g)) {
+            std::swap(g->stA, g->stB);   // the graph as seen from the other parity
+            const bool other = graph_matches(g);
+            std::swap(g->stA, g->stB);
+            for (const long long k = other ? 1 : 2; s < k; ++s) {
+                st = step_plain(g);
+                if (st != CLBM_OK) return st;
             }
-            CK(cudaEventRecord(g->ev[g->ev_used], g->stream));
+            if (!other) capture_graph(g);
         }
-        if (use_tma(g)) {
-            const int src = g->stA == g->phys[0] ? 0 : 1;
-            const int rc = general_grid(g)
-                               ? launch_step_tma_general(g->Q, g->prec, *g->tma, a, src, g->nsm, g->stream)
-                               : launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->variant != 2,
-                                                 g->stream);
-            if (rc != 0) return fail(CLBM_ECUDA, "TMA-staged update could not be launched");
-        } else {
-            launch_step(g->Q, g->prec, a, g->stream);
+        if (graph_matches(g)) {
+            for (; n - s >= GRAPH_STEPS; s += GRAPH_STEPS) {
+                st = step_graph(g);
+                if (st != CLBM_OK) return st;
+            }
         }
-        if (timed) {
-            CK(cudaEventRecord(g->ev[g->ev_used + 1], g->stream));
-            g->ev_used += 2;
-        }
-        g->launches += 1;
-        void* t = g->stA;
-        g->stA = g->stB;
-        g->stB = t;
-        g->t++;
+    }
+    for (; s < n; ++s) {
+        st = step_plain(g);
+        if (st != CLBM_OK) return st;
     }
     CK(cudaGetLastError());
     return CLBM_OK;
@@ -809,6 +969,7 @@ clbm_status clbm_set_profiling(clbm_handle g, int period) {
     g->prof_period = period > 0 ? period : 1;
     g->prof_count = 0;
     g->ev_used = 0;
+    g->ev_launches = 0;
     return CLBM_OK;
 }
 
@@ -824,8 +985,9 @@ clbm_status clbm_kernel_time(clbm_handle g, double* ms, long long* launches) {
         tot += x;
     }
     *ms = tot;
-    *launches = (long long)(g->ev_used / 2);
+    *launches = g->ev_launches;
     g->ev_used = 0;
+    g->ev_launches = 0;
     return CLBM_OK;
 }
 
@@ -954,6 +1116,10 @@ clbm_status clbm_destroy(clbm_handle g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (cudaEvent_t e : g->gdummy)
+        if (e) cudaEventDestroy(e);
     if (g->stage) cudaFree(g->stage);
     if (g->tma) free_tma_maps(g->tma);
     if (g->owns_ws) cudaFree(g->ws);
