@@ -98,7 +98,9 @@ clbm_status clbm3_restore(clbm3_handle h, const void* buf);
 /* Advance n >= 0 time steps (Sec. 2: advection Eq. 12, moments Eqs. 7-10,
  * lagged force Eq. 15, Ut Eq. 18, f^eq Eq. 19, dPi Eq. 16, dN Eq. 17, BGK
  * Eqs. 6, 11; App. B walls): two launches per step (ghost rows, update),
- * asynchronous on the grid's stream. */
+ * asynchronous on the grid's stream.  Runs of more than 21 steps replay a
+ * CUDA graph of 10 steps (rebuilt when the case changes; bitwise the plain
+ * launches; plain launches on a stream that cannot be captured). */
 clbm_status clbm3_step(clbm3_handle h, long long n);
 
 /* rho and Ut^k of the collision the next step makes (Ut: [3][n1][n2][n3]);

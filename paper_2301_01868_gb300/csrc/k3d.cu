@@ -587,6 +587,13 @@ struct clbm3_grid {
     bool have_case;
     long long t;
     std::vector<double> hedges;
+    // CUDA graph of GRAPH3_STEPS time steps (ghost rows + update each; an
+    // even count, so cur ends where it started), keyed by the launch
+    // arguments of its first step
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    Args3 gargs;
+    bool graphs_off;         // capture failed once (e.g. the legacy default stream)
 };
 
 namespace k3api {
@@ -669,6 +676,58 @@ void launch_cells(const clbm3_grid* g, const Args3& A, double* rho, double* ut) 
         using S = typename decltype(tag)::type;
         k3_step<S, typename Store<S>::C, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
     });
+}
+
+constexpr int GRAPH3_STEPS = 10;
+
+// One time step with plain launches.
+void step3_plain(clbm3_grid* g) {
+    const Args3 A = args(g);
+    launch_boundary(g, A);
+    launch_cells<false>(g, A, nullptr, nullptr);
+    g->cur ^= 1;
+    g->t++;
+}
+
+// Whether the graph replays what plain launches from the current buffer do.
+bool graph3_matches(const clbm3_grid* g) {
+    if (!g->gexec) return false;
+    const Args3 A = args(g);
+    return memcmp(&A, &g->gargs, sizeof A) == 0;
+}
+
+// Capture GRAPH3_STEPS steps from the current buffer; on failure the grid
+// keeps to plain launches.
+void capture3(clbm3_grid* g) {
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->gexec = nullptr;
+    g->graph = nullptr;
+    if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        g->graphs_off = true;
+        return;
+    }
+    const Args3 first = args(g);
+    for (int k = 0; k < GRAPH3_STEPS; ++k) {
+        const Args3 A = args(g);
+        launch_boundary(g, A);
+        launch_cells<false>(g, A, nullptr, nullptr);
+        g->cur ^= 1;
+    }
+    cudaGraph_t graph = nullptr;
+    const bool ok = cudaStreamEndCapture(g->stream, &graph) == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&g->gexec, graph, 0) == cudaSuccess;
+    cudaGetLastError();
+    if (!ok) {
+        if (g->gexec) cudaGraphExecDestroy(g->gexec);
+        if (graph) cudaGraphDestroy(graph);
+        g->gexec = nullptr;
+        g->graphs_off = true;
+        return;
+    }
+    g->graph = graph;
+    g->gargs = first;
 }
 
 clbm_status staging(clbm3_grid* g, double** out) {
@@ -952,13 +1011,25 @@ clbm_status clbm3_step(clbm3_handle g, long long n) {
     if (n < 0) return fail3(CLBM_EINVAL, "n < 0");
     if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
     CK3(cudaSetDevice(g->device));
-    for (long long s = 0; s < n; ++s) {
-        const Args3 A = args(g);
-        launch_boundary(g, A);
-        launch_cells<false>(g, A, nullptr, nullptr);
-        g->cur ^= 1;
-        g->t++;
+    long long s = 0;
+    // long runs replay a captured graph (one host call per GRAPH3_STEPS
+    // steps); two plain steps first set the kernels up and bring cur back
+    if (!g->graphs_off && n >= 2 * GRAPH3_STEPS + 2) {
+        if (!graph3_matches(g)) {
+            g->cur ^= 1;
+            const bool other = graph3_matches(g);
+            g->cur ^= 1;
+            for (const long long k = other ? 1 : 2; s < k; ++s) step3_plain(g);
+            if (!other) capture3(g);
+        }
+        if (graph3_matches(g)) {
+            for (; n - s >= GRAPH3_STEPS; s += GRAPH3_STEPS) {
+                CK3(cudaGraphLaunch(g->gexec, g->stream));
+                g->t += GRAPH3_STEPS;
+            }
+        }
     }
+    for (; s < n; ++s) step3_plain(g);
     CK3(cudaGetLastError());
     return CLBM_OK;
 }
@@ -1021,6 +1092,9 @@ clbm_status clbm3_time(clbm3_handle g, long long* t) {
 clbm_status clbm3_destroy(clbm3_handle g) {
     if (!g) return CLBM_OK;
     cudaSetDevice(g->device);
+    cudaStreamSynchronize(g->stream);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
     cudaFree(g->edges);
     cudaFree(g->geo);
     cudaFree(g->tab);

@@ -75,3 +75,31 @@ def test_profiling_samples_graph_replays():
     assert n == 100 and ms > 0.0     # ten replays of ten launches each
     g.set_profiling(False)
     g.close()
+
+
+def test_3d_graph_replay_is_bitwise_the_plain_launches():
+    from paper_2301_01868_gb300 import clbm
+    e = I.polar_edges(1.0, 2.0, 8, 0.35)
+    grids = []
+    for _ in range(2):
+        g = clbm.Grid3(8, 50, 4, e, kind=clbm.ANNULUS3, step3=0.15, precision="fp32", bc_lo=clbm.MOVING,
+                       bc_hi=clbm.NOSLIP, stream=torch.cuda.Stream())
+        g.set_case(0.8, 1.0, 0.03, 0.0, (0.0, 0.0, 1e-6))
+        grids.append(g)
+    a, b = grids
+    for n in (50, 23, 41):
+        for _ in range(n):
+            a.step(1)
+        b.step(n)
+        sa = a.state()
+        assert np.isfinite(sa).all()
+        assert np.array_equal(sa, b.state()), n
+    for g in (a, b):
+        g.set_case(0.9, 1.0, 0.01, 0.0)
+    for _ in range(30):
+        a.step(1)
+    b.step(30)
+    assert np.array_equal(a.state(), b.state())
+    assert a.t == b.t
+    a.close()
+    b.close()
