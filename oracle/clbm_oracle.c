@@ -608,6 +608,47 @@ void orc_totals(const orc_grid* g, double* out) {
     out[2] = p2;
 }
 
+/* Sec. 3.1 diagnostics from given moment fields.  The tangent vectors and the
+ * position of a planar or polar cell are those of column 1 (R22): a polar
+ * cell at column j is the column-1 cell turned about the origin, and |u| and
+ * (x cross u).z do not change under a rotation of both x and u. */
+void orc_flow_diagnostics(const orc_grid* g, const double* rho, const double* Ut1,
+                          const double* Ut2, const double* Ut1_prev,
+                          const double* Ut2_prev, long long dt, double* out) {
+    const int have_prev = Ut1_prev != NULL && Ut2_prev != NULL;
+    double sum_dd = 0.0, sum_uu = 0.0, ke = 0.0, am = 0.0, umax = 0.0;
+    for (int i = 1; i <= g->n1; ++i)
+        for (int j = 1; j <= g->n2; ++j) {
+            size_t m = cidx(g, i, j);
+            int jc = geo_col(g, j);
+            vec2 t1 = tangent(g, 0, i, jc), t2 = tangent(g, 1, i, jc);
+            vec2 x = g->pos[pidx(g, i, jc)];
+            double J = g->Jvol[m];
+            vec2 u = {Ut1[m] * t1.x + Ut2[m] * t2.x, Ut1[m] * t1.y + Ut2[m] * t2.y};
+            double uu = u.x * u.x + u.y * u.y;
+            sum_uu += J * uu;
+            ke += 0.5 * J * rho[m] * uu;
+            if (g->kind != ORC_PLANAR) am += J * rho[m] * (x.x * u.y - x.y * u.x);
+            if (sqrt(uu) > umax) umax = sqrt(uu);
+            if (have_prev) {
+                vec2 up = {Ut1_prev[m] * t1.x + Ut2_prev[m] * t2.x,
+                           Ut1_prev[m] * t1.y + Ut2_prev[m] * t2.y};
+                double ex = u.x - up.x, ey = u.y - up.y;
+                sum_dd += J * (ex * ex + ey * ey);
+            }
+        }
+    double res = INFINITY;
+    if (have_prev && dt > 0) {
+        if (sum_uu > 0.0) res = sqrt(sum_dd) / ((double)dt * sqrt(sum_uu));
+        else res = sum_dd > 0.0 ? INFINITY : 0.0;
+    }
+    out[0] = res;
+    out[1] = ke;
+    out[2] = am;
+    out[3] = umax;
+    out[4] = sum_uu;
+}
+
 void orc_get_volume(const orc_grid* g, double* J) {
     memcpy(J, g->Jvol, (size_t)g->n1 * (size_t)g->n2 * sizeof(double));
 }

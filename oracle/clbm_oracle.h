@@ -95,6 +95,28 @@ double orc_feq(const orc_grid* g, int alpha, double rho, const double* U,
 /* Totals of the state N'(t-1): out[0]=sum N', out[1..2]=sum c^k N'. */
 void orc_totals(const orc_grid* g, double* out);
 
+/* Flow diagnostics of Sec. 3.1, where a steady state is judged by the total
+ * kinetic energy (and, for the circular flows, the angular momentum) no
+ * longer changing while the mass stays fixed.  Inputs are cell fields
+ * [n1][n2]: the density rho and the contravariant velocity Ut^k (Eq. 18) of
+ * every cell, as orc_moments gives them; Ut1_prev / Ut2_prev (both may be
+ * NULL) hold the velocity dt steps earlier.  The physical velocity of a cell
+ * is u = Ut^1 g_1 + Ut^2 g_2 with the tangent vectors of its node (Sec. 2),
+ * J is the cell volume of N = J f (after a no-flow adjustment, the adjusted
+ * one), x the node position.
+ *   out[0]  residual ||u - u_prev||_J / (dt ||u||_J), ||v||_J^2 = sum J v.v
+ *           (+inf without a previous velocity or with dt <= 0; 0 when u and
+ *           u_prev both vanish);
+ *   out[1]  kinetic energy 1/2 sum J rho |u|^2;
+ *   out[2]  angular momentum about the origin, sum J rho (x cross u).z, on
+ *           polar and general grids (planar grids have no natural origin:
+ *           0 there);
+ *   out[3]  max |u|;
+ *   out[4]  sum J |u|^2. */
+void orc_flow_diagnostics(const orc_grid* g, const double* rho, const double* Ut1,
+                          const double* Ut2, const double* Ut1_prev,
+                          const double* Ut2_prev, long long dt, double* out);
+
 /* Volume J used by N = J f; set_volume overwrites it ([n1][n2]). */
 void orc_get_volume(const orc_grid* g, double* J);
 void orc_set_volume(orc_grid* g, const double* J);

@@ -49,6 +49,7 @@ def lib():
         L.orc_feq.restype = C.c_double
         L.orc_feq.argtypes = [C.c_void_p, C.c_int, C.c_double, dp, dp, dp]
         L.orc_totals.argtypes = [C.c_void_p, dp]
+        L.orc_flow_diagnostics.argtypes = [C.c_void_p] + [dp] * 5 + [C.c_longlong, dp]
         L.orc_get_volume.argtypes = [C.c_void_p, dp]
         L.orc_set_volume.argtypes = [C.c_void_p, dp]
         L.orc_no_flow_adjust.argtypes = [C.c_void_p, C.c_longlong, dp]
@@ -180,6 +181,29 @@ class Grid:
         out = np.empty(3)
         lib().orc_totals(self._h, _p(out))
         return out
+
+    def flow_diagnostics(self, rho, Ut1, Ut2, prev=None, dt=0):
+        """Sec. 3.1 diagnostics of given fields (each (n1, n2)); prev is the
+        (Ut1, Ut2) pair dt steps earlier or None.  dict of res, ke, am (angular
+        momentum about the origin; 0 on planar grids), umax, uu (sum J |u|^2)."""
+        f = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, Ut1, Ut2)]
+        for a in f:
+            assert a.shape == (self.n1, self.n2)
+        p = (None, None) if prev is None else tuple(
+            np.ascontiguousarray(a, dtype=np.float64) for a in prev)
+        out = np.empty(5)
+        lib().orc_flow_diagnostics(self._h, _p(f[0]), _p(f[1]), _p(f[2]), _p(p[0]), _p(p[1]),
+                                   int(dt), _p(out))
+        return dict(res=out[0], ke=out[1], am=out[2], umax=out[3], uu=out[4])
+
+    def diagnostics(self, prev=None, dt=0):
+        """flow_diagnostics of the current state's moments (orc_moments),
+        plus the moment fields themselves (rho, Ut1, Ut2) and the totals
+        (mass, P1, P2 of the state N'(t-1))."""
+        m = self.moments()
+        d = self.flow_diagnostics(m["rho"], m["Ut1"], m["Ut2"], prev, dt)
+        d.update(rho=m["rho"], Ut1=m["Ut1"], Ut2=m["Ut2"], totals=self.totals())
+        return d
 
     def volume(self):
         out = np.empty((self.n1, self.n2))
