@@ -119,9 +119,13 @@ class Server:
         self.done = []
         self.used = 0.0
         self._batches = {}
+        self._retired = []        # grids of retired lattices, freed once no batch lists them
         self._dirty = True
         self.t0 = None
         self._next_id = 0
+        self.tunes = 0            # autotuner runs (a shape class is timed once per process)
+        self.deferred = 0         # admission checks that found the head of the queue over budget
+        self.peak_bytes = 0.0     # most workspace bytes held at once
 
     # ------------------------------------------------------------ requests
     def submit(self, req):
@@ -146,17 +150,28 @@ class Server:
             req = self.queue[0]
             need = clbm.workspace_bytes(req.lattice, self.precision, req.n1, req.n2)
             if self.used + need > self.budget:
+                self.deferred += 1
                 break
             self.queue.pop(0)
             g = build_grid(req, self.precision, self.stream, self.device)
             self.active.append(dict(req=req, grid=g, bytes=need, steps=0, t_admit=now, checks=0))
             self.used += need
+            self.peak_bytes = max(self.peak_bytes, self.used)
             self._dirty = True
 
-    def _rebuild(self):
+    def _close_batches(self):
+        """Destroy every batch, then the grids of retired lattices (a batch
+        holds its lattices' handles until it is destroyed)."""
         for b, _ in self._batches.values():
             b.close()
         self._batches = {}
+        for g, nbytes in self._retired:
+            g.close()
+            self.used -= nbytes
+        self._retired = []
+
+    def _rebuild(self):
+        self._close_batches()
         groups = {}
         for a in self.active:
             groups.setdefault(a["req"].lattice, []).append(a)
@@ -171,12 +186,13 @@ class Server:
         m = g.moments(names=("rho", "Ut1", "Ut2"))
         t_done = self._now()
         out = dict(rid=req.rid, case=req.case, lattice=req.lattice, n1=req.n1, n2=req.n2,
-                   steps=a["steps"], residual=res, converged=converged,
+                   steps=g.t, residual=res, converged=converged,
                    status=_status(converged, res),
                    latency=t_done - req.arrival, t_admit=a["t_admit"], t_done=t_done,
                    Ut2_profile=m["Ut2"][:, 0].copy(), rho_profile=m["rho"][:, 0].copy())
-        g.close()
-        self.used -= a["bytes"]
+        # the grid's memory is released (and leaves the budget) with the
+        # batch that still lists it
+        self._retired.append((g, a["bytes"]))
         self.done.append(out)
         req.future.set_result(out)
         self._dirty = True
@@ -186,6 +202,9 @@ class Server:
         """Serve until the queue is empty and every admitted lattice retired."""
         self.t0 = time.perf_counter()
         while self.queue or self.active:
+            if self._retired:          # free retired lattices before admitting more
+                self._close_batches()
+                self._dirty = True
             self._admit()
             if not self.active:
                 wait = self.queue[0].arrival - self._now()
@@ -195,29 +214,32 @@ class Server:
             if self._dirty:
                 self._rebuild()
                 if self.tune:
+                    # time the variants only for a shape class not timed yet in
+                    # this process; tuning advances every member (steps + 1 per
+                    # usable variant), which the grids' own time counters record
                     for b, _ in self._batches.values():
-                        b.tune(steps=2)
-                        for a in _:
-                            a["steps"] += 4 * 3
+                        if not b.variant()[1]:
+                            b.tune(steps=2)
+                            self.tunes += 1
             for b, members in self._batches.values():
                 b.step(self.chunk)
-                for a in members:
-                    a["steps"] += self.chunk
             for Q, (b, members) in list(self._batches.items()):
                 res, _ = b.residual()   # NaN marks a lattice that went unstable
                 for a, r in zip(members, res):
                     a["checks"] += 1
+                    a["steps"] = a["grid"].t
                     conv = a["checks"] > 1 and np.isfinite(r) and r <= a["req"].tol
                     if conv or a["steps"] >= a["req"].max_steps or not np.isfinite(r) and a["checks"] > 1:
                         self.active.remove(a)
                         self._retire(a, float(r), bool(conv))
-        for b, _ in self._batches.values():
-            b.close()
-        self._batches = {}
+        self._close_batches()
         return self.stats()
 
     def stats(self):
-        return _stats(self.done)
+        out = _stats(self.done)
+        out.update(deferred_admissions=self.deferred, peak_workspace_bytes=self.peak_bytes,
+                   budget_bytes=self.budget, tuner_runs=self.tunes)
+        return out
 
 
 def serve_serial(requests, precision="fp32", chunk=100, device=0):
@@ -251,6 +273,7 @@ def serve_serial(requests, precision="fp32", chunk=100, device=0):
         t_done = time.perf_counter() - t0
         done.append(dict(rid=req.rid, steps=steps, residual=r, converged=bool(conv),
                          status=_status(conv, r), latency=t_done - req.arrival, t_done=t_done,
+                         service=t_done - max(req.arrival, now),
                          Ut2_profile=m["Ut2"][:, 0].copy(), rho_profile=m["rho"][:, 0].copy()))
         g.close()
     return done, _stats(done)
@@ -281,8 +304,9 @@ def _stats(done):
 def poisson_requests(n, rate, seed=20230105, n1_range=(16, 64), n2_range=(16, 128),
                      tau_range=(0.55, 1.0), speed_range=(1e-3, 1e-2), tol=1e-8, max_steps=100000,
                      lattices=(9, 21)):
-    """Seeded request stream: Poisson arrivals at `rate` per second, case and
-    lattice uniform, sizes log-uniform, tau and target speed uniform.  The
+    """Seeded request stream: Poisson arrivals at `rate` per second (0: all at
+    once), case and lattice uniform, sizes log-uniform, tau and target speed
+    uniform; one seed gives the same requests at every rate.  The
     circular flows (annulus 1 <= r <= 2) take the azimuthal size from the
     radial one so that cells are near-square at the inner wall, as the paper's
     polar grids are (Sec. 3.3); an independent n2 gives cells of aspect ratio
@@ -291,7 +315,10 @@ def poisson_requests(n, rate, seed=20230105, n1_range=(16, 64), n2_range=(16, 12
     t = 0.0
     out = []
     for k in range(n):
-        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        # the gap is drawn at every rate (0: everything at t = 0), so streams
+        # of one seed hold the same requests at any rate
+        gap = rng.exponential(1.0)
+        t += gap / rate if rate > 0 else 0.0
         n1 = int(round(math.exp(rng.uniform(math.log(n1_range[0]), math.log(n1_range[1])))))
         n2 = int(round(math.exp(rng.uniform(math.log(n2_range[0]), math.log(n2_range[1])))))
         case = CASES[rng.integers(len(CASES))]

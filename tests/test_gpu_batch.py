@@ -1,11 +1,13 @@
-"""Batched stepping: lattices of uneven shapes advanced together give the
-same result as each advanced alone, for every tile variant."""
+"""Batched stepping: lattices of uneven shapes advanced together match the
+FP64 oracle run of each lattice (velocity and state) and give the same
+result as each advanced alone, for every tile variant."""
 import math
 
 import numpy as np
 import pytest
 
 import clbm_inputs as I
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +37,25 @@ def make_grid(kind, Q, prec, n1, n2, stream, seed, iters=0):
     return g
 
 
+def make_oracle(kind, Q, n1, n2, seed, iters=0):
+    """The oracle's copy of make_grid's lattice (same seeded tau, edges,
+    walls, wall speed and body force)."""
+    rng = np.random.default_rng(seed)
+    tau = float(rng.uniform(0.6, 1.0))
+    if kind == "polar":
+        e = I.polar_edges(1.0, 2.0, n1, 0.3)
+        o = O.Grid(Q, n1, n2, O.POLAR, edges=e, bc_lo=O.MOVING, bc_hi=O.NOSLIP)
+        o.set_case(tau, 1.0, 0.02 * (1.0 / n1) / math.sin(2.0 * math.pi / n2), 0.0)
+    else:
+        e = I.geometric_stretch_edges(n1, 1.03, float(n1))
+        o = O.Grid(Q, n1, n2, O.PLANAR, edges=e, step2=1.0, bc_lo=O.NOSLIP, bc_hi=O.MOVING)
+        nu = (1 / 3 if Q == 9 else 2 / 3) * (tau - 0.5)
+        o.set_case(tau, 1.0, 0.0, 0.01, (0.0, 8 * nu * 0.02 / n1 ** 2))
+    o.set_force_iterations(iters)
+    o.init_rest()
+    return o
+
+
 SHAPES = [("polar", 12, 50), ("planar", 9, 33), ("polar", 20, 130), ("planar", 17, 257),
           ("planar", 4, 5), ("polar", 16, 64)]
 
@@ -46,6 +67,50 @@ def build(Q, prec, stream, iters=(0,) * len(SHAPES)):
 
 @pytest.mark.parametrize("Q,prec", [(21, 0), (9, 0), (21, 1), (9, 1)])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_batch_matches_oracle(Q, prec, variant):
+    """Every lattice of a batch against its own oracle run: 61 steps, a
+    residual call (the reduction updates every lattice's snapshot and the
+    descriptors), 30 more steps.  Velocity (Ut, normwise) within 1e-12 in
+    FP64 and 1e-5 in FP32; the state's deviation from rest,
+    ||N - N_oracle|| / ||N_oracle - N_rest||, within 1e-11 / 1e-5 (D2Q9's
+    wall rows on the stretched channels amplify rounding under the lagged
+    force -- a property of the method the oracle shares -- so its FP64 state
+    parity measures 1.3e-12 while its velocity stays within 1e-12)."""
+    if variant == 4 and prec == 0:
+        pytest.skip("the pipelined TMA variant stores 16/32-bit populations")
+    c = _clbm()
+    stream = torch.cuda.Stream()
+    # D2Q9 polar lattices iterate the force, as the server runs them: with the
+    # lagged force their inner-wall radial mode amplifies rounding (a
+    # property of the method the oracle shares), which would measure that
+    # amplification instead of the batch
+    iters = (1, 0, 1, 0, 0, 2) if Q == 9 else (0,) * len(SHAPES)
+    grids = build(Q, prec, stream, iters)
+    ors = [make_oracle(k, Q, n1, n2, sd, it)
+           for sd, ((k, n1, n2), it) in enumerate(zip(SHAPES, iters))]
+    rest = [o.state() for o in ors]
+    b = c.Batch(grids)
+    b.set_variant(variant)
+    b.step(61)
+    b.residual()
+    b.step(30)
+    tol_u, tol_s = (1e-12, 1e-11) if prec == 0 else (1e-5, 1e-5)
+    for k, (g, o) in enumerate(zip(grids, ors)):
+        o.step(91)
+        assert g.t == 91
+        ref = o.moments()
+        m = g.moments()
+        eu = math.sqrt((((m["Ut1"] - ref["Ut1"]) ** 2 + (m["Ut2"] - ref["Ut2"]) ** 2).sum())
+                       / ((ref["Ut1"] ** 2 + ref["Ut2"] ** 2).sum()))
+        so = o.state()
+        es = np.linalg.norm(g.state() - so) / np.linalg.norm(so - rest[k])
+        assert eu <= tol_u, (k, SHAPES[k], "velocity", eu)
+        assert es <= tol_s, (k, SHAPES[k], "state", es)
+    b.close()
+
+
+@pytest.mark.parametrize("Q,prec", [(21, 0), (9, 0), (21, 1), (9, 1)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_batch_matches_lattices_alone(Q, prec, variant):
     if variant == 4 and prec == 0:
         pytest.skip("the pipelined TMA variant stores 16/32-bit populations")
@@ -53,6 +118,7 @@ def test_batch_matches_lattices_alone(Q, prec, variant):
     stream = torch.cuda.Stream()
     alone = build(Q, prec, stream)
     mixed = build(Q, prec, stream)
+    start = [g.state() for g in alone]
     for g in alone:
         g.set_kernel(1)
         g.step(61)
@@ -60,11 +126,13 @@ def test_batch_matches_lattices_alone(Q, prec, variant):
     b.set_variant(variant)
     b.step(61)
     b.residual()
-    for ga, gm in zip(alone, mixed):
+    for ga, gm, s0 in zip(alone, mixed, start):
         assert gm.t == 61
         sa, sm = ga.state(), gm.state()
-        scale = np.abs(sa).max()
-        tol = 1e-13 if prec == 0 else 1e-6
+        # relative to how far the state moved from its start (the rest
+        # populations themselves are exact in every kernel)
+        scale = np.abs(sa - s0).max()
+        tol = 1e-12 if prec == 0 else 1e-5
         assert np.abs(sa - sm).max() <= tol * scale
     b.close()
 

@@ -1,6 +1,13 @@
-"""Serving: continuous batching of solve requests on one GPU."""
+"""Serving: continuous batching of solve requests on one GPU.  Each served
+result is checked against the FP64 oracle run for the same number of steps
+(which also checks the step count the server reports), and against the same
+request solved alone."""
+import math
+
 import numpy as np
 import pytest
+
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +83,94 @@ def test_poisson_stream_converges():
             assert d["status"] == "converged"
     assert st["converged"] >= 10
     assert st["p50_s"] <= st["p99_s"]
+
+
+def oracle_of(req, steps):
+    """The request's lattice advanced by the oracle: the flows of Sec. 3 in
+    lattice units as the server sets them up (planar channels of unit cells;
+    the annulus 1 <= r <= 2 with n1 uniform radial cells; wall speeds as
+    contravariant U0^2 = u dx / |g_2|; the forced flows' acceleration chosen
+    so that the exact profile peaks at the requested speed)."""
+    Q, n1, n2 = req.lattice, req.n1, req.n2
+    T0 = 1.0 / 3.0 if Q == 9 else 2.0 / 3.0
+    nu = T0 * (req.tau - 0.5)
+    it = 1 if Q == 9 and req.case.startswith("circular") else 0
+    if req.case.startswith("planar"):
+        e = np.arange(n1 + 1, dtype=np.float64)
+        if req.case == "planar_couette":
+            o = O.Grid(Q, n1, n2, O.PLANAR, edges=e, step2=1.0, bc_lo=O.NOSLIP, bc_hi=O.MOVING)
+            o.set_case(req.tau, 1.0, 0.0, req.speed)
+        else:
+            o = O.Grid(Q, n1, n2, O.PLANAR, edges=e, step2=1.0)
+            o.set_case(req.tau, 1.0, 0.0, 0.0, (0.0, 8.0 * nu * req.speed / n1 ** 2))
+    else:
+        dx = 1.0 / n1
+        e = 1.0 + dx * np.arange(n1 + 1, dtype=np.float64)
+        sn = math.sin(2.0 * math.pi / n2)
+        if req.case == "circular_couette":
+            o = O.Grid(Q, n1, n2, O.POLAR, edges=e, bc_lo=O.MOVING, bc_hi=O.NOSLIP)
+            o.set_case(req.tau, 1.0, req.speed * dx / sn, 0.0)
+        else:
+            M = 1.0 / dx
+            r = np.linspace(M, M + n1, 2001)
+            peak = float(((r ** 2 - M ** 2) * ((M + n1) ** 2 - r ** 2) / r).max())
+            o = O.Grid(Q, n1, n2, O.POLAR, edges=e)
+            o.set_case(req.tau, 1.0, 0.0, 0.0, (0.0, 8.0 * nu * req.speed / (sn * peak)))
+    o.set_force_iterations(it)
+    o.init_rest()
+    o.step(steps)
+    return o.moments()
+
+
+def _stream(max_steps):
+    """Requests of all four flows and both lattices arriving while others
+    run (membership changes, so batches are rebuilt and re-tuned)."""
+    S = _serve()
+    R = S.Request
+    out = [R("planar_couette", 9, 16, 8, 0.8, 0.01), R("circular_couette", 21, 12, 75, 0.9, 0.01),
+           R("planar_poiseuille", 21, 20, 6, 0.7, 0.02), R("circular_poiseuille", 9, 10, 63, 1.0, 0.01),
+           R("planar_couette", 21, 9, 5, 0.6, 0.005), R("circular_poiseuille", 21, 8, 50, 0.75, 0.008),
+           R("planar_poiseuille", 9, 14, 7, 0.95, 0.004), R("circular_couette", 9, 9, 57, 0.85, 0.006)]
+    for k, r in enumerate(out):
+        r.tol, r.max_steps, r.arrival = 1e-30, max_steps + 37 * k, 0.004 * k
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_served_profiles_match_the_oracle_with_tuning(precision, tol):
+    """Continuous batching with the autotuner on: each result's velocity
+    profile equals the oracle's after the number of steps the server
+    reports (tuning advances the lattices too), within the precision's
+    velocity tolerance.  FP32 storage rounds the state once per step, and on
+    the body-force flows that rounding of a small per-step increment
+    accumulates (the single-lattice path shows the same error, bit for bit):
+    the FP32 bound is max(1e-5, steps x 2^-24)."""
+    S = _serve()
+    srv = S.Server(precision=precision, chunk=40, tune=True)
+    reqs = _stream(600)   # developed enough that FP32 rounding is small against the flow
+    futs = [srv.submit(r) for r in reqs]
+    srv.run()
+    assert srv.tunes >= 1
+    for r, f in zip(reqs, futs):
+        d = f.result()
+        assert d["steps"] >= r.max_steps and d["status"] == "capped"
+        ref = oracle_of(r, d["steps"])["Ut2"][:, 0]
+        err = np.linalg.norm(d["Ut2_profile"] - ref) / np.linalg.norm(ref)
+        bound = tol if precision == "fp64" else max(tol, d["steps"] * 2.0 ** -24)
+        assert err <= bound, (r.case, r.lattice, d["steps"], err)
+
+
+def test_tuner_runs_once_per_shape_class():
+    """Rebuilding batches as lattices come and go reuses the tuner's choice
+    for a class already timed in this process."""
+    S = _serve()
+    srv = S.Server(precision="fp32", chunk=40, tune=True)
+    for r in _stream(200) + _stream(240):
+        srv.submit(r)
+    srv.run()
+    srv2 = S.Server(precision="fp32", chunk=40, tune=True)
+    for r in _stream(200) + _stream(240):
+        srv2.submit(r)
+    srv2.run()
+    assert srv2.tunes == 0
+    assert [d["steps"] for d in srv2.done] and all(d["status"] == "capped" for d in srv2.done)
