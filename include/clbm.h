@@ -61,7 +61,8 @@ typedef enum {
 /* Geometry of the coordinate map x(q) (Sec. 2, App. C, App. D). */
 typedef enum {
     CLBM_GEOM_PLANAR = 0,  /* x = (x^1_i, (j - 1/2) step2), x^1_i edge midpoints */
-    CLBM_GEOM_POLAR = 1,   /* x = r_i (cos th_j, sin th_j), th_j = (j - 1/2) 2 pi / n2 */
+    CLBM_GEOM_POLAR = 1,   /* x = r_i (cos th_j, sin th_j), th_j = (j - 1/2) 2 pi / n2
+                              (n2_period in place of n2 when set) */
     CLBM_GEOM_GENERAL = 2  /* node positions given (nodes); Sec. 2 in full generality:
                               metric, volume and Theta of every cell, per-cell tables */
 } clbm_geom_kind;
@@ -96,6 +97,9 @@ typedef struct {
                                are the ghost nodes of App. B (e.g. mirror images
                                through straight walls), the columns beyond the ends
                                the periodic images.  Read during create only. */
+    int n2_period;          /* POLAR: columns of the whole ring, th_j = (j - 1/2) 2 pi /
+                               n2_period (a slab of a ring split along q^2); <= 0
+                               means n2.  Ignored by the other kinds. */
 } clbm_grid_desc;
 
 typedef struct {
@@ -161,6 +165,35 @@ clbm_status clbm_moments(clbm_handle h, double* rho, double* U1, double* U2,
                          double* Ut1, double* Ut2, double* F1, double* F2,
                          int dst_is_device);
 
+/* Asynchronous host copies, for a caller that streams starts in and results
+ * out while the grid computes (the copies run on a copy stream the grid
+ * creates on first use, with two FP64 upload slots of Q n1 n2 values and two
+ * moment slots of 3 n1 n2 values that it allocates then and keeps).  Host
+ * buffers should be page-locked: from pageable memory a copy does not
+ * overlap.  Every host buffer must stay valid, and an upload's unchanged,
+ * until clbm_wait_copies returns (or, for an upload, until the grid's stream
+ * has run the clbm_set_uploaded_state that consumes it).
+ *   clbm_upload_state_async: start copying N'(q, t-1) (host, FP64
+ *     [Q][n1][n2]) into the next upload slot; returns at once.  CLBM_EBUSY
+ *     when two uploads wait to be set already.
+ *   clbm_set_uploaded_state: make the oldest waiting upload the grid's state,
+ *     as clbm_set_state does, ordered on the grid's stream after its copy
+ *     (no host wait); CLBM_EINVAL if none waits.
+ *   clbm_download_moments_async: the moments rho, Ut^1, Ut^2 (as
+ *     clbm_moments gives them) of the current state, computed on the grid's
+ *     stream into the next moment slot and copied into the host buffers
+ *     ([n1][n2] FP64 each, any may be NULL) on the copy stream; returns at
+ *     once.
+ *   clbm_wait_copies: block until every copy issued so far has landed;
+ *     reports errors of the grid's earlier work as a synchronising call.
+ * The paper has no counterpart: these keep host transfers off the update's
+ * critical path when every step's input comes from, and its result goes
+ * to, host memory. */
+clbm_status clbm_upload_state_async(clbm_handle h, const double* Np);
+clbm_status clbm_set_uploaded_state(clbm_handle h);
+clbm_status clbm_download_moments_async(clbm_handle h, double* rho, double* Ut1, double* Ut2);
+clbm_status clbm_wait_copies(clbm_handle h);
+
 /* Convergence and conservation diagnostics (Sec. 3.1: mass, kinetic energy,
  * angular momentum).  res = ||u(t) - u(t')||_J / ((t - t') ||u(t)||_J) with
  * physical u = Ut^k g_k and t' the time of the previous call (+inf on the
@@ -172,6 +205,44 @@ clbm_status clbm_moments(clbm_handle h, double* rho, double* U1, double* U2,
  * not finite and positive, CLBM_ETIMEOUT if a bounded device wait of an
  * earlier update gave up.  Synchronises. */
 clbm_status clbm_residual(clbm_handle h, double* res, double cons[6]);
+
+/* The sums behind clbm_residual, for callers that combine several grids (the
+ * slabs of one lattice split along q^2 over several GPUs): parts = {sum J
+ * |u(t) - u(t')|^2, sum J |u|^2, sum N', sum c^1 N', sum c^2 N', kinetic
+ * energy, angular momentum, max |u|, cells with a non-finite or non-positive
+ * density}, *dt = t - t' (0 on the first call).  Over several grids the
+ * parts add (max |u| takes the maximum) and the residual is
+ * sqrt(sum parts[0]) / (dt sqrt(sum parts[1])).  Moves the snapshot like
+ * clbm_residual; same errors.  Synchronises. */
+clbm_status clbm_residual_parts(clbm_handle h, double parts[9], long long* dt);
+
+/* Slabs along q^2 (one lattice split over several GPUs, each holding a run of
+ * columns as a grid of its own; POLAR slabs give the ring's size in
+ * n2_period).  The update (Eq. 12) pulls population a from the cell c_a
+ * behind, so a slab's first |c2| columns read the lower neighbour's last
+ * columns for every population with c2 > 0, and its last columns the upper
+ * neighbour's first columns for c2 < 0: one strip per (population, depth),
+ * 12 per side for D2Q21 (7 at depth 1, 4 at depth 2, 1 at depth 3), 3 for
+ * D2Q9, each covering the n1 + 2h stored rows (App. B's ghost rows
+ * included: they are filled per column).  Protocol: after clbm_set_case /
+ * clbm_set_state (and the like) call clbm_fill_ghosts, then exchange; after
+ * every clbm_step(1) exchange; an exchange packs both sides, sends side 0 to
+ * the lower and side 1 to the upper neighbour, and unpacks what the lower
+ * neighbour sent as side 0 and what the upper one sent as side 1.  Every
+ * call that reads the state (step, moments, residual) then sees the
+ * neighbours' columns; without exchanges the grid is periodic on its own.
+ *   clbm_fill_ghosts: rebuild the current state's ghost rows and columns now
+ *     if it was set from outside (what clbm_step would do first).  Async.
+ *   clbm_halo_values: values of one side's strips, in the storage type
+ *     (8 / 4 / 2 bytes per value for FP64 / FP32 / FP16 and BF16).
+ *   clbm_halo_pack / clbm_halo_unpack: side 0 or 1, buf device memory of
+ *     clbm_halo_values values, caller-owned; values move as stored, bit for
+ *     bit.  Async on the grid's stream.  CLBM_EINVAL for general grids and
+ *     slabs narrower than the stencil (n2 < 3 for D2Q21). */
+clbm_status clbm_fill_ghosts(clbm_handle h);
+clbm_status clbm_halo_values(clbm_handle h, size_t* values);
+clbm_status clbm_halo_pack(clbm_handle h, int side, void* buf);
+clbm_status clbm_halo_unpack(clbm_handle h, int side, const void* buf);
 
 /* "No flow" adjustment (Sec. 3.1, Eq. 23): in FP64, run the grid from rest
  * with U0 = 0 and no body force for nsteps, then J <- J rho_nf / rho0 (per
@@ -259,6 +330,12 @@ clbm_status clbm_batch_set_variant(clbm_batch_handle b, int variant);
  * ms_per_step[5] (may be NULL) the timings (-1 for a variant the batch
  * cannot use).  Synchronises. */
 clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* ms_per_step);
+/* The batch's update variant (0-4, as clbm_batch_set_variant) and whether it
+ * came from the tuner's cache when the batch was created (1) or is the
+ * default / a later choice (0): a caller that rebuilds batches as lattices
+ * come and go re-tunes only classes it has not timed.  variant and cached
+ * may be NULL.  Host only. */
+clbm_status clbm_batch_get_variant(clbm_batch_handle b, int* variant, int* cached);
 clbm_status clbm_batch_launch_count(clbm_batch_handle b, long long* launches);
 clbm_status clbm_batch_destroy(clbm_batch_handle b);
 

@@ -37,7 +37,7 @@ class _Desc(C.Structure):
                 ("kind", C.c_int), ("edges1", C.POINTER(C.c_double)), ("step2", C.c_double),
                 ("dx", C.c_double), ("bc_lo", C.c_int), ("bc_hi", C.c_int), ("device", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("nodes", C.POINTER(C.c_double))]
+                ("nodes", C.POINTER(C.c_double)), ("n2_period", C.c_int)]
 
 
 class _Case(C.Structure):
@@ -80,6 +80,15 @@ def lib():
             "clbm_step": [h, ll],
             "clbm_moments": [h, vp, vp, vp, vp, vp, vp, vp, C.c_int],
             "clbm_residual": [h, dp, dp],
+            "clbm_upload_state_async": [h, vp],
+            "clbm_set_uploaded_state": [h],
+            "clbm_download_moments_async": [h, vp, vp, vp],
+            "clbm_wait_copies": [h],
+            "clbm_residual_parts": [h, dp, C.POINTER(ll)],
+            "clbm_fill_ghosts": [h],
+            "clbm_halo_values": [h, C.POINTER(C.c_size_t)],
+            "clbm_halo_pack": [h, C.c_int, vp],
+            "clbm_halo_unpack": [h, C.c_int, vp],
             "clbm_no_flow_adjust": [h, ll, vp],
             "clbm_time": [h, C.POINTER(ll)],
             "clbm_set_stream": [h, vp],
@@ -95,6 +104,7 @@ def lib():
             "clbm_batch_residual": [h, vp, vp],
             "clbm_batch_set_variant": [h, C.c_int],
             "clbm_batch_tune": [h, C.c_int, C.POINTER(C.c_int), vp],
+            "clbm_batch_get_variant": [h, C.POINTER(C.c_int), C.POINTER(C.c_int)],
             "clbm_batch_launch_count": [h, C.POINTER(ll)],
             "clbm_batch_destroy": [h],
             "clbm_destroy": [h],
@@ -144,7 +154,8 @@ def _is_device(x):
     return x is not None and not isinstance(x, np.ndarray) and x.is_cuda
 
 
-def _desc(lattice, precision, n1, n2, kind, edges, step2, dx, bc_lo, bc_hi, device, stream, nodes=None):
+def _desc(lattice, precision, n1, n2, kind, edges, step2, dx, bc_lo, bc_hi, device, stream, nodes=None,
+          n2_period=0):
     dp = C.POINTER(C.c_double)
     if kind == GENERAL:
         P = np.ascontiguousarray(nodes, dtype=np.float64)
@@ -157,7 +168,7 @@ def _desc(lattice, precision, n1, n2, kind, edges, step2, dx, bc_lo, bc_hi, devi
     if e.shape != (n1 + 1,):
         raise ValueError("edges must have n1+1 entries")
     d = _Desc(lattice, precision, n1, n2, kind, e.ctypes.data_as(dp), float(step2), float(dx), bc_lo,
-              bc_hi, device, stream, None, 0, None)
+              bc_hi, device, stream, None, 0, None, int(n2_period))
     return d, e
 
 
@@ -186,7 +197,7 @@ class Grid:
     """
 
     def __init__(self, lattice, n1, n2, edges, kind=PLANAR, step2=1.0, precision=FP64, dx=0.0,
-                 bc_lo=NOSLIP, bc_hi=NOSLIP, device=0, stream=None, nodes=None):
+                 bc_lo=NOSLIP, bc_hi=NOSLIP, device=0, stream=None, nodes=None, n2_period=0):
         import torch
 
         if isinstance(precision, str):
@@ -198,7 +209,7 @@ class Grid:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         d, self._edges = _desc(self.Q, self.precision, self.n1, self.n2, self.kind, edges, step2, dx,
                                int(bc_lo), int(bc_hi), self.device.index, self.stream.cuda_stream,
-                               nodes)
+                               nodes, n2_period)
         nb = C.c_size_t()
         _check(lib().clbm_workspace_bytes(C.byref(d), C.byref(nb)))
         self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
@@ -323,12 +334,77 @@ class Grid:
         _check(lib().clbm_moments(self._h, *ptrs, int(device)))
         return out
 
+    # asynchronous host copies -----------------------------------------------
+    def upload_state_async(self, Np):
+        """Start copying N'(q, t-1) (float64 (Q, n1, n2) in host memory, best
+        page-locked) into one of the grid's two upload slots on its copy
+        stream; returns at once.  The array must stay alive and unchanged
+        until set_uploaded_state() has been called for it and the grid's
+        stream has passed that point (e.g. wait_copies() or the next
+        synchronising call)."""
+        arr = Np.numpy() if hasattr(Np, "numpy") else Np
+        if arr.shape != (self.Q, self.n1, self.n2) or arr.dtype != np.float64 or not arr.flags.c_contiguous:
+            raise ValueError("state must be a contiguous float64 (Q, n1, n2) host array")
+        _check(lib().clbm_upload_state_async(self._h, arr.ctypes.data))
+
+    def set_uploaded_state(self):
+        """Make the oldest upload the grid's state (on the grid's stream, after
+        its copy; no host wait), as set_state would."""
+        _check(lib().clbm_set_uploaded_state(self._h))
+
+    def download_moments_async(self, out):
+        """Compute rho, Ut1, Ut2 of the current state on the grid's stream and
+        copy them on the copy stream into out's float64 (n1, n2) host arrays
+        (keys rho, Ut1, Ut2, any may be missing; best page-locked); returns at
+        once.  wait_copies() blocks until they have landed."""
+        ptrs = []
+        for k in ("rho", "Ut1", "Ut2"):
+            a = out.get(k)
+            if a is not None:
+                a = a.numpy() if hasattr(a, "numpy") else a
+                if a.shape != (self.n1, self.n2) or a.dtype != np.float64 or not a.flags.c_contiguous:
+                    raise ValueError("%s must be a contiguous float64 (n1, n2) host array" % k)
+                ptrs.append(a.ctypes.data)
+            else:
+                ptrs.append(None)
+        _check(lib().clbm_download_moments_async(self._h, *ptrs))
+
+    def wait_copies(self):
+        """Block until every asynchronous copy issued so far has landed."""
+        _check(lib().clbm_wait_copies(self._h))
+
     def residual(self):
         """(res, cons): cons = mass, P1, P2, kinetic energy, angular momentum, max|u|."""
         r = C.c_double()
         cons = (C.c_double * 6)()
         _check(lib().clbm_residual(self._h, C.byref(r), cons))
         return r.value, np.array(list(cons))
+
+    def residual_parts(self):
+        """(parts[9], dt): the sums behind residual() (clbm_residual_parts)."""
+        parts = (C.c_double * 9)()
+        dt = C.c_longlong()
+        st = lib().clbm_residual_parts(self._h, parts, C.byref(dt))
+        if st != 4:
+            _check(st)
+        return np.array(list(parts)), dt.value
+
+    # slabs along q^2 (slab.py drives these) ----------------------------------
+    def fill_ghosts(self):
+        _check(lib().clbm_fill_ghosts(self._h))
+
+    def halo_values(self):
+        n = C.c_size_t()
+        _check(lib().clbm_halo_values(self._h, C.byref(n)))
+        return n.value
+
+    def halo_pack(self, side, buf):
+        """Pack side 0 (for the lower neighbour) or 1 into a device tensor of
+        halo_values() storage-type values."""
+        _check(lib().clbm_halo_pack(self._h, int(side), _ptr(buf)))
+
+    def halo_unpack(self, side, buf):
+        _check(lib().clbm_halo_unpack(self._h, int(side), _ptr(buf)))
 
     def no_flow_adjust(self, nsteps):
         rho_nf = np.empty((self.n1, self.n2))
@@ -397,6 +473,14 @@ class Batch:
         ms = np.empty(self.VARIANTS)
         _check(lib().clbm_batch_tune(self._h, int(steps), C.byref(best), ms.ctypes.data))
         return best.value, ms
+
+    def variant(self):
+        """(variant, cached): the update variant and whether it came from the
+        tuner's cache of this process when the batch was created."""
+        v = C.c_int()
+        cached = C.c_int()
+        _check(lib().clbm_batch_get_variant(self._h, C.byref(v), C.byref(cached)))
+        return v.value, bool(cached.value)
 
     def launch_count(self):
         n = C.c_longlong()

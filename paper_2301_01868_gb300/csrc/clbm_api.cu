@@ -79,7 +79,9 @@ struct clbm_grid {
     std::vector<double> edges;
     double step2;
     double* stage;          // lazily allocated FP64 staging buffer for host transfers
+    struct HostPipe* pipe;  // asynchronous host copies (created on first use)
     int ncol;               // geometry columns: 1 (planar, polar) or n2 (general)
+    int n2_period;          // columns of the whole ring (polar slabs), else n2
     double rest_mass;       // rho0 times the total volume (the rest part of the mass)
     std::vector<double> nodes;  // node positions of a general grid (for the no-flow clone)
     void* phys[2];          // the two state buffers (stA / stB alternate over them)
@@ -264,6 +266,61 @@ clbm_status staging(clbm_grid* g, double** out) {
     return CLBM_OK;
 }
 
+// Asynchronous host copies of one grid: a copy stream of its own, two FP64
+// state slots (uploads) and two moment slots (downloads), each slot with an
+// event that marks it filled and one that marks it read, so that an upload
+// for the next start overlaps the update of this one, and a download of
+// these moments overlaps the next update.  (Outside the unnamed namespace:
+// clbm_grid names it.)
+}  // namespace
+
+struct HostPipe {
+    cudaStream_t copy = nullptr;
+    double* in[2] = {nullptr, nullptr};    // Q n1 n2 FP64 each
+    double* out[2] = {nullptr, nullptr};   // 3 n1 n2 FP64 each: rho, Ut^1, Ut^2
+    cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
+    bool in_used[2] = {false, false}, out_used[2] = {false, false};
+    int next_in = 0, next_set = 0, next_out = 0, staged = 0;
+};
+
+namespace {
+
+void free_pipe(HostPipe* p) {
+    if (!p) return;
+    if (p->copy) cudaStreamSynchronize(p->copy);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(p->in[k]);
+        cudaFree(p->out[k]);
+        for (cudaEvent_t e : {p->in_ready[k], p->in_free[k], p->out_ready[k], p->out_free[k]})
+            if (e) cudaEventDestroy(e);
+    }
+    if (p->copy) cudaStreamDestroy(p->copy);
+    delete p;
+}
+
+clbm_status host_pipe(clbm_grid* g, HostPipe** out) {
+    if (!g->pipe) {
+        HostPipe* p = new (std::nothrow) HostPipe();
+        if (!p) return fail(CLBM_ENOMEM, "host copy pipeline");
+        const size_t nc = (size_t)g->n1 * g->n2;
+        bool ok = cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking) == cudaSuccess;
+        for (int k = 0; k < 2 && ok; ++k) {
+            ok = cudaMalloc((void**)&p->in[k], (size_t)g->Q * nc * 8) == cudaSuccess &&
+                 cudaMalloc((void**)&p->out[k], 3 * nc * 8) == cudaSuccess;
+            for (cudaEvent_t* e : {&p->in_ready[k], &p->in_free[k], &p->out_ready[k], &p->out_free[k]})
+                ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+        }
+        if (!ok) {
+            free_pipe(p);
+            cudaGetLastError();
+            return fail(CLBM_ENOMEM, "host copy pipeline: device buffers, stream or events");
+        }
+        g->pipe = p;
+    }
+    *out = g->pipe;
+    return CLBM_OK;
+}
+
 // Ghost rows and columns of the current state (what the next collision
 // pulls), rebuilt only after the state or the case was set from outside:
 // every update fills those of the buffer it writes.
@@ -350,6 +407,9 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
         pos.resize((size_t)(d->n1 + 8) * 9 * 2);
     }
     const double pi = 3.14159265358979323846;
+    const int n2_period = d->n2_period > 0 ? d->n2_period : d->n2;
+    if (d->kind == CLBM_GEOM_POLAR && n2_period < d->n2)
+        return fail(CLBM_EINVAL, "n2_period (%d) < n2 (%d)", n2_period, d->n2);
     for (int i = -3; !general && i <= d->n1 + 4; ++i) {
         const double s = node_coord(e, d->n1, i);
         if (d->kind == CLBM_GEOM_POLAR && !(s > 0.0))
@@ -361,7 +421,7 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
                 p[0] = s;
                 p[1] = (j - 0.5) * d->step2;
             } else {
-                const double th = (j - 0.5) * (2.0 * pi / d->n2);
+                const double th = (j - 0.5) * (2.0 * pi / n2_period);
                 p[0] = s * cos(th);
                 p[1] = s * sin(th);
             }
@@ -373,6 +433,7 @@ clbm_status clbm_create_grid(const clbm_grid_desc* d, clbm_handle* out) {
     g->prec = d->precision;
     g->n1 = d->n1;
     g->n2 = d->n2;
+    g->n2_period = n2_period;
     g->ld = ld;
     g->h = h;
     g->kind = d->kind;
@@ -832,9 +893,146 @@ clbm_status clbm_moments(clbm_handle g, double* rho, double* U1, double* U2, dou
     return check_err(g);
 }
 
-clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
-    Range nvtx_range("clbm_residual");
+clbm_status clbm_upload_state_async(clbm_handle g, const double* Np) {
+    Range nvtx_range("clbm_upload_state_async");
+    if (!g || !Np) return fail(CLBM_EINVAL, "handle or Np is NULL");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    HostPipe* p = nullptr;
+    st = host_pipe(g, &p);
+    if (st != CLBM_OK) return st;
+    if (p->staged == 2) return fail(CLBM_EBUSY, "two uploads wait already: set one first");
+    const int s = p->next_in;
+    // the slot is free once the conversion that read it last has run
+    if (p->in_used[s]) CK(cudaStreamWaitEvent(p->copy, p->in_free[s], 0));
+    CK(cudaMemcpyAsync(p->in[s], Np, (size_t)g->Q * g->n1 * g->n2 * 8, cudaMemcpyHostToDevice, p->copy));
+    CK(cudaEventRecord(p->in_ready[s], p->copy));
+    p->in_used[s] = true;
+    p->next_in ^= 1;
+    p->staged++;
+    return CLBM_OK;
+}
+
+clbm_status clbm_set_uploaded_state(clbm_handle g) {
+    Range nvtx_range("clbm_set_uploaded_state");
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
+    if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
+    if (!g->pipe || g->pipe->staged == 0) return fail(CLBM_EINVAL, "no upload waits to be set");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    HostPipe* p = g->pipe;
+    const int s = p->next_set;
+    CK(cudaStreamWaitEvent(g->stream, p->in_ready[s], 0));
+    launch_state_from_fp64(g->Q, g->prec, p->in[s], g->geo, g->stA, g->n1, g->n2, g->ld, g->h, g->ncol,
+                           g->stream);
+    launch_wall_init(g->prec, g->wall_r, g->wall_u, nullptr, nullptr, g->n1, g->n2, g->h, g->cs.rho0,
+                     g->stream);
+    g->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(p->in_free[s], g->stream));
+    p->next_set ^= 1;
+    p->staged--;
+    g->have_prev = false;
+    g->ghosts_ok = false;
+    return CLBM_OK;
+}
+
+clbm_status clbm_download_moments_async(clbm_handle g, double* rho, double* Ut1, double* Ut2) {
+    Range nvtx_range("clbm_download_moments_async");
+    if (!g) return fail(CLBM_EINVAL, "handle is NULL");
+    if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    HostPipe* p = nullptr;
+    st = host_pipe(g, &p);
+    if (st != CLBM_OK) return st;
+    const size_t nc = (size_t)g->n1 * g->n2;
+    const int s = p->next_out;
+    // the slot is free once the copies that read it last have landed
+    if (p->out_used[s]) CK(cudaStreamWaitEvent(g->stream, p->out_free[s], 0));
+    fill_ghosts(g);
+    MomArgs m = mom_args(g);
+    m.rho = p->out[s];
+    m.Ut1 = p->out[s] + nc;
+    m.Ut2 = p->out[s] + 2 * nc;
+    launch_moments(g->Q, g->prec, m, g->cs.force_iterations, 0, g->stream);
+    g->launches++;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(p->out_ready[s], g->stream));
+    CK(cudaStreamWaitEvent(p->copy, p->out_ready[s], 0));
+    double* dst[3] = {rho, Ut1, Ut2};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k]) CK(cudaMemcpyAsync(dst[k], p->out[s] + k * nc, nc * 8, cudaMemcpyDeviceToHost, p->copy));
+    CK(cudaEventRecord(p->out_free[s], p->copy));
+    p->out_used[s] = true;
+    p->next_out ^= 1;
+    return CLBM_OK;
+}
+
+clbm_status clbm_wait_copies(clbm_handle g) {
+    Range nvtx_range("clbm_wait_copies");
+    if (!g) return fail(CLBM_EINVAL, "handle is NULL");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    if (g->pipe) CK(cudaStreamSynchronize(g->pipe->copy));
+    return check_err(g);
+}
+
+clbm_status clbm_fill_ghosts(clbm_handle g) {
+    Range nvtx_range("clbm_fill_ghosts");
+    if (!g) return fail(CLBM_EINVAL, "handle is NULL");
+    if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    fill_ghosts(g);
+    CK(cudaGetLastError());
+    return CLBM_OK;
+}
+
+clbm_status clbm_halo_values(clbm_handle g, size_t* values) {
+    if (!g || !values) return fail(CLBM_EINVAL, "NULL argument");
+    *values = (size_t)halo_entries(g->Q) * (g->n1 + 2 * g->h);
+    return CLBM_OK;
+}
+
+clbm_status clbm_halo_pack(clbm_handle g, int side, void* buf) {
+    Range nvtx_range("clbm_halo_pack");
+    if (!g || !buf) return fail(CLBM_EINVAL, "handle or buf is NULL");
+    if (side != 0 && side != 1) return fail(CLBM_EINVAL, "side must be 0 or 1");
+    if (g->n2 < g->h) return fail(CLBM_EINVAL, "a slab needs n2 >= %d columns", g->h);
+    if (g->ncol != 1) return fail(CLBM_EINVAL, "halo strips need a planar or polar grid");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    launch_halo(g->Q, g->prec, g->stA, buf, (long long)(g->n1 + 2 * g->h) * g->ld, g->ld, g->n1 + 2 * g->h,
+                g->n2, side, 0, g->stream);
+    g->launches++;
+    CK(cudaGetLastError());
+    return CLBM_OK;
+}
+
+clbm_status clbm_halo_unpack(clbm_handle g, int side, const void* buf) {
+    Range nvtx_range("clbm_halo_unpack");
+    if (!g || !buf) return fail(CLBM_EINVAL, "handle or buf is NULL");
+    if (side != 0 && side != 1) return fail(CLBM_EINVAL, "side must be 0 or 1");
+    if (g->n2 < g->h) return fail(CLBM_EINVAL, "a slab needs n2 >= %d columns", g->h);
+    if (g->ncol != 1) return fail(CLBM_EINVAL, "halo strips need a planar or polar grid");
+    clbm_status st = select(g);
+    if (st != CLBM_OK) return st;
+    launch_halo(g->Q, g->prec, g->stA, const_cast<void*>(buf), (long long)(g->n1 + 2 * g->h) * g->ld, g->ld,
+                g->n1 + 2 * g->h, g->n2, side, 1, g->stream);
+    g->launches++;
+    CK(cudaGetLastError());
+    return CLBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The residual / conservation sums of the current state (slots of NRED, the
+// rest part of the mass added) and the steps since the last call (0 on the
+// first); moves the snapshot to this state.
+clbm_status residual_sums(clbm_grid* g, double (&v)[NRED], long long* dt_out) {
     if (!g->have_case) return fail(CLBM_EINVAL, "call clbm_set_case first");
     clbm_status st = select(g);
     if (st != CLBM_OK) return st;
@@ -853,25 +1051,53 @@ clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
     launch_reduce_final(g->partial, nb, g->red, g->stream);
     g->launches += 2;
     CK(cudaGetLastError());
-    double v[NRED];
     CK(cudaMemcpyAsync(v, g->red, sizeof(v), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     st = check_err(g);
     if (st != CLBM_OK) return st;
-    const long long dt = g->t - g->t_prev;
-    double r = INFINITY;
-    if (g->have_prev && dt > 0) r = v[1] > 0.0 ? sqrt(v[0]) / (dt * sqrt(v[1])) : (v[0] > 0 ? INFINITY : 0.0);
-    if (res) *res = r;
+    *dt_out = g->have_prev ? g->t - g->t_prev : 0;
     v[2] += g->rest_mass;
-    if (cons)
-        for (int k = 0; k < 6; ++k) cons[k] = v[2 + k];
     g->have_prev = true;
     g->t_prev = g->t;
+    return CLBM_OK;
+}
+
+clbm_status unstable_status(const clbm_grid* g, const double (&v)[NRED]) {
     if (v[8] > 0.0 || !std::isfinite(v[2]))
         return fail(CLBM_EUNSTABLE, "%g cells with a non-finite or non-positive density at t=%lld",
                     v[8], g->t);
     return CLBM_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+clbm_status clbm_residual(clbm_handle g, double* res, double cons[6]) {
+    Range nvtx_range("clbm_residual");
+    if (!g) return fail(CLBM_EINVAL, "handle is NULL");
+    double v[NRED];
+    long long dt = 0;
+    clbm_status st = residual_sums(g, v, &dt);
+    if (st != CLBM_OK) return st;
+    double r = INFINITY;
+    if (dt > 0) r = v[1] > 0.0 ? sqrt(v[0]) / (dt * sqrt(v[1])) : (v[0] > 0 ? INFINITY : 0.0);
+    if (res) *res = r;
+    if (cons)
+        for (int k = 0; k < 6; ++k) cons[k] = v[2 + k];
+    return unstable_status(g, v);
+}
+
+clbm_status clbm_residual_parts(clbm_handle g, double parts[9], long long* dt) {
+    Range nvtx_range("clbm_residual_parts");
+    if (!g || !parts || !dt) return fail(CLBM_EINVAL, "NULL argument");
+    double v[NRED];
+    clbm_status st = residual_sums(g, v, dt);
+    if (st != CLBM_OK) return st;
+    for (int k = 0; k < 9; ++k) parts[k] = v[k];
+    return unstable_status(g, v);
+}
+
 
 clbm_status clbm_no_flow_adjust(clbm_handle g, long long nsteps, double* rho_nf) {
     Range nvtx_range("clbm_no_flow_adjust");
@@ -896,6 +1122,7 @@ clbm_status clbm_no_flow_adjust(clbm_handle g, long long nsteps, double* rho_nf)
     d.bc_hi = g->bc_hi;
     d.device = g->device;
     d.stream = g->stream;
+    d.n2_period = g->n2_period;
     clbm_handle nf = nullptr;
     st = clbm_create_grid(&d, &nf);
     if (st != CLBM_OK) return st;
@@ -1121,6 +1348,7 @@ clbm_status clbm_destroy(clbm_handle g) {
     for (cudaEvent_t e : g->gdummy)
         if (e) cudaEventDestroy(e);
     if (g->stage) cudaFree(g->stage);
+    free_pipe(g->pipe);
     if (g->tma) free_tma_maps(g->tma);
     if (g->owns_ws) cudaFree(g->ws);
     delete g;
@@ -1136,6 +1364,7 @@ struct clbm_batch {
     int Q, prec, device;
     cudaStream_t stream;
     int variant;
+    bool cached;                     // variant taken from the tuner's cache at creation
     int phase;                       // time steps taken through the batch, mod 2
     BatchGrid* d_grids;
     std::vector<BatchGrid> h_grids;
@@ -1414,7 +1643,10 @@ clbm_status clbm_batch_create(const clbm_handle* grids, int n, clbm_batch_handle
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(shape_class(b));
-        if (it != g_tune_cache.end()) b->variant = it->second;
+        if (it != g_tune_cache.end()) {
+            b->variant = it->second;
+            b->cached = true;
+        }
     }
     *out = b;
     return CLBM_OK;
@@ -1556,6 +1788,13 @@ clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* m
     return CLBM_OK;
 }
 
+clbm_status clbm_batch_get_variant(clbm_batch_handle b, int* variant, int* cached) {
+    if (!b) return fail(CLBM_EINVAL, "batch is NULL");
+    if (variant) *variant = b->variant;
+    if (cached) *cached = b->cached ? 1 : 0;
+    return CLBM_OK;
+}
+
 clbm_status clbm_batch_launch_count(clbm_batch_handle b, long long* launches) {
     if (!b || !launches) return fail(CLBM_EINVAL, "NULL argument");
     *launches = b->launches;
@@ -1564,7 +1803,8 @@ clbm_status clbm_batch_launch_count(clbm_batch_handle b, long long* launches) {
 
 clbm_status clbm_batch_destroy(clbm_batch_handle b) {
     if (!b) return CLBM_OK;
-    if (!b->g.empty()) cudaSetDevice(b->g[0]->device);
+    // the batch's own copy of the device: its grids may already be gone
+    cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     cudaFree(b->d_grids);

@@ -181,6 +181,11 @@ void launch_rest_mass(int Q, const double* geo, int count, int mult, double rho0
 void launch_scale_volume(int Q, double* geo, const double* rho_nf, int count, double rho0,
                          cudaStream_t stream);
 void launch_row_mean(const double* field, int n1, int n2, double* out, cudaStream_t stream);
+// Halo strips of slabs along q^2 (k_halo.cu): entries per side (D2Q21 12,
+// D2Q9 3) and the pack (unpack = 0) / unpack of one side's strips.
+int halo_entries(int Q);
+void launch_halo(int Q, int prec, void* state, void* buf, long long plane, int ld, int rows, int n2,
+                 int side, int unpack, cudaStream_t stream);
 
 // TMA-staged fused update (k_step_tma.cu): tensor maps of the two state
 // buffers, their construction, and the launch (src = physical source buffer).
