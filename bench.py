@@ -161,6 +161,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_T0 = time.perf_counter()
+
+
+def progress(what):
+    """One line on stderr per finished part of the run (the JSON line goes to stdout)."""
+    print("[bench %.0f s] %s done" % (time.perf_counter() - _T0, what), file=sys.stderr, flush=True)
+
+
 def max_over_ranks(x, dist, device):
     """Largest value of x over all ranks (x itself without a process group)."""
     import torch
@@ -198,9 +206,12 @@ def annulus(wl):
     return Q, prec, n1, n2, e, tau, U0
 
 
-def cpu_baseline(wl, target_s=12.0, max_steps=50):
+def cpu_baseline(wl, target_s=12.0, max_steps=50, parity=True):
     """The FP64 oracle as it stands on this host's cores: MLUPS on the full
-    workload grid, as many whole time steps as fit in about target_s."""
+    workload grid, as many whole time steps as fit in about target_s.  With
+    parity, the same grid is then advanced on the GPU for as many steps from
+    rest and its velocity compared with the oracle's (normwise L2 over every
+    cell: the full-size parity of the timed configuration)."""
     from oracle import oracle as O
     Q, prec, n1, n2, e, tau, U0 = annulus(wl)
     o = O.Grid(Q, n1, n2, O.POLAR, edges=e, bc_lo=O.MOVING, bc_hi=O.NOSLIP)
@@ -213,11 +224,179 @@ def cpu_baseline(wl, target_s=12.0, max_steps=50):
     t0 = time.perf_counter()
     o.step(n)
     dt = time.perf_counter() - t0
-    steps = n
-    return {"value": n1 * n2 * steps / dt / 1e6, "unit": "MLUPS", "cores": O.threads(),
-            "kind": "oracle",
-            "sample": "%d time steps of the full %dx%d D2Q21 FP64 oracle grid (%.1f s), "
-                      "after one untimed step" % (steps, n1, n2, dt)}
+    out = {"value": n1 * n2 * n / dt / 1e6, "unit": "MLUPS", "cores": O.threads(),
+           "kind": "oracle",
+           "sample": "%d time steps of the full %dx%d D2Q%d FP64 oracle grid (%.1f s), "
+                     "after one untimed step" % (n, n1, n2, Q, dt)}
+    if parity:
+        from paper_2301_01868_gb300 import clbm
+        ref = o.moments()
+        g = clbm.Grid(Q, n1, n2, e, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING,
+                      bc_hi=clbm.NOSLIP)
+        g.set_case(tau, 1.0, U0, 0.0)
+        g.step(1 + n)
+        m = g.moments(names=("Ut1", "Ut2"))
+        g.close()
+        num = ((m["Ut1"] - ref["Ut1"]) ** 2 + (m["Ut2"] - ref["Ut2"]) ** 2).sum()
+        den = (ref["Ut1"] ** 2 + ref["Ut2"] ** 2).sum()
+        out["parity"] = {"steps": 1 + n, "velocity_l2_vs_oracle": float(math.sqrt(num / den)),
+                         "what": "whole %dx%d grid from rest, GPU (%s, automatic kernel) against "
+                                 "the oracle after the same steps" % (n1, n2, prec)}
+    return out
+
+
+def steady_accuracy():
+    """L2 velocity errors of the precision ladder at a steady state against
+    the FP64 oracle and the exact profile (Eq. 27): circular Couette on the
+    annulus at N_r = 32, N_theta = 201, tau = 0.8, 6000 steps from rest; the
+    oracle's profile is the committed fixture tests/golden/steady_profiles.txt
+    (written by the oracle; the bench does not run it)."""
+    from paper_2301_01868_gb300 import clbm
+    path = os.path.join(ROOT, "tests", "golden", "steady_profiles.txt")
+    hdr, rows = {}, []
+    with open(path) as f:
+        for ln in f:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            p = ln.split()
+            if p[0].isalpha():
+                hdr[p[0]] = float(p[1])
+            else:
+                rows.append([float(x) for x in p])
+    rows = np.array(rows)
+    nr, nt, tau, uw, steps = (int(hdr["NR"]), int(hdr["NTHETA"]), hdr["TAU"], hdr["UWALL"],
+                              int(hdr["STEPS"]))
+    r_lat, exact, orc = rows[:, 0], rows[:, 1], {21: rows[:, 2], 9: rows[:, 3]}
+    edges = I.polar_edges(1.0, 2.0, nr)
+    sn = math.sin(2.0 * math.pi / nt)
+    U0 = uw / (sn * (1.0 / ((2.0 - 1.0) / nr)))
+    out = []
+    for Q, prec in ((21, "fp64"), (21, "fp32"), (21, "fp16"), (21, "bf16"), (9, "fp64"), (9, "fp32")):
+        g = clbm.Grid(Q, nr, nt, edges, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING,
+                      bc_hi=clbm.NOSLIP)
+        g.set_case(tau, 1.0, U0, 0.0)
+        g.step(steps)
+        u = g.moments(names=("Ut2",))["Ut2"][:, 0] * sn * r_lat
+        g.close()
+        out.append({"lattice": "D2Q%d" % Q, "storage": prec,
+                    "l2_vs_oracle": float(np.linalg.norm(u - orc[Q]) / np.linalg.norm(orc[Q])),
+                    "l2_vs_exact": float(np.linalg.norm(u - exact) / np.linalg.norm(exact)),
+                    "oracle_l2_vs_exact": float(np.linalg.norm(orc[Q] - exact) / np.linalg.norm(exact))})
+    return {"case": "circular Couette, annulus 1 <= r <= 2, N_r=%d, N_theta=%d, tau=%g, "
+                    "%d steps from rest" % (nr, nt, tau, steps), "ladder": out}
+
+
+def _timed_steps(g, torch, stream, steps):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    g.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def precision_records(steps=300):
+    """The other storage types and lattices on the bench grid (annulus
+    1024 x 4096, CR = 0.35): average update launch from CUDA events (graph
+    replays of 10 launches), MLUPS, and the fraction of the measured HBM
+    peak at 2 Q s bytes per cell update."""
+    import torch
+    from paper_2301_01868_gb300 import clbm
+    peak, _ = peaks()
+    out = []
+    for wl in ("circular_couette_d2q21_f16_1024x4096", "circular_couette_d2q21_bf16_1024x4096",
+               "circular_couette_d2q9_fp32_1024x4096", "circular_couette_d2q21_fp64_1024x4096"):
+        Q, prec, n1, n2, e, tau, U0 = annulus(wl)
+        stream = torch.cuda.Stream()
+        g = clbm.Grid(Q, n1, n2, e, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING,
+                      bc_hi=clbm.NOSLIP, stream=stream)
+        g.set_case(tau, 1.0, U0, 0.0)
+        n = steps if prec != "fp64" else 60
+        g.step(n)
+        g.set_profiling(True, period=10)
+        ms = _timed_steps(g, torch, stream, n)
+        kms, kl = g.kernel_time()
+        g.set_profiling(False)
+        g.close()
+        alg = 2 * Q * STORAGE_BYTES[prec] * n1 * n2
+        k_avg = kms / kl if kl else ms / n
+        out.append({"workload": wl, "mlups": n1 * n2 * n / (ms * 1e-3) / 1e6, "kernel_ms_avg": k_avg,
+                    "algorithmic_bytes_per_launch": alg,
+                    "hbm_frac": alg / (k_avg * 1e-3) / 1e9 / peak,
+                    "bound": "FP64 pipe (HBM fraction for reference)" if prec == "fp64" else "hbm"})
+    return out
+
+
+def config_records():
+    """The small configurations, GPU beside the oracle on the same grid:
+    planar Couette (D2Q9 FP64, 16 x 32 cells twice as long as wide, top wall
+    at 0.01, tau = 1, 20000 steps: MLUPS and the L2 error of the final
+    profile against the linear exact one) and the stretched planar
+    Poiseuille ladder (D2Q21 FP64 and FP32, 64x16 .. 512x128, stretch
+    1.02^(64/n1) per cell, g = 1e-6 (64/n1)^2, tau = 0.6: MLUPS over 2000
+    steps).  The oracle is timed on the host cores over a bounded number of
+    steps, and the GPU's velocity after those steps is compared with the
+    oracle's."""
+    import torch
+    from oracle import oracle as O
+    from paper_2301_01868_gb300 import clbm
+    stream = torch.cuda.Stream()
+    out = {}
+    # planar Couette
+    n1, n2 = 16, 32
+    e = I.uniform_edges(n1)
+    g = clbm.Grid(9, n1, n2, e, kind=clbm.PLANAR, step2=2.0, precision="fp64", bc_lo=clbm.NOSLIP,
+                  bc_hi=clbm.MOVING, stream=stream)
+    g.set_case(1.0, 1.0, 0.0, 0.005)
+    ms = _timed_steps(g, torch, stream, 20000)
+    u = 2.0 * g.moments(names=("Ut2",))["Ut2"][:, 0]
+    g.close()
+    ex = 0.01 * (np.arange(n1) + 0.5) / n1
+    o = O.Grid(9, n1, n2, O.PLANAR, edges=e, step2=2.0, bc_lo=O.NOSLIP, bc_hi=O.MOVING)
+    o.set_case(1.0, 1.0, 0.0, 0.005)
+    o.init_rest()
+    t0 = time.perf_counter()
+    o.step(2000)
+    dto = time.perf_counter() - t0
+    g2 = clbm.Grid(9, n1, n2, e, kind=clbm.PLANAR, step2=2.0, precision="fp64", bc_lo=clbm.NOSLIP,
+                   bc_hi=clbm.MOVING, stream=stream)
+    g2.set_case(1.0, 1.0, 0.0, 0.005)
+    g2.step(2000)
+    ug, uo = g2.moments(names=("Ut2",))["Ut2"], o.moments()["Ut2"]
+    g2.close()
+    out["planar_couette_d2q9_fp64_16x32"] = {
+        "gpu_mlups": n1 * n2 * 20000 / (ms * 1e-3) / 1e6, "steps": 20000,
+        "l2_vs_exact": float(np.linalg.norm(u - ex) / np.linalg.norm(ex)),
+        "oracle_mlups": n1 * n2 * 2000 / dto / 1e6, "oracle_cores": O.threads(), "oracle_steps": 2000,
+        "l2_vs_oracle_at_oracle_steps": float(np.linalg.norm(ug - uo) / np.linalg.norm(uo))}
+    # stretched planar Poiseuille ladder
+    tau = 0.6
+    nu = (2.0 / 3.0) * (tau - 0.5)
+    for (n1, n2) in ((64, 16), (128, 32), (256, 64), (512, 128)):
+        e = I.geometric_stretch_edges(n1, 1.02 ** (64.0 / n1), float(n1))
+        gacc = 1e-6 * (64.0 / n1) ** 2
+        rec = {"stretch_per_cell": 1.02 ** (64.0 / n1), "g": gacc}
+        osteps = 2000 if n1 <= 128 else 200
+        o = O.Grid(21, n1, n2, O.PLANAR, edges=e, step2=1.0)
+        o.set_case(tau, 1.0, 0.0, 0.0, (0.0, gacc))
+        o.init_rest()
+        t0 = time.perf_counter()
+        o.step(osteps)
+        dto = time.perf_counter() - t0
+        uo = o.moments()["Ut2"]
+        rec.update(oracle_mlups=n1 * n2 * osteps / dto / 1e6, oracle_cores=O.threads(), oracle_steps=osteps)
+        for prec in ("fp64", "fp32"):
+            g = clbm.Grid(21, n1, n2, e, kind=clbm.PLANAR, step2=1.0, precision=prec, stream=stream)
+            g.set_case(tau, 1.0, 0.0, 0.0, (0.0, gacc))
+            g.step(osteps)
+            ug = g.moments(names=("Ut2",))["Ut2"]
+            ms = _timed_steps(g, torch, stream, 2000)
+            g.close()
+            rec[prec] = {"gpu_mlups": n1 * n2 * 2000 / (ms * 1e-3) / 1e6,
+                         "l2_vs_oracle_at_oracle_steps": float(np.linalg.norm(ug - uo) / np.linalg.norm(uo))}
+        out["planar_poiseuille_d2q21_%dx%d" % (n1, n2)] = rec
+    return out
 
 
 def run_reference(args):
@@ -241,6 +420,8 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = n1 * n2 * args.steps / dt / 1e6
     cfg = config_of(wl, args)
+    cfg.update(n1=n1, n2=n2, sample_of="%dx%d" % WORKLOADS[wl][2:4],
+               l2="oracle on the host (no GPU)")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -285,8 +466,10 @@ def main():
                          "3 TMA-staged warp-specialised pipeline")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving comparison (continuous batching vs serial solves)")
-    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the accuracy, precision, batch and small-configuration records")
     ap.add_argument("--batch", action="store_true",
                     help="only the batched form against per-lattice launches (512 lattices)")
     ap.add_argument("--batch-lattices", type=int, default=512)
@@ -387,13 +570,28 @@ def main():
            "data": "synthetic", "config": config_of(wl, args), "roofline": roof,
            "gpu_launches": launches, "clocks": ck, "e2e": e2e,
            "residual_last": last[0] if last else None}
+    g.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not general:
         out["cpu_baseline"] = cpu_baseline(wl)
+        progress("cpu baseline")
+    if rank == 0 and world == 1 and not args.no_extras:
+        out["accuracy"] = steady_accuracy()
+        if "cpu_baseline" in out:
+            out["accuracy"]["full_grid"] = out["cpu_baseline"].get("parity")
+        progress("accuracy")
+        if wl == DEFAULT:
+            out["precisions"] = precision_records()
+            progress("precisions")
+            out["batch"] = batch_record()
+            progress("batch")
+            if not args.no_cpu_baseline:
+                out["configs"] = config_records()
+                progress("configs")
     if rank == 0 and world == 1 and not args.no_serve:
         out["serving"] = run_serving(args.serve_requests)
+        progress("serving")
     if rank == 0:
         print(json.dumps(out))
-    g.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -483,34 +681,92 @@ def run_3d(args):
     g.close()
 
 
-def run_serving(n, verbose=False):
-    """Served solves/s and time-to-converged: a seeded Poisson stream of solve
-    requests (the four flows, D2Q9 / D2Q21 at random, sizes log-uniform on a
-    scaled ladder 8..32 x 8..64, tau in [0.55, 1], target speed in
-    [1e-3, 1e-2], residual tolerance 1e-8, FP32 state, 150 GB budget) through
-    the continuous-batching server and, as the baseline, the same requests
-    solved one after another with single-lattice launches."""
-    from paper_2301_01868_gb300 import serve
-    rate = 200.0
-    kw = dict(n1_range=(8, 32), n2_range=(8, 64), tol=1e-8, max_steps=150000)
+def _fifo_latencies(reqs, service):
+    """Time-to-done of one FIFO server with the given service times at the
+    requests' arrival times (the serial baseline at any arrival rate, from
+    its service times measured once)."""
+    t_free = 0.0
+    out = []
+    for r in sorted(reqs, key=lambda q: q.arrival):
+        start = max(r.arrival, t_free)
+        t_free = start + service[r.rid]
+        out.append((r.rid, t_free - r.arrival, t_free))
+    return out
+
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+LADDER = dict(n1_range=(8, 256), n2_range=(8, 512), tol=1e-8, max_steps=30000)
+LITERAL = dict(n1_range=(64, 2048), n2_range=(64, 4096), tol=1e-8, max_steps=500)
+
+
+def run_serving(n=48, rates=(0.5, 0.8, 1.2), literal_n=64, verbose=False):
+    """Served solves/s and time-to-converged (continuous batching against
+    serial single-lattice solves), on seeded Poisson streams of solve
+    requests: the four flows, D2Q9 / D2Q21 at random, tau in [0.55, 1],
+    target speed in [1e-3, 1e-2], residual tolerance 1e-8, FP32 state with
+    FP64 residuals.
+
+    ladder: n1 log-uniform 8..256 (circular n2 = round(2 pi n1), planar n2
+      log-uniform 8..512), a cap of 30,000 steps per request.  The serial
+      path solves the stream once, back to back: its capacity C (solves/s)
+      and each request's service time.  The server then takes the same
+      requests at Poisson rates of 0.5, 0.8 and 1.2 C, with an HBM budget of
+      30 % of the stream's total workspace so that admission binds; the
+      serial latencies at each rate follow from its measured service times
+      (one FIFO server at the same arrivals).
+    literal: a sample of the configured distribution (n1 log-uniform
+      64..2048, n2 64..4096, circular n2 from n1 as above) all queued at
+      once under the configured 150 GB budget, each capped at 500 steps (a
+      literal request needs up to ~3e7 steps to converge): the server's
+      solves/s and the converged / capped / diverged counts."""
+    from paper_2301_01868_gb300 import clbm, serve
+    t_start = time.perf_counter()
+    base = serve.poisson_requests(n, 0.0, **LADDER)
+    done_serial, serial = serve.serve_serial(base, precision="fp32", chunk=100)
+    service = {d["rid"]: d["service"] for d in done_serial}
+    status_serial = {d["rid"]: d["status"] for d in done_serial}
+    cap = n / sum(service.values())
+    need = [clbm.workspace_bytes(r.lattice, clbm.FP32, r.n1, r.n2) for r in base]
+    budget = 1.5 * max(need)      # two of the largest lattices never fit at once
+    sweep = []
+    for f in rates:
+        reqs = serve.poisson_requests(n, f * cap, **LADDER)
+        srv = serve.Server(precision="fp32", hbm_budget=budget, chunk=100)
+        for r in reqs:
+            srv.submit(r)
+        st = srv.run()
+        fifo = _fifo_latencies(reqs, service)
+        conv_lat = [lat for rid, lat, _ in fifo if status_serial[rid] == "converged"]
+        span = max(t for _, _, t in fifo)
+        differ = sum(1 for d in srv.done if d["status"] != status_serial[d["rid"]])
+        sweep.append({"rate_x_serial_capacity": f, "arrival_rate_per_s": f * cap,
+                      "batched": st,
+                      "serial": {"solves_per_s": n / span,
+                                 "converged_per_s": sum(v == "converged" for v in status_serial.values()) / span,
+                                 "p50_s": _pct(conv_lat, 50), "p99_s": _pct(conv_lat, 99)},
+                      "status_differs": differ})
+        if verbose:
+            print(json.dumps(sweep[-1]), file=sys.stderr)
+    lit = serve.poisson_requests(literal_n, 0.0, seed=20230106, **LITERAL)
     srv = serve.Server(precision="fp32", hbm_budget=150e9, chunk=100)
-    for r in serve.poisson_requests(n, rate, **kw):
+    for r in lit:
         srv.submit(r)
-    batched = srv.run()
-    reqs = serve.poisson_requests(n, rate, **kw)
-    done_serial, serial = serve.serve_serial(reqs, precision="fp32", chunk=100)
-    st_b = {d["rid"]: d["status"] for d in srv.done}
-    differ = [{"rid": r.rid, "case": r.case, "lattice": r.lattice, "n1": r.n1, "n2": r.n2,
-               "batched": st_b[r.rid], "serial": d["status"]}
-              for r, d in zip(sorted(reqs, key=lambda q: q.arrival), done_serial)
-              if st_b[r.rid] != d["status"]]
-    out = {"requests": n, "arrival_rate_per_s": rate,
-           "ladder": "n1 8..32, n2 8..64 log-uniform (circular: n2 = round(2 pi n1)); tol 1e-8; "
-                     "cap 150000 steps",
-           "batched": batched, "serial": serial, "status_differs": differ,
-           "speedup_solves_per_s": batched["solves_per_s"] / serial["solves_per_s"],
-           "speedup_converged_per_s": (batched["converged_per_s"] / serial["converged_per_s"]
-                                       if serial["converged_per_s"] > 0 else None)}
+    literal = srv.run()
+    literal["cells_per_request_mean"] = float(np.mean([r.n1 * r.n2 for r in lit]))
+    mid = sweep[len(sweep) // 2]
+    out = {"requests_per_rate": n,
+           "ladder": "n1 8..256 log-uniform (circular n2 = round(2 pi n1), planar n2 8..512); "
+                     "tol 1e-8; cap 30000 steps; HBM budget 1.5 x the largest request's workspace",
+           "serial_capacity_solves_per_s": cap, "serial": serial, "budget_bytes": budget,
+           "sweep": sweep,
+           "speedup_solves_per_s_at_0.8": mid["batched"]["solves_per_s"] / mid["serial"]["solves_per_s"],
+           "literal": dict(literal, requests=literal_n,
+                           distribution="n1 64..2048, n2 64..4096 log-uniform (circular n2 = round(2 pi n1)); "
+                                        "tol 1e-8; cap 500 steps; 150 GB budget; all queued at t = 0"),
+           "wall_s": time.perf_counter() - t_start}
     return out
 
 
@@ -534,15 +790,18 @@ def batch_requests(n, seed=20230105):
     return out
 
 
-def run_batch(args):
-    """--batch: the batched form against per-lattice launches on the same
-    lattices (MLUPS over all lattices, K timed steps each, after warm-up;
-    the batch's tile variant from its autotuner)."""
+def batch_record(n_lattices=512, steps=20, warmup=3, verbose=False):
+    """The batched form against per-lattice launches on the same lattices:
+    MLUPS over all lattices for `steps` timed steps after warm-up, the
+    batch's update variant from its autotuner, and the roofline of the
+    batched update (168 B per cell update, D2Q21 FP32) from CUDA events
+    around the timed steps (one persistent launch per time step, replayed two
+    steps per CUDA graph)."""
     import torch
     from paper_2301_01868_gb300 import clbm, serve
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    reqs = batch_requests(args.batch_lattices)
+    reqs = batch_requests(n_lattices)
     t0 = time.perf_counter()
     grids = [serve.build_grid(r, clbm.FP32, stream) for r in reqs]
     setup_s = time.perf_counter() - t0
@@ -551,99 +810,98 @@ def run_batch(args):
     b = clbm.Batch(grids)
     best, ms = b.tune(steps=2)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    b.step(args.warmup)
+    b.step(warmup)
     torch.cuda.synchronize()
     l0 = b.launch_count()
     ev0.record(stream)
-    b.step(args.steps)
+    b.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     t_b = ev0.elapsed_time(ev1)
     l_b = b.launch_count() - l0
     b.close()
     for g in grids:
-        g.step(args.warmup)
+        g.step(warmup)
     torch.cuda.synchronize()
     ev0.record(stream)
     for g in grids:
-        g.step(args.steps)
+        g.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     t_l = ev0.elapsed_time(ev1)
     for g in grids:
         g.close()
-    out = {"metric": "batched MLUPS (all lattices)", "unit": "MLUPS", "lattices": len(reqs),
-           "cells": cells, "workspace_bytes": ws, "steps": args.steps, "warmup": args.warmup,
-           "setup_s": setup_s, "tuned_variant": int(best), "variant_ms_per_step": list(map(float, ms)),
-           "batched": {"value": cells * args.steps / (t_b * 1e-3) / 1e6, "ms": t_b, "launches": l_b},
-           "per_lattice": {"value": cells * args.steps / (t_l * 1e-3) / 1e6, "ms": t_l,
-                           "launches": len(reqs) * args.steps},
-           "config": {"workload": "batched_512_d2q21_fp32", "lattice": "D2Q21", "storage": "fp32",
-                      "shapes": "planar n1 32..1024 x n2 32..2048; circular n2 32..2048, "
-                                "n1 = n2 / 2 pi", "tau": "U[0.55, 1]"},
-           "data": "synthetic"}
-    print(json.dumps(out))
+    peak, peak_src = peaks()
+    alg = 2 * 21 * 4 * cells
+    achieved = alg / (t_b / steps * 1e-3) / 1e9
+    return {"metric": "batched MLUPS (all lattices)", "unit": "MLUPS", "lattices": len(reqs),
+            "cells": cells, "workspace_bytes": ws, "steps": steps, "warmup": warmup,
+            "setup_s": setup_s, "tuned_variant": int(best),
+            "variant_ms_per_step": list(map(float, ms)),
+            "batched": {"value": cells * steps / (t_b * 1e-3) / 1e6, "ms": t_b, "launches": l_b},
+            "per_lattice": {"value": cells * steps / (t_l * 1e-3) / 1e6, "ms": t_l,
+                            "launches": len(reqs) * steps},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src + " (hbm_gbs)",
+                         "algorithmic_bytes_per_step": alg,
+                         "timed": "whole batched time step (graph replays of two steps)"},
+            "config": {"workload": "batched_%d_d2q21_fp32" % len(reqs), "lattice": "D2Q21",
+                       "storage": "fp32",
+                       "shapes": "case uniform over the four flows; planar n1 32..1024 x n2 "
+                                 "32..2048; circular n2 32..2048 with n1 = round(n2 / 2 pi) "
+                                 "(near-square cells at the inner wall)",
+                       "tau": "U[0.55, 1]", "steps_configured": 5000,
+                       "steps_timed": steps},
+            "data": "synthetic"}
+
+
+def run_batch(args):
+    """--batch: only the batched record, printed as one JSON line."""
+    print(json.dumps(batch_record(args.batch_lattices, args.steps, max(3, args.warmup))))
 
 
 def run_e2e(g, args, torch, stream, world, dist, cells, Q, inputs="state"):
     """Same metric through the public API with host buffers.  Every step
     uploads that step's inputs from pinned host memory, advances `chunk` time
     steps and reads the moments rho, Ut^1, Ut^2 back into pinned host memory.
-    inputs "state" (the default): the full FP64 N' (clbm_set_state, Q values
-    per cell), pipelined -- a copy stream uploads step k+1's input into a
-    second device buffer and downloads step k-1's moments while step k
-    computes, so each step's copies stay inside the timed region but overlap
-    the update; "state_serial": the same copies one after another with the
-    compute (host buffers passed to clbm_set_state / clbm_moments);
+    inputs "state" (the default): the full FP64 N' through the library's
+    asynchronous host copies (clbm_upload_state_async / clbm_set_uploaded_state
+    / clbm_download_moments_async / clbm_wait_copies): the library's copy
+    stream uploads step k + 1's state and downloads step k - 1's moments
+    while step k computes, so every copy stays inside the timed region but
+    overlaps the update; "state_serial": the same copies one after another
+    with the compute (clbm_set_state / clbm_moments with host buffers);
     "fields": the macroscopic start rho, U^1, U^2 (clbm_set_equilibrium, 3
     FP64 values per cell; fewer bytes, but the FP64 equilibrium on the device
-    costs more than the saved transfer: 21,061 against 25,403 MLUPS serially
-    on the 1024 x 4096 annulus)."""
+    costs more than the saved transfer)."""
     n1, n2 = g.n1, g.n2
     names = ("rho", "Ut1", "Ut2")
-    if inputs == "state":
-        host_state = torch.empty((Q, n1, n2), dtype=torch.float64, pin_memory=True)
-        host_state.copy_(g.state(device=True).cpu())
-        dev_in = [torch.empty((Q, n1, n2), dtype=torch.float64, device=g.device) for _ in range(2)]
-        dev_out = [{k: torch.empty((n1, n2), dtype=torch.float64, device=g.device) for k in names}
-                   for _ in range(2)]
-        host_out = [{k: torch.empty((n1, n2), dtype=torch.float64, pin_memory=True) for k in names}
-                    for _ in range(2)]
-        cs = torch.cuda.Stream(device=g.device)
-        up_ev = [torch.cuda.Event() for _ in range(2)]
-        dl_ev = [torch.cuda.Event() for _ in range(2)]
-        dl_pending = [False, False]
 
-        def upload(k):
-            with torch.cuda.stream(cs):
-                dev_in[k % 2].copy_(host_state, non_blocking=True)
-                up_ev[k % 2].record(cs)
+    def pinned(shape):
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+
+    if inputs == "state":
+        host_state = pinned((Q, n1, n2))
+        host_state[...] = g.state()
+        host_out = [{k: pinned((n1, n2)) for k in names} for _ in range(2)]
 
         def run(nsteps):
-            upload(0)
+            g.upload_state_async(host_state)
+            if nsteps > 1:
+                g.upload_state_async(host_state)
             for k in range(nsteps):
-                b = k % 2
-                stream.wait_event(up_ev[b])
-                g.set_state(dev_in[b])                  # converts on the grid's stream; synchronises it
-                if k + 1 < nsteps:
-                    upload(k + 1)                       # overlaps this step's update
+                g.set_uploaded_state()
+                if k + 2 < nsteps:
+                    g.upload_state_async(host_state)     # overlaps this step's update
                 g.step(args.chunk)
-                if dl_pending[b]:
-                    stream.wait_event(dl_ev[b])         # step k-2's download has read this buffer
-                g.moments(device=True, names=names, out=dev_out[b])   # synchronises the grid's stream
-                with torch.cuda.stream(cs):
-                    for nm in names:
-                        host_out[b][nm].copy_(dev_out[b][nm], non_blocking=True)
-                    dl_ev[b].record(cs)
-                dl_pending[b] = True
-            cs.synchronize()
+                g.download_moments_async(host_out[k % 2])   # overlaps the next update
+            g.wait_copies()
         h2d = Q * cells * 8
     else:
-        pinned = {k: torch.empty((n1, n2), dtype=torch.float64, pin_memory=True).numpy() for k in names}
+        out = {k: pinned((n1, n2)) for k in names}
         if inputs == "state_serial":
-            host_state = torch.empty((Q, n1, n2), dtype=torch.float64, pin_memory=True)
-            host_state.copy_(g.state(device=True).cpu())
-            state_np = host_state.numpy()
+            state_np = pinned((Q, n1, n2))
+            state_np[...] = g.state()
 
             def upload():
                 g.set_state(state_np)
@@ -652,7 +910,7 @@ def run_e2e(g, args, torch, stream, world, dist, cells, Q, inputs="state"):
             m = g.moments(names=("rho", "U1", "U2"))
             fields = []
             for k in ("rho", "U1", "U2"):
-                f = torch.empty((n1, n2), dtype=torch.float64, pin_memory=True).numpy()
+                f = pinned((n1, n2))
                 f[...] = m[k]
                 fields.append(f)
 
@@ -664,7 +922,7 @@ def run_e2e(g, args, torch, stream, world, dist, cells, Q, inputs="state"):
             for _ in range(nsteps):
                 upload()
                 g.step(args.chunk)
-                g.moments(names=names, out=pinned)
+                g.moments(names=names, out=out)
 
     run(1)
     torch.cuda.synchronize()
@@ -674,14 +932,16 @@ def run_e2e(g, args, torch, stream, world, dist, cells, Q, inputs="state"):
     run(args.steps)
     torch.cuda.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-    what = {"state": "state upload (FP64 N' through clbm_set_state from a device buffer that a copy stream "
-                     "fills from pinned host memory while the previous step computes)",
-            "state_serial": "state upload (FP64 N' from pinned host memory through clbm_set_state)",
+    what = {"state": "FP64 N' uploaded from pinned host memory by the library's copy stream while the "
+                     "previous step computes (clbm_upload_state_async, clbm_set_uploaded_state)",
+            "state_serial": "FP64 N' from pinned host memory through clbm_set_state, in series",
             "fields": "macroscopic start (FP64 rho, U^1, U^2 through clbm_set_equilibrium)"}[inputs]
+    down = ("moments (FP64 rho, Ut^1, Ut^2) downloaded by the library's copy stream while the next "
+            "step computes (clbm_download_moments_async, clbm_wait_copies)" if inputs == "state"
+            else "moments (FP64 rho, Ut^1, Ut^2) through clbm_moments into pinned host memory")
     return {"value": cells * args.chunk * args.steps * world / dt / 1e6, "unit": "MLUPS",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 3 * cells * 8,
-            "note": "per step: %s, %d time steps, moments download (FP64 rho, Ut^1, Ut^2)"
-                    % (what, args.chunk)}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 3 * cells * 8, "inputs": inputs,
+            "note": "per step: %s, %d time steps, %s" % (what, args.chunk, down)}
 
 
 if __name__ == "__main__":

@@ -60,3 +60,24 @@ def test_single_process_needs_no_group():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+
+
+def test_serial_fifo_latencies_from_service_times():
+    """The serial baseline at a given arrival rate: one FIFO server fed the
+    measured service times (start = max(arrival, previous finish))."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+
+    class R:
+        def __init__(self, rid, arrival):
+            self.rid, self.arrival = rid, arrival
+
+    reqs = [R(0, 0.0), R(1, 0.5), R(2, 3.0), R(3, 3.1)]
+    service = {0: 1.0, 1: 1.0, 2: 0.2, 3: 0.5}
+    out = {rid: (lat, t) for rid, lat, t in bench._fifo_latencies(reqs, service)}
+    assert out[0] == (1.0, 1.0)
+    assert out[1] == (1.5, 2.0)          # waits for request 0
+    assert abs(out[2][0] - 0.2) < 1e-12 and abs(out[2][1] - 3.2) < 1e-12   # server idle at 3.0
+    assert abs(out[3][0] - 0.6) < 1e-12 and abs(out[3][1] - 3.7) < 1e-12

@@ -30,6 +30,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"] == "circular_couette_d2q21_fp32_1024x4096"
+    # the grid the oracle actually ran, a bounded sample of the workload's
+    assert (d["config"]["n1"], d["config"]["n2"]) == (128, 512)
 
 
 def test_reference_arm_other_ranks_stay_silent():
