@@ -294,7 +294,10 @@ clbm_status clbm_launch_count(clbm_handle h, long long* launches);
  * array of 8192 * 3 + 3 doubles (196 632 bytes) that every GPU which loads
  * the library keeps until exit, so n1 * n2 may not exceed 2 097 152 (larger
  * grids get CLBM_EINVAL).  The first call on each device looks up that
- * array's device address; make that first call before any stream capture.
+ * array's device address, and so does the first call after the device's
+ * context changed (a cudaDeviceReset loads the module again); make such a
+ * call before any stream capture.  A CUDA error already pending when the
+ * call starts is reported (CLBM_ECUDA) and left in place.
  * All calls share the scratch: calls that overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller. */
 clbm_status clbm_totals_noalloc(int lattice, const double* Np, int n1, int n2, double* out,

@@ -26,6 +26,30 @@ static __device__ __align__(256) double g_na_scratch[NA_MAX_BLOCKS * 3 + 3];
 
 std::mutex g_na_mu;
 double* g_na_ptr[64] = {nullptr};  // device address of g_na_scratch, per device
+void* g_na_ctx[64] = {nullptr};    // the context that address belongs to
+
+// The calling thread's current context (the driver's cuCtxGetCurrent, found
+// through the runtime so the library needs no link to the driver library);
+// nullptr when it cannot be asked.  A device reset or a new primary context
+// loads the module again, and the array's address with it, so the address
+// is resolved again whenever the context differs from the one it came from.
+void* current_context() {
+    using Fn = int (*)(void**);
+    static Fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (Fn)f;
+        tried = true;
+    }
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 template <int Q>
 __global__ void __launch_bounds__(NA_THREADS) k_totals_partial(const double* __restrict__ Np,
@@ -103,18 +127,30 @@ extern "C" clbm_status clbm_totals_noalloc(int lattice, const double* Np, int n1
         set_last_error("clbm_totals_noalloc: no current CUDA device");
         return CLBM_ECUDA;
     }
+    // an error left by earlier work is not this call's: report it, untouched
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        char msg[200];
+        snprintf(msg, sizeof(msg), "clbm_totals_noalloc: an earlier CUDA error is pending: %s",
+                 cudaGetErrorString(pending));
+        set_last_error(msg);
+        return CLBM_ECUDA;
+    }
     double* scratch = nullptr;
     {
-        // First call on a device: resolve the device address of the static
-        // scratch (host code may not use the symbol itself as a pointer).
+        // First call on a device (or in a new context of it): resolve the
+        // device address of the static scratch (host code may not use the
+        // symbol itself as a pointer).
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ptr[dev]) {
+        void* ctx = current_context();
+        if (!g_na_ptr[dev] || ctx != g_na_ctx[dev] || !ctx) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
                 set_last_error("clbm_totals_noalloc: cudaGetSymbolAddress failed");
                 return CLBM_ECUDA;
             }
             g_na_ptr[dev] = (double*)p;
+            g_na_ctx[dev] = ctx;
         }
         scratch = g_na_ptr[dev];
     }

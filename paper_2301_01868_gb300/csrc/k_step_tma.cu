@@ -88,7 +88,10 @@ struct PipeGeom {
     // configuration keeps about the same bytes on their way from HBM per SM
     static constexpr int FIT = (220 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = FIT > 8 ? 8 : (FIT < 2 ? 2 : FIT);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16 + 128;
+    // per stage, a slot for the tile's descriptor when the producer publishes
+    // it (batches: the lattice a tile belongs to comes from global memory)
+    static constexpr int TILE_SLOT = 256;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16 + STAGES * TILE_SLOT + 128;
     static_assert(SMEM + 2048 <= 227 * 1024, "pipeline stages exceed shared memory");
 };
 
@@ -380,15 +383,25 @@ __device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0,
 // an error, stops the other warps at their next wait, and lets the loads in
 // flight land before the CTA exits.  Every thread returns (the producer warp
 // first), so a caller may follow with CTA-wide work.
-template <int Q, typename S, typename C, typename TileOf, typename CellFn>
+//
+// PUBLISH: the producer alone calls tile_of and stores the tile it returns in
+// the stage's shared-memory slot before it issues the loads (the arrive that
+// starts the stage's transaction count releases that store; the consumers'
+// wait on the full barrier acquires it), and the consumers read the tile from
+// there -- for tiles whose description sits in global memory (batches),
+// which every consumer would otherwise fetch, with its latency, at every tile.
+template <int Q, typename S, typename C, bool PUBLISH = false, typename TileOf, typename CellFn>
 __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_of, CellFn&& cell) {
     using G = TileGeom<Q, S>;
     using P = PipeGeom<Q, S>;
+    using Tile = decltype(tile_of(0, 0));
+    static_assert(sizeof(Tile) <= P::TILE_SLOT, "tile descriptor exceeds its shared-memory slot");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* const smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     uint64_t* const full = (uint64_t*)(smem + P::STAGES * P::STAGE_BYTES);
     uint64_t* const empty = full + P::STAGES;
     volatile int* const s_abort = (volatile int*)(empty + P::STAGES);
+    Tile* const slots = (Tile*)(smem + P::STAGES * P::STAGE_BYTES + 2 * P::STAGES * 8 + 16);
     auto stage_in = [&](int st) { return smem + st * P::STAGE_BYTES; };
     auto stage_tab = [&](int st) { return smem + st * P::STAGE_BYTES + P::IN_BYTES; };
 
@@ -414,7 +427,8 @@ __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_
                     break;
                 }
                 if (*s_abort) break;
-                const auto t = tile_of(tile, it);
+                const Tile t = tile_of(tile, it);
+                if (PUBLISH) slots[st] = t;
                 ws_issue<Q, S, C>(t.ld8, t.i0, t.j0, t.lat.n1, t.tab, stage_in(st), stage_tab(st),
                                   &full[st]);
             }
@@ -435,8 +449,13 @@ __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_
             break;
         }
         if (*s_abort) break;
-        const auto t = tile_of(tile, it);
-        cell(t, (const S*)stage_in(st), (const C*)stage_tab(st), r, cc);
+        if (PUBLISH) {
+            const Tile t = slots[st];
+            cell(t, (const S*)stage_in(st), (const C*)stage_tab(st), r, cc);
+        } else {
+            const Tile t = tile_of(tile, it);
+            cell(t, (const S*)stage_in(st), (const C*)stage_tab(st), r, cc);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
     }
@@ -537,7 +556,7 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     k_batch_ws(const BatchGrid* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                const int4* __restrict__ work, int nwork, int parity, int* err) {
     const CUtensorMap* fenced = nullptr;  // producer: maps acquired last
-    ws_pipeline<Q, S, C>(nwork, err, [&](int e, int) {
+    ws_pipeline<Q, S, C, true>(nwork, err, [&](int e, int) {
         const int4 w = work[e];
         const BatchGrid& g = grids[w.x];
         const int src = g.parity ^ parity;

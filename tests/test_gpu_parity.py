@@ -9,7 +9,8 @@ Tolerances (normwise relative L2 over all cells):
   coarse for this method; the precision ladder reports it, it is no default).
 Cases that start from j-dependent random perturbations run at most 200 steps
 on cells of aspect ratio near one: the D2Q21 equilibrium amplifies
-j-dependent modes on anisotropic cells (recorded in the design doc), so only
+j-dependent modes on anisotropic cells (a property of the method that the
+oracle shares: tests/test_oracle_stability.py), so only
 j-invariant states are run for 1000 steps on those grids.
 """
 import math
