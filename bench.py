@@ -42,6 +42,9 @@ WORKLOADS = {
     "circular_couette_d2q21_fp64_1024x4096": (21, "fp64", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
     "circular_couette_d2q9_fp32_1024x4096": (9, "fp32", 1024, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
     "circular_couette_d2q21_fp32_128x512": (21, "fp32", 128, 512, 1.0, 2.0, 0.35, 0.8, 0.01),
+    # half the bench grid: the case ncu's full captures run on (state 2 x 176 MB, above L2)
+    "circular_couette_d2q21_fp32_512x4096": (21, "fp32", 512, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
+    "circular_couette_d2q21_f16_512x4096": (21, "fp16", 512, 4096, 1.0, 2.0, 0.35, 0.8, 0.01),
 }
 # general (non-separable) grids: name -> (Q, precision, n1, n2, amplitude, tau, u_wall)
 GENERAL_WORKLOADS = {
@@ -443,7 +446,8 @@ def config_of(wl, args):
     return {"workload": wl, "lattice": "D2Q%d" % Q, "n1": n1, "n2": n2, "geometry": geom,
             "tau": tau, "u_wall": uw,
             "storage": prec, "chunk": args.chunk,
-            "kernel": {0: "auto", 1: "per-cell", 2: "tma-tiles", 3: "tma-pipeline"}[args.kernel],
+            "kernel": {0: "auto", 1: "per-cell", 2: "tma-tiles", 3: "tma-pipeline",
+                       4: "tma-pipeline, two cells per thread"}[args.kernel],
             "l2": "inputs larger than L2 (state %d MB)" % (2 * Q * n1 * n2 * STORAGE_BYTES[prec] >> 20),
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -463,7 +467,8 @@ def main():
                          "the previous step (default), the same copies in series, or the macroscopic fields")
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one thread per cell, 2 TMA-staged tiles, "
-                         "3 TMA-staged warp-specialised pipeline")
+                         "3 TMA-staged warp-specialised pipeline, 4 the same with two cells per "
+                         "thread in packed arithmetic")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving comparison (continuous batching vs serial solves)")
     ap.add_argument("--serve-requests", type=int, default=48)

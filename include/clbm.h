@@ -269,14 +269,18 @@ clbm_status clbm_set_stream(clbm_handle h, void* stream);
 clbm_status clbm_set_profiling(clbm_handle h, int period);
 clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
 
-/* Kernel of the bulk update: 0 automatic (variant 3 where available, else 1;
- * general grids: 1), 1 one thread per cell with direct loads, 2 TMA-staged
- * tiles with a shared output tile (planar and polar grids), 3 TMA-staged
- * tiles in a warp-specialised pipeline (general grids: the state staged, the
- * per-cell tables read by the consumers) (2 and 3: FP32 / FP16 / BF16
+/* Kernel of the bulk update: 0 automatic (general grids: 1; planar and polar
+ * grids with TMA maps: 4 for FP16 / BF16 storage, 3 for FP32; else 1), 1 one
+ * thread per cell with direct loads, 2 TMA-staged tiles with a shared output
+ * tile (planar and polar grids), 3 TMA-staged tiles in a warp-specialised
+ * pipeline (general grids: the state staged, the per-cell tables read by the
+ * consumers), 4 the same pipeline with two neighbouring cells per thread in
+ * packed FP32 arithmetic (planar and polar grids) (2-4: FP32 / FP16 / BF16
  * storage and rows of at least 16 bytes; the implicit-force passes always
- * use variant 1).  All run the same arithmetic.  CLBM_EINVAL for a variant
- * the grid cannot use. */
+ * use variant 1).  All run the same update; the packed form rounds each lane
+ * as the scalar form but may contract a different multiply-add pairing, so
+ * FP32 results agree to rounding, not bit for bit.  CLBM_EINVAL for a
+ * variant the grid cannot use. */
 clbm_status clbm_set_kernel(clbm_handle h, int variant);
 
 /* Number of kernel launches this grid has issued since creation. */

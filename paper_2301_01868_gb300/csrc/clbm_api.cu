@@ -205,6 +205,19 @@ StepArgs step_args(const clbm_grid* g, const void* src, void* dst) {
 // grids only.
 bool general_grid(const clbm_grid* g) { return g->ncol > 1; }
 
+// Which TMA-staged update a planar or polar grid runs: kernel 2 the tiles
+// with a shared output tile, 3 the pipeline, 4 the pipeline with two cells
+// per thread; automatic: the two-cell pipeline for 16-bit storage (bound by
+// instruction issue there, it executes 29 % fewer instructions: 105.7 us
+// against 110.9 us per launch on the 1024 x 4096 annulus) and the one-cell
+// pipeline for FP32 (bound by HBM, where the two-cell form's fewer resident
+// warps cost more than its instructions save: 133 us against 116 us).
+int tma_mode(const clbm_grid* g) {
+    if (g->variant == 2) return 0;
+    if (g->variant == 4 || (g->variant == 0 && g->prec >= 2)) return 2;
+    return 1;
+}
+
 bool use_tma(const clbm_grid* g) {
     if (!g->tma || g->cs.force_iterations > 0) return false;
     if (general_grid(g)) return g->variant == 3;
@@ -666,7 +679,7 @@ static clbm_status launch_update(clbm_grid* g, const StepArgs& a) {
         const int src = a.src == g->phys[0] ? 0 : 1;
         const int rc = general_grid(g)
                            ? launch_step_tma_general(g->Q, g->prec, *g->tma, a, src, g->nsm, g->stream)
-                           : launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, g->variant != 2, g->stream);
+                           : launch_step_tma(g->Q, g->prec, *g->tma, a, src, g->nsm, tma_mode(g), g->stream);
         if (rc != 0) return fail(CLBM_ECUDA, "TMA-staged update could not be launched");
     } else {
         launch_step(g->Q, g->prec, a, g->stream);
@@ -1220,11 +1233,11 @@ clbm_status clbm_kernel_time(clbm_handle g, double* ms, long long* launches) {
 
 clbm_status clbm_set_kernel(clbm_handle g, int variant) {
     if (!g) return fail(CLBM_EINVAL, "handle is NULL");
-    if (variant < 0 || variant > 3) return fail(CLBM_EINVAL, "variant must be 0, 1, 2 or 3");
+    if (variant < 0 || variant > 4) return fail(CLBM_EINVAL, "variant must be 0 .. 4");
     if (variant >= 2 && !g->tma)
         return fail(CLBM_EINVAL, "the TMA-staged update needs 16/32-bit storage on sm_90 or newer");
-    if (variant == 2 && general_grid(g))
-        return fail(CLBM_EINVAL, "general grids run kernel 1 or 3 (kernel 2 reads row tables)");
+    if ((variant == 2 || variant == 4) && general_grid(g))
+        return fail(CLBM_EINVAL, "general grids run kernel 1 or 3 (kernels 2 and 4 read row tables)");
     g->variant = variant;
     return CLBM_OK;
 }

@@ -28,6 +28,7 @@
 
 #include "clbm_batch.cuh"
 #include "clbm_cell.cuh"
+#include "clbm_f2.cuh"
 #include "clbm_sync.cuh"
 
 namespace clbm {
@@ -40,14 +41,16 @@ __host__ __device__ __forceinline__ constexpr int tma_store_cols(int n2) {
 }
 
 // Shared-memory layout of one tile (elements of the storage type S).
-template <int Q, typename S>
+// TRO: rows of a tile when not the default (the two-cells-per-thread update
+// runs 12-row tiles so that it keeps 12 consumer warps per SM).
+template <int Q, typename S, int TRO = 0>
 struct TileGeom {
     // D2Q21: 8 rows for every storage type (16-bit tiles of 10 rows, 20
     // consumer warps, ran 4-6 % slower: the register file then holds 80
     // registers per thread and the kernel spills).  D2Q9 (about 80
     // registers): 12 rows, 24 consumer warps, measured 3.5 % faster than 8
     // rows (10: +0.4 %, 14: +2.5 %)
-    static constexpr int TR = Q == 9 ? 12 : 8, TJ = 64, NT = TR * TJ;
+    static constexpr int TR = TRO ? TRO : (Q == 9 ? 12 : 8), TJ = 64, NT = TR * TJ;
     static constexpr int HX = 8;                                  // column halo where c2 != 0
     static constexpr int ALIGN = 128 / (int)sizeof(S);            // keep sub-tiles 128-B aligned
     __host__ __device__ static constexpr int iabs(int x) { return x < 0 ? -x : x; }
@@ -76,11 +79,13 @@ struct TileGeom {
 // warps that each update 32 cells of a tile row and store them straight to
 // global memory (128-byte row segments).  Full / empty mbarriers per stage
 // replace every CTA-wide barrier of the tile loop.
-template <int Q, typename S>
+// CPT: cells per consumer thread (2: neighbouring cells of a row in the two
+// lanes of the packed F2 arithmetic, half as many consumer warps).
+template <int Q, typename S, int CPT = 1, int TRO = 0>
 struct PipeGeom {
-    using G = TileGeom<Q, S>;
-    static constexpr int CONSUMERS = G::NT / 32;
-    static constexpr int NTHREADS = G::NT + 32;
+    using G = TileGeom<Q, S, TRO>;
+    static constexpr int CONSUMERS = G::NT / 32 / CPT;
+    static constexpr int NTHREADS = CONSUMERS * 32 + 32;
     static constexpr int IN_BYTES = (G::BUF * (int)sizeof(S) + 127) / 128 * 128;
     static constexpr int STAGE_BYTES = IN_BYTES + (G::TABB + 127) / 128 * 128;
     // as many stages as fit in 220 KB of shared memory (2 to 8): the smaller
@@ -100,6 +105,7 @@ struct PipeGeom {
 struct TmaMaps {
     CUtensorMap ld[2][8];
     CUtensorMap st[2];
+    CUtensorMap ld12[2][8];   // the same load boxes for 12-row tiles (two cells per thread)
 };
 
 namespace {
@@ -162,7 +168,7 @@ __device__ __forceinline__ void issue_tile(const TmaMaps& maps, int buf, int til
 }
 
 template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(TileGeom<Q, S>::NT, 1)
+__global__ void __launch_bounds__((TileGeom<Q, S>::NT), 1)
     k_fused_tma(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
     using G = TileGeom<Q, S>;
     using T = Tab<Q>;
@@ -356,10 +362,10 @@ __device__ __forceinline__ void ws_update_cell_gen(const WsLattice<S>& L, const 
 
 // Issue the TMA boxes of tile (i0, j0) from the 8 load maps of the source
 // buffer, plus the tile's table rows, on barrier bar.
-template <int Q, typename S, typename C>
+template <int Q, typename S, typename C, int TRO = 0>
 __device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0, int n1, const C* tab,
                                          unsigned char* sm_in, unsigned char* sm_tab, uint64_t* bar) {
-    using G = TileGeom<Q, S>;
+    using G = TileGeom<Q, S, TRO>;
     constexpr int H = Lat<Q>::H;
     const int nrows = n1 - i0 < G::TR ? n1 - i0 : G::TR;
     uint32_t bytes = tab ? (uint32_t)nrows * Tab<Q>::S * 4 : 0u;   // no rows: per-cell tables
@@ -390,10 +396,11 @@ __device__ __forceinline__ void ws_issue(const CUtensorMap* ld8, int i0, int j0,
 // wait on the full barrier acquires it), and the consumers read the tile from
 // there -- for tiles whose description sits in global memory (batches),
 // which every consumer would otherwise fetch, with its latency, at every tile.
-template <int Q, typename S, typename C, bool PUBLISH = false, typename TileOf, typename CellFn>
+template <int Q, typename S, typename C, bool PUBLISH = false, int CPT = 1, int TRO = 0, typename TileOf,
+          typename CellFn>
 __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_of, CellFn&& cell) {
-    using G = TileGeom<Q, S>;
-    using P = PipeGeom<Q, S>;
+    using G = TileGeom<Q, S, TRO>;
+    using P = PipeGeom<Q, S, CPT, TRO>;
     using Tile = decltype(tile_of(0, 0));
     static_assert(sizeof(Tile) <= P::TILE_SLOT, "tile descriptor exceeds its shared-memory slot");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -429,8 +436,8 @@ __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_
                 if (*s_abort) break;
                 const Tile t = tile_of(tile, it);
                 if (PUBLISH) slots[st] = t;
-                ws_issue<Q, S, C>(t.ld8, t.i0, t.j0, t.lat.n1, t.tab, stage_in(st), stage_tab(st),
-                                  &full[st]);
+                ws_issue<Q, S, C, TRO>(t.ld8, t.i0, t.j0, t.lat.n1, t.tab, stage_in(st), stage_tab(st),
+                                       &full[st]);
             }
             // the loads of the last issued tiles must land before the CTA exits
             for (int t = it > P::STAGES ? it - P::STAGES : 0; t < it; ++t)
@@ -439,7 +446,8 @@ __device__ __forceinline__ void ws_pipeline(int ntiles, int* err, TileOf&& tile_
         return;
     }
 
-    const int r = tid / G::TJ, cc = tid % G::TJ;
+    // the consumer's cell (CPT = 2: cells cc and cc + 1, cc even)
+    const int r = tid / (G::TJ / CPT), cc = (tid % (G::TJ / CPT)) * CPT;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int st = it % P::STAGES;
@@ -505,7 +513,7 @@ struct RowWalk {
 // The pipelined update of one lattice (PipeGeom): tile t of a CTA uses stage
 // t mod STAGES.
 template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+__global__ void __launch_bounds__((PipeGeom<Q, S>::NTHREADS), 1)
     k_fused_ws(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
     using G = TileGeom<Q, S>;
     const int cols = (a.n2 + G::TJ - 1) / G::TJ;
@@ -520,6 +528,94 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
     }, WsUpdate<Q, S, C>{});
 }
 
+// Two neighbouring cells (i, j) and (i, j + 1), j even, of a tile staged in
+// shared memory, computed together in the packed F2 arithmetic (the same
+// update, each lane rounded as the scalar form): pull, collide, store both
+// cells' values in one store per population, and per cell the periodic
+// copies, ghost values and wall moments it supplies.
+// Rows of the two-cells-per-thread update's tiles: 12 rows keep 12 consumer
+// warps per SM at 128 registers without spills (8 rows: 8 warps, and the
+// kernel waits on latency -- 45 % issue-active against the one-cell kernel's
+// 63 %; 16 rows: the 120-register limit of 17 warps spills 180 bytes and
+// ran slower).  FP16 storage on the 1024 x 4096 annulus: 105.7 us per
+// launch against 110.9 us one cell per thread, with 29 % fewer instructions.
+constexpr int PAIR_TR = 12;
+
+template <int Q, typename S>
+__device__ __forceinline__ void ws_update_pair(const WsLattice<S>& L, const Consts<F2>& k, const S* in,
+                                               const float* tab_rows, int i0, int j0, int r, int cc) {
+    using G = TileGeom<Q, S, PAIR_TR>;
+    constexpr int H = Lat<Q>::H;
+    constexpr int SC = Store<S>::SCALE;
+    const int i = i0 + r, j = j0 + cc;
+    if (i >= L.n1 || j >= L.n2) return;
+    const bool both = j + 1 < L.n2;
+    const RowTab2<Q> tb{tab_rows + r * Tab<Q>::S};
+    Cell<Q, F2> c;
+    pull_cell<Q, F2, SC>(
+        [&](int al, int dr, int dc) -> F2 {
+            const S* p = in + G::off(al) + (r + G::row0(al) + dr) * G::width(al) + cc + G::col0(al) + dc;
+            // cc and col0 are even: the pair is aligned when the shift is
+            return F2(((G::col0(al) + dc) & 1) ? Ld2<S, false>::ld(p) : Ld2<S, true>::ld(p));
+        },
+        tb, k, c);
+    S* dst = L.dst + (long long)(i + H) * L.ld + j + GC;
+    const int dwa = wrap_offset(j, L.n2), dwb = both ? wrap_offset(j + 1, L.n2) : 0;
+    const int pl = (int)L.plane;
+    collide_emit<Q, F2, SC>(tb, c, k, [&](int al, F2 v) {
+        St2<S>::st(dst + al * pl, v, both);
+        if (dwa != 0) __stcs(dst + (al * pl + dwa), S(v.v.x));
+        if (dwb != 0) __stcs(dst + (al * pl + 1 + dwb), S(v.v.y));
+    });
+    if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
+        const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
+                                float(L.U0_lo), float(L.U0_hi), L.n2 < 2 * GC, 1};
+        ef.fill(i, j, dst, L.plane, c.rho.v.x, c.Ut2.v.x);
+        if (both) ef.fill(i, j + 1, dst + 1, L.plane, c.rho.v.y, c.Ut2.v.y);
+    }
+    if (i < H || i >= L.n1 - H) {
+        const int row = i < H ? i : H + (L.n1 - 1 - i);
+        float* wr = (float*)L.wall_rho + row * L.n2 + j;
+        float* wu = (float*)L.wall_ut2 + row * L.n2 + j;
+        wr[0] = c.rho.v.x;
+        wu[0] = c.Ut2.v.x;
+        if (both) {
+            wr[1] = c.rho.v.y;
+            wu[1] = c.Ut2.v.y;
+        }
+    }
+}
+
+template <int Q, typename S>
+struct WsUpdatePair {
+    __device__ __forceinline__ void operator()(const WsTile<Q, S, float>& t, const S* in, const float* tab,
+                                               int r, int cc) const {
+        const Consts<float>& f = t.k;
+        const Consts<F2> k2{F2(f.rho0), F2(f.g1), F2(f.g2), F2(f.tau_inv), F2(f.omt), F2(f.pref)};
+        ws_update_pair<Q, S>(t.lat, k2, in, tab, t.i0, t.j0, r, cc);
+    }
+};
+
+// The pipelined update with two cells per consumer thread: the same tiles,
+// stages and producer, half as many consumer warps, each thread computing a
+// pair of neighbouring cells in packed arithmetic (shared row table, paired
+// loads and stores).
+template <int Q, typename S>
+__global__ void __launch_bounds__((PipeGeom<Q, S, 2, PAIR_TR>::NTHREADS), 1)
+    k_fused_ws2(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
+    using G = TileGeom<Q, S, PAIR_TR>;
+    const int cols = (a.n2 + G::TJ - 1) / G::TJ;
+    const int ntiles = ((a.n1 + G::TR - 1) / G::TR) * cols;
+    const WsLattice<S> lat{(S*)a.dst, a.ghost, a.wall_rho, a.wall_ut2, a.plane, a.ld, a.n1, a.n2,
+                           a.bc_lo, a.bc_hi, a.U0_lo, a.U0_hi};
+    RowWalk w(cols);
+    ws_pipeline<Q, S, float, false, 2, PAIR_TR>(ntiles, a.err, [&](int, int t) {
+        if (t > 0) w.next();
+        return WsTile<Q, S, float>{maps.ld12[src], (const float*)a.tab, lat, Consts<float>::make(a.k),
+                                   w.band * G::TR, w.col * G::TJ};
+    }, WsUpdatePair<Q, S>{});
+}
+
 // General grids: the same pipeline, no table rows staged (the producer's
 // table pointer is null); each consumer reads its cell's table planes.
 template <int Q, typename S, typename C>
@@ -532,7 +628,7 @@ struct WsUpdateGen {
 };
 
 template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+__global__ void __launch_bounds__((PipeGeom<Q, S>::NTHREADS), 1)
     k_fused_ws_gen(const __grid_constant__ TmaMaps maps, const StepArgs a, int src) {
     using G = TileGeom<Q, S>;
     const int cols = (a.n2 + G::TJ - 1) / G::TJ;
@@ -552,7 +648,7 @@ __global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
 // memory (written before the launch; acquired for the tensor-map proxy
 // before use).
 template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+__global__ void __launch_bounds__((PipeGeom<Q, S>::NTHREADS), 1)
     k_batch_ws(const BatchGrid* __restrict__ grids, const CUtensorMap* __restrict__ maps,
                const int4* __restrict__ work, int nwork, int parity, int* err) {
     const CUtensorMap* fenced = nullptr;  // producer: maps acquired last
@@ -593,7 +689,7 @@ struct ResTile {
 // stages instead of waiting cell by cell, so the pass runs near the
 // bandwidth of one read of the state.
 template <int Q, typename S, typename C>
-__global__ void __launch_bounds__(PipeGeom<Q, S>::NTHREADS, 1)
+__global__ void __launch_bounds__((PipeGeom<Q, S>::NTHREADS), 1)
     k_residual_ws(const __grid_constant__ TmaMaps maps, const MomArgs a, int src) {
     using G = TileGeom<Q, S>;
     const int cols = (a.n2 + G::TJ - 1) / G::TJ;
@@ -651,6 +747,25 @@ static int run_ws(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cuda
     const int tiles = ((a.n1 + G::TR - 1) / G::TR) * ((a.n2 + G::TJ - 1) / G::TJ);
     const int grid = tiles < nsm ? tiles : nsm;
     k_fused_ws<Q, S, C><<<grid, P::NTHREADS, P::SMEM, s>>>(maps, a, src);
+    return 0;
+}
+
+template <int Q, typename S>
+static int run_ws2(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cudaStream_t s) {
+    using G = TileGeom<Q, S, PAIR_TR>;
+    using P = PipeGeom<Q, S, 2, PAIR_TR>;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_fused_ws2<Q, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM) !=
+            cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    const int tiles = ((a.n1 + G::TR - 1) / G::TR) * ((a.n2 + G::TJ - 1) / G::TJ);
+    const int grid = tiles < nsm ? tiles : nsm;
+    k_fused_ws2<Q, S><<<grid, P::NTHREADS, P::SMEM, s>>>(maps, a, src);
     return 0;
 }
 
@@ -794,22 +909,29 @@ int launch_step_tma_general(int Q, int prec, const TmaMaps& maps, const StepArgs
     }
 }
 
-int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
-                    int pipelined, cudaStream_t s) {
+template <int Q, typename S>
+static int run_mode(int mode, const TmaMaps& maps, const StepArgs& a, int src, int nsm, cudaStream_t s) {
+    return mode == 0 ? run_tma<Q, S>(maps, a, src, nsm, s)
+         : mode == 1 ? run_ws<Q, S>(maps, a, src, nsm, s)
+                     : run_ws2<Q, S>(maps, a, src, nsm, s);
+}
+
+// mode 0: TMA tiles with a shared output tile; 1: the pipelined update; 2:
+// the pipelined update with two cells per consumer thread.
+int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm, int mode,
+                    cudaStream_t s) {
     if (Q == 9) {
         switch (prec) {
-            case 1: return pipelined ? run_ws<9, float>(maps, a, src, nsm, s) : run_tma<9, float>(maps, a, src, nsm, s);
-            case 2: return pipelined ? run_ws<9, __half>(maps, a, src, nsm, s) : run_tma<9, __half>(maps, a, src, nsm, s);
-            case 3: return pipelined ? run_ws<9, __nv_bfloat16>(maps, a, src, nsm, s)
-                                     : run_tma<9, __nv_bfloat16>(maps, a, src, nsm, s);
+            case 1: return run_mode<9, float>(mode, maps, a, src, nsm, s);
+            case 2: return run_mode<9, __half>(mode, maps, a, src, nsm, s);
+            case 3: return run_mode<9, __nv_bfloat16>(mode, maps, a, src, nsm, s);
             default: return -1;
         }
     }
     switch (prec) {
-        case 1: return pipelined ? run_ws<21, float>(maps, a, src, nsm, s) : run_tma<21, float>(maps, a, src, nsm, s);
-        case 2: return pipelined ? run_ws<21, __half>(maps, a, src, nsm, s) : run_tma<21, __half>(maps, a, src, nsm, s);
-        case 3: return pipelined ? run_ws<21, __nv_bfloat16>(maps, a, src, nsm, s)
-                                 : run_tma<21, __nv_bfloat16>(maps, a, src, nsm, s);
+        case 1: return run_mode<21, float>(mode, maps, a, src, nsm, s);
+        case 2: return run_mode<21, __half>(mode, maps, a, src, nsm, s);
+        case 3: return run_mode<21, __nv_bfloat16>(mode, maps, a, src, nsm, s);
         default: return -1;
     }
 }
@@ -835,6 +957,13 @@ static int encode_maps(EncodeFn enc, TmaMaps* m, void* bufA, void* bufB, int n1,
             const int ac1 = shape / 2, has2 = shape & 1;
             cuuint32_t box[3] = {(cuuint32_t)(has2 ? G::TJ + 2 * G::HX : G::TJ), (cuuint32_t)(G::TR + ac1), 1};
             if (enc(&m->ld[b][shape], dt, 3, bases[b], dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return -1;
+            using G12 = TileGeom<Q, S, PAIR_TR>;
+            cuuint32_t box12[3] = {(cuuint32_t)(has2 ? G12::TJ + 2 * G12::HX : G12::TJ),
+                                   (cuuint32_t)(G12::TR + ac1), 1};
+            if (enc(&m->ld12[b][shape], dt, 3, bases[b], dims, strides, box12, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return -1;
