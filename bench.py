@@ -478,6 +478,9 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="only the batched form against per-lattice launches (512 lattices)")
     ap.add_argument("--batch-lattices", type=int, default=512)
+    ap.add_argument("--slab", action="store_true",
+                    help="with N ranks, split the one lattice into N slabs along q^2 (strong "
+                         "scaling, a halo exchange every time step) instead of N replicas")
     ap.add_argument("--three-d", default=None, choices=sorted(THREE_D_WORKLOADS),
                     help="only the three-dimensional (D3Q39) update on this workload")
     args = ap.parse_args()
@@ -490,6 +493,8 @@ def main():
     if args.serve:
         print(json.dumps(run_serving(args.serve_requests, verbose=True)))
         return
+    if args.slab:
+        return run_slab(args)
 
     import torch
     from paper_2301_01868_gb300 import clbm
@@ -597,6 +602,71 @@ def main():
         progress("serving")
     if rank == 0:
         print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_slab(args):
+    """--slab: the workload's lattice split into one slab per rank along the
+    periodic direction (paper_2301_01868_gb300.slab), each step followed by
+    the halo exchange of the crossing populations with both neighbours
+    (NCCL point-to-point between GPUs) and the residual reduced over the
+    ranks.  value = the whole lattice's cell updates per second of the
+    slowest rank (strong scaling: the work is fixed as N grows)."""
+    import torch
+    from paper_2301_01868_gb300 import clbm, slab
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    Q, prec, n1, n2, e, tau, U0 = annulus(args.workload)
+    stream = torch.cuda.Stream()
+    s = slab.Slab(Q, n1, n2, e, kind=clbm.POLAR, precision=prec, bc_lo=clbm.MOVING, bc_hi=clbm.NOSLIP,
+                  device=local, stream=stream, rank=rank, world=world)
+    s.set_case(tau, 1.0, U0, 0.0)
+
+    def bench_step():
+        s.step(args.chunk)
+        return s.residual()
+
+    for _ in range(args.warmup):
+        bench_step()
+    clocks = Clocks(smi_index(local))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches0 = s.grid.launch_count()
+    last = None
+    for _ in range(args.steps):
+        last = bench_step()
+    ev1.record(stream)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    value = n1 * n2 * args.chunk * args.steps / (ms * 1e-3) / 1e6
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 compute, f16 storage",
+                     "bf16": "f32 compute, bf16 storage"}[prec],
+           "data": "synthetic",
+           "config": dict(config_of(args.workload, args), parallelism="slabs along q^2 (%d)" % world,
+                          slab_columns=[s.j0, s.j1]),
+           "gpu_launches": s.grid.launch_count() - launches0, "clocks": ck,
+           "residual_last": last[0] if last else None, "roofline": None, "e2e": None}
+    if rank == 0:
+        print(json.dumps(out))
+    s.close()
     if dist is not None:
         dist.destroy_process_group()
 

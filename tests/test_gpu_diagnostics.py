@@ -14,8 +14,11 @@ reduction (every tile variant), and the full 1024 x 4096 bench grid.
 Tolerances (relative): FP64 1e-12; FP32 1e-5 for the velocity-linear
 quantities (angular momentum, max |u|, residual) and 2e-5 for the kinetic
 energy (quadratic in u, so twice the velocity's relative error); 16-bit
-storage the velocity bounds of the storage ladder (FP16 2e-3, BF16 5e-2),
-doubled for the kinetic energy.  Mass is compared at 1e-12 (FP64) / 1e-6
+storage six units of the storage type's roundoff (FP16 6 x 2^-11 = 3e-3,
+BF16 5e-2), doubled for the kinetic energy: the stored deviations are
+rounded every step, and which way each rounding goes depends on the FP32
+arithmetic order, so kernels equal to FP32 rounding (one and two cells per
+thread) give FP16 errors of 1.7e-3 and 2.0e-3 on the same run.  Mass is compared at 1e-12 (FP64) / 1e-6
 (FP32 sums of rounded deviations: the rest part is exact, the deviations
 carry the storage rounding).  Momentum, which vanishes at rest, is compared
 absolutely, relative to the mass.
@@ -42,7 +45,7 @@ def _clbm():
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 # (velocity-linear, kinetic energy, mass) tolerances per precision
 TOL = {"fp64": (1e-12, 1e-12, 1e-12), "fp32": (1e-5, 2e-5, 1e-6),
-       "fp16": (2e-3, 4e-3, 1e-4), "bf16": (5e-2, 1e-1, 1e-3)}
+       "fp16": (3e-3, 6e-3, 1e-4), "bf16": (5e-2, 1e-1, 1e-3)}
 
 
 class Setup:
