@@ -10,8 +10,8 @@ the n1 + 2h stored rows), D2Q9 3.  Every slab is a grid of its own (the
 geometry of planar and polar grids is the same for every column, so each
 slab computes it alone: polar slabs take the ring's angular step); the
 library packs and unpacks the strips (clbm_halo_pack / clbm_halo_unpack),
-the ranks swap them with torch.distributed point-to-point messages (NCCL on
-GPUs, device buffers; gloo on CPU, host buffers), and the convergence and
+the ranks swap them with torch.distributed point-to-point messages (NCCL:
+device buffers; gloo: through host memory), and the convergence and
 conservation sums are reduced over the ranks.
 
 Slabs whose ranks share one process (all on one GPU) exchange by device
@@ -124,12 +124,26 @@ class Slab:
         self.torch = torch
 
     # ------------------------------------------------------------- exchange
+    def _host_staged(self):
+        """Whether the strips travel through host memory (a gloo group)."""
+        if self.world == 1:
+            return False
+        import torch.distributed as dist
+        return dist.get_backend(self.group) == "gloo"
+
     def _exchange(self):
         g, (s_lo, s_hi, r_lo, r_hi) = self.grid, self.bufs
         g.halo_pack(0, s_lo)
         g.halo_pack(1, s_hi)
         g.stream.synchronize()
-        exchange(s_lo, s_hi, r_lo, r_hi, self.rank, self.world, self.group)
+        if self._host_staged():
+            # bytes, whatever the storage type: the values move bit for bit
+            h = [b.view(self.torch.uint8).cpu() for b in (s_lo, s_hi, r_lo, r_hi)]
+            exchange(h[0], h[1], h[2], h[3], self.rank, self.world, self.group)
+            r_lo.view(self.torch.uint8).copy_(h[2])
+            r_hi.view(self.torch.uint8).copy_(h[3])
+        else:
+            exchange(s_lo, s_hi, r_lo, r_hi, self.rank, self.world, self.group)
         self.torch.cuda.current_stream(g.device).synchronize()
         g.halo_unpack(0, r_lo)
         g.halo_unpack(1, r_hi)

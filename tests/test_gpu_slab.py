@@ -105,3 +105,69 @@ def test_narrow_slab_is_rejected():
     with pytest.raises(clbm.ClbmError):
         g.halo_pack(0, buf)
     g.close()
+
+
+def _slab_rank(rank, world, port, q):
+    """One rank of a gloo process group with its slab on the one GPU (the
+    kernels of the ranks never wait on each other: every exchange goes
+    through the host between launches)."""
+    import os
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2301_01868_gb300 import clbm, slab
+        from oracle import oracle as Orc
+        n1 = 16
+        n2, e = annulus(21, n1)
+        U0 = clbm.wall_speed_polar(0.02, 1.0, n2, 1.0 / n1)
+        s = slab.Slab(21, n1, n2, e, kind=clbm.POLAR, precision=0, bc_lo=clbm.MOVING, bc_hi=clbm.NOSLIP,
+                      stream=torch.cuda.Stream())
+        s.set_case(0.8, 1.0, U0, 0.0)
+        o = Orc.Grid(21, n1, n2, Orc.POLAR, edges=e, bc_lo=Orc.MOVING, bc_hi=Orc.NOSLIP)
+        o.set_case(0.8, 1.0, U0, 0.0)
+        o.init_rest()
+        start = o.state() * (1.0 + I.smooth_field((21, n1, n2), seed=3, amplitude=1e-3))
+        s.set_state(np.ascontiguousarray(start[:, :, s.j0:s.j1]))
+        s.residual()
+        s.step(80)
+        res, cons = s.residual()
+        q.put((rank, s.j0, s.j1, s.state(), res, cons))
+        s.close()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_distributed_slabs_over_gloo_ranks_equal_the_whole_lattice():
+    """Two processes, a gloo group, one slab each (slab.Slab, the class a
+    multi-GPU run uses, exchanging its strips through host memory): the
+    gathered state equals the unsplit lattice's bit for bit in FP64, and
+    the reduced residual and conservation values equal its own."""
+    import socket
+    import torch.multiprocessing as mp
+    clbm, _ = _mods()
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_slab_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted([q.get(timeout=300) for _ in range(2)], key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    n1 = 16
+    n2, e = annulus(21, n1)
+    full, _ = run_pair(21, 0, 1, clbm.POLAR, n1, n2, e,
+                       (0.8, 1.0, clbm.wall_speed_polar(0.02, 1.0, n2, 1.0 / n1), 0.0), 80)
+    whole = full.state()
+    assert out[0][1] == 0 and out[-1][2] == n2
+    joined = np.concatenate([st for _, _, _, st, _, _ in out], axis=2)
+    assert np.array_equal(joined, whole)
+    r_f, c_f = full.residual()
+    for _, _, _, _, res, cons in out:
+        assert res == pytest.approx(r_f, rel=1e-12)
+        np.testing.assert_allclose(cons, c_f, rtol=1e-12, atol=1e-15 * abs(c_f[0]))
+    full.close()
