@@ -337,6 +337,13 @@ clbm_status clbm_batch_set_variant(clbm_batch_handle b, int variant);
  * ms_per_step[5] (may be NULL) the timings (-1 for a variant the batch
  * cannot use).  Synchronises. */
 clbm_status clbm_batch_tune(clbm_batch_handle b, int steps, int* best, double* ms_per_step);
+/* Each batched time step runs as one launch per wave: consecutive lattices
+ * whose workspaces add up to at most `bytes` (4 GiB by default; a lattice
+ * larger than that forms a wave alone).  The update slows as the state one
+ * launch sweeps grows into tens of GB (512 lattices, 39.5 GB: 72 % of the
+ * copy rate in one launch, 77 % in waves of 4 GiB).  Host only. */
+clbm_status clbm_batch_set_wave_bytes(clbm_batch_handle b, size_t bytes);
+
 /* The batch's update variant (0-4, as clbm_batch_set_variant) and whether it
  * came from the tuner's cache when the batch was created (1) or is the
  * default / a later choice (0): a caller that rebuilds batches as lattices

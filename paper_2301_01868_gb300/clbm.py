@@ -105,6 +105,7 @@ def lib():
             "clbm_batch_set_variant": [h, C.c_int],
             "clbm_batch_tune": [h, C.c_int, C.POINTER(C.c_int), vp],
             "clbm_batch_get_variant": [h, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+            "clbm_batch_set_wave_bytes": [h, C.c_size_t],
             "clbm_batch_launch_count": [h, C.POINTER(ll)],
             "clbm_batch_destroy": [h],
             "clbm_destroy": [h],
@@ -473,6 +474,11 @@ class Batch:
         ms = np.empty(self.VARIANTS)
         _check(lib().clbm_batch_tune(self._h, int(steps), C.byref(best), ms.ctypes.data))
         return best.value, ms
+
+    def set_wave_bytes(self, nbytes):
+        """Run each time step as one launch per wave of consecutive lattices
+        holding at most nbytes of workspace (4 GiB by default)."""
+        _check(lib().clbm_batch_set_wave_bytes(self._h, int(nbytes)))
 
     def variant(self):
         """(variant, cached): the update variant and whether it came from the

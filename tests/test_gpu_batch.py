@@ -65,6 +65,31 @@ def build(Q, prec, stream, iters=(0,) * len(SHAPES)):
             for s, ((k, n1, n2), it) in enumerate(zip(SHAPES, iters))]
 
 
+@pytest.mark.parametrize("variant", [1, 4])
+def test_batch_in_waves_of_one_lattice_matches_oracle(variant):
+    """Waves of one lattice each (a step is then one launch per lattice):
+    every lattice still equals its oracle run."""
+    c = _clbm()
+    stream = torch.cuda.Stream()
+    grids = build(21, 1, stream)
+    ors = [make_oracle(k, 21, n1, n2, sd) for sd, (k, n1, n2) in enumerate(SHAPES)]
+    b = c.Batch(grids)
+    b.set_variant(variant)
+    b.set_wave_bytes(1)
+    b.step(45)
+    l0 = b.launch_count()
+    b.step(2)
+    assert b.launch_count() - l0 == 2 * len(grids)
+    for g, o in zip(grids, ors):
+        o.step(47)
+        assert g.t == 47
+        ref, m = o.moments(), g.moments()
+        eu = math.sqrt((((m["Ut1"] - ref["Ut1"]) ** 2 + (m["Ut2"] - ref["Ut2"]) ** 2).sum())
+                       / ((ref["Ut1"] ** 2 + ref["Ut2"] ** 2).sum()))
+        assert eu <= 1e-5
+    b.close()
+
+
 @pytest.mark.parametrize("Q,prec", [(21, 0), (9, 0), (21, 1), (9, 1)])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_batch_matches_oracle(Q, prec, variant):
