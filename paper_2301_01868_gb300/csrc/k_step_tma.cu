@@ -534,11 +534,12 @@ __global__ void __launch_bounds__((PipeGeom<Q, S>::NTHREADS), 1)
 // cells' values in one store per population, and per cell the periodic
 // copies, ghost values and wall moments it supplies.
 // Rows of the two-cells-per-thread update's tiles: 12 rows keep 12 consumer
-// warps per SM at 128 registers without spills (8 rows: 8 warps, and the
-// kernel waits on latency -- 45 % issue-active against the one-cell kernel's
-// 63 %; 16 rows: the 120-register limit of 17 warps spills 180 bytes and
-// ran slower).  FP16 storage on the 1024 x 4096 annulus: 105.7 us per
-// launch against 110.9 us one cell per thread, with 29 % fewer instructions.
+// warps per SM at 128 registers without spills.  FP16 storage on the
+// 1024 x 4096 annulus, per launch: 8 rows 8 warps, latency-bound (45 %
+// issue-active against the one-cell kernel's 63 %); 10 rows 125.0 us; 12
+// rows 105.7 us (one cell per thread: 110.9 us, with 29 % more
+// instructions); 14 rows 113.6 us (four pipeline stages instead of five);
+// 16 rows spill at the 120-register limit of 17 warps, 114.8 us.
 constexpr int PAIR_TR = 12;
 
 template <int Q, typename S>
