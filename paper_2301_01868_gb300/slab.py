@@ -124,12 +124,16 @@ class Slab:
         self.torch = torch
 
     # ------------------------------------------------------------- exchange
+    def _backend(self):
+        """The process group's backend ("" with one rank and no group)."""
+        if self.world == 1:
+            return ""
+        import torch.distributed as dist
+        return dist.get_backend(self.group)
+
     def _host_staged(self):
         """Whether the strips travel through host memory (a gloo group)."""
-        if self.world == 1:
-            return False
-        import torch.distributed as dist
-        return dist.get_backend(self.group) == "gloo"
+        return self._backend() == "gloo"
 
     def _exchange(self):
         g, (s_lo, s_hi, r_lo, r_hi) = self.grid, self.bufs
@@ -168,13 +172,8 @@ class Slab:
     def residual(self):
         """(res, cons) of the whole lattice (collective over the ranks)."""
         parts, dt = self.grid.residual_parts()
-        dev = "cpu"
-        try:
-            import torch.distributed as dist
-            if self.world > 1 and dist.get_backend(self.group) == "nccl":
-                dev = self.grid.device
-        except Exception:
-            pass
+        # NCCL reduces device tensors, gloo host ones
+        dev = self.grid.device if self._backend() == "nccl" else "cpu"
         tot = reduce_parts(parts, self.rank, self.world, self.group, device=dev)
         return combine_parts(tot, dt)
 
