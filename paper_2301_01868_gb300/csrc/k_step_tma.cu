@@ -539,7 +539,8 @@ __global__ void __launch_bounds__((PipeGeom<Q, S>::NTHREADS), 1)
 // issue-active against the one-cell kernel's 63 %); 10 rows 125.0 us; 12
 // rows 105.7 us (one cell per thread: 110.9 us, with 29 % more
 // instructions); 14 rows 113.6 us (four pipeline stages instead of five);
-// 16 rows spill at the 120-register limit of 17 warps, 114.8 us.
+// 16 rows spill at 96 registers (114.8 us), and held to 120 registers
+// with __maxnreg__ its 544 threads cannot be launched.
 constexpr int PAIR_TR = 12;
 
 template <int Q, typename S>

@@ -171,3 +171,21 @@ def test_distributed_slabs_over_gloo_ranks_equal_the_whole_lattice():
         assert res == pytest.approx(r_f, rel=1e-12)
         np.testing.assert_allclose(cons, c_f, rtol=1e-12, atol=1e-15 * abs(c_f[0]))
     full.close()
+
+
+def test_bench_slab_mode_runs_on_one_rank():
+    """bench.py --slab on one rank (the slab is its own neighbour): one JSON
+    line with strong scaling and the slab's columns."""
+    import json
+    import os
+    import subprocess
+    import sys
+    from conftest import ROOT
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--slab", "--workload",
+                          "circular_couette_d2q21_fp32_128x512", "--steps", "2", "--warmup", "1",
+                          "--chunk", "5"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([ln for ln in out.stdout.splitlines() if ln.strip()][-1])
+    assert d["scaling"] == "strong" and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["config"]["slab_columns"] == [0, 512]
+    assert d["gpu_launches"] > 0
