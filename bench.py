@@ -715,6 +715,8 @@ def run_3d(args):
     g = clbm.Grid3(n1, n2, n3, e, kind=clbm.ANNULUS3, step3=dx, precision=prec, bc_lo=clbm.MOVING,
                    bc_hi=clbm.NOSLIP, stream=stream)
     g.set_case(tau, 1.0, U0, 0.0)
+    if args.kernel:
+        g.set_kernel(args.kernel)
     chunk = args.chunk
     for _ in range(args.warmup):
         g.step(chunk)

@@ -111,6 +111,15 @@ clbm_status clbm3_moments(clbm3_handle h, double* rho, double* Ut, int dst_is_de
  * state, reduced on the device in a fixed order.  Synchronises. */
 clbm_status clbm3_totals(clbm3_handle h, double out[4]);
 
+/* Update kernel: 0 the automatic choice, 1 the pulled populations held in
+ * registers until the collision (six blocks per SM for FP32 compute; the
+ * only form of FP64 grids), 2 held in shared memory (seven blocks per SM; the
+ * automatic choice of FP32, FP16 and BF16 storage).  The same arithmetic in
+ * the same order (Eqs. 6-19, App. B): both give the same bits.  FP64 grids
+ * accept 0 and 1; CLBM_EINVAL otherwise.  Synchronises the grid's stream and
+ * drops its captured graph. */
+clbm_status clbm3_set_kernel(clbm3_handle h, int kernel);
+
 clbm_status clbm3_time(clbm3_handle h, long long* t);
 clbm_status clbm3_destroy(clbm3_handle h);
 

@@ -118,6 +118,7 @@ def lib():
             "clbm3_moments": [h, vp, vp, C.c_int],
             "clbm3_totals": [h, dp],
             "clbm3_time": [h, C.POINTER(ll)],
+            "clbm3_set_kernel": [h, C.c_int],
             "clbm3_set_equilibrium": [h, vp, vp, C.c_int],
             "clbm3_checkpoint_bytes": [h, C.POINTER(C.c_size_t)],
             "clbm3_checkpoint": [h, vp],
@@ -632,6 +633,11 @@ class Grid3:
         out = (C.c_double * 4)()
         _check(lib().clbm3_totals(self._h, out))
         return np.array(list(out))
+
+    def set_kernel(self, kernel):
+        """Update kernel: 0 automatic, 1 pulled populations in registers, 2 in
+        shared memory (FP32 compute only; the automatic choice there)."""
+        _check(lib().clbm3_set_kernel(self._h, int(kernel)))
 
     @property
     def t(self):

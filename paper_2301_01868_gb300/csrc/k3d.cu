@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "clbm3.cuh"
@@ -33,6 +34,15 @@ __device__ __forceinline__ int wrapm(int x, int n) {
     while (x < 0) x += n;
     while (x >= n) x -= n;
     return x;
+}
+
+// x in [-3, n + 3) mapped into [0, n): one conditional correction when the
+// extent is at least 4 (every shift of the lattice is at most 3), the loop
+// of wrapm for the narrower extents.
+__device__ __forceinline__ int wrap3(int x, int n) {
+    if (n < 4) return wrapm(x, n);
+    x = x < 0 ? x + n : x;
+    return x >= n ? x - n : x;
 }
 
 // ------------------------------------------------------------- geometry
@@ -248,10 +258,23 @@ __device__ __forceinline__ C ldt(const C* p) { return *p; }
 // memory once per block and every coefficient is a shared-memory read.  Six
 // blocks per SM (FP32 compute: 80 registers, a few bytes spilled) measured
 // 8 % faster than four (128 registers, no spills); seven and eight spill more.
-template <typename S, typename C, bool MOM>
-__global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 6 : 2)
+// With the pulled pairs in shared memory (SPAIRS, the default for FP32
+// compute) seven blocks fit in 72 registers: on the 128 x 804 x 32 annulus
+// 14,702 MLUPS against 13,914 (FP32 storage) and 15,862 against 14,841 (FP16);
+// eight blocks (64 registers) 13,107.  Two cells per thread in packed FP32
+// (168 registers, three blocks) measured 11,617, and all 78 reads issued as
+// asynchronous 4-byte copies into shared memory 12,419: the update is bound
+// by the latency of its loads, which wants resident warps.
+template <typename S, typename C, bool MOM, int MINB = (sizeof(C) == 4 ? 6 : 2), bool SPAIRS = false>
+__global__ void __launch_bounds__(TB, MINB)
     k3_step(Args3 A, double* __restrict__ mrho, double* __restrict__ mut) {
+    static_assert(!SPAIRS || (!MOM && sizeof(C) == 4), "shared-memory pairs: FP32-compute update only");
     __shared__ __align__(16) C ts[Tab3::S];
+    using P = typename PairOf<C>::T;
+    // SPAIRS: the pulled pairs wait for the collision in shared memory (one
+    // 8-byte slot per pair and thread, conflict-free) instead of 38
+    // registers, which makes room for seven blocks per SM instead of six
+    __shared__ P sdd[SPAIRS ? NP : 1][TB];
     const int n23 = A.n2 * A.n3;
     const int jk = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y, i = r + 1;
@@ -267,8 +290,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 6 : 2)
     int jo[7], ko[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-        jo[q] = wrapm(j - (q - 3), A.n2) * A.n3;
-        ko[q] = wrapm(k - (q - 3), A.n3);
+        jo[q] = wrap3(j - (q - 3), A.n2) * A.n3;
+        ko[q] = wrap3(k - (q - 3), A.n3);
     }
     // 32-bit element offsets (the grid's 39 planes hold fewer than 2^31
     // values, which clbm3_create_grid checks)
@@ -279,9 +302,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 6 : 2)
     // (Eq. 15), two directions a, b = -a at a time in the two lanes of a pair.
     // The arithmetic carries the storage scale SC (values as stored, a power
     // of two: exactly SC times the unscaled sums) up to the moments.
-    using P = typename PairOf<C>::T;
     constexpr int SC = Store<S>::SCALE;
-    P dd[NP];
+    P dd[SPAIRS ? 1 : NP];
     const C d0 = Store<S>::ldr(src + own);
     P sd = mkp(d0, C(0)), s1 = mkp(C(0), C(0)), s2 = s1, s3 = s1;
     P f1 = mkp(ldt(t + Tab3::F0) * C(SC), C(0)), f2 = mkp(ldt(t + Tab3::F0 + 1) * C(SC), C(0)),
@@ -299,7 +321,8 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 6 : 2)
         const P d = c1 == 0 ? pp
                     : SC == 1 ? padd(pp, mkp(w1.z, w1.w))
                               : pfma(mkp(w1.z, w1.w), mkp(C(SC), C(SC)), pp);
-        dd[p] = d;
+        if constexpr (SPAIRS) sdd[p][threadIdx.x] = d;
+        else dd[p] = d;
         sd = padd(sd, d);
         if (c1) s1 = pfma(mkp(C(c1), C(-c1)), d, s1);
         if (c2) s2 = pfma(mkp(C(c2), C(-c2)), d, s2);
@@ -428,7 +451,7 @@ __global__ void __launch_bounds__(TB, sizeof(C) == 4 ? 6 : 2)
         const C X = xs.s, Y = ys.s;
         const C w = C(w3(a));
         // (N'_a, N'_b) = (1 - 1/tau)(d_a, d_b) + J w (X + Y, X - Y)
-        const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(dd[p], omt2));
+        const P o = pfma(pmul(J2, mkp(w, w)), mkp(X + Y, X - Y), pmul(SPAIRS ? sdd[p][threadIdx.x] : dd[SPAIRS ? 0 : p], omt2));
         StStream<S>::str(dst + a * pl, o.x);
         StStream<S>::str(dst + b * pl, o.y);
     }
@@ -594,6 +617,7 @@ struct clbm3_grid {
     cudaGraphExec_t gexec;
     Args3 gargs;
     bool graphs_off;         // capture failed once (e.g. the legacy default stream)
+    int kernel;              // update: 0 automatic, 1 pulled pairs in registers, 2 in shared memory
 };
 
 namespace k3api {
@@ -674,7 +698,14 @@ template <bool MOM>
 void launch_cells(const clbm3_grid* g, const Args3& A, double* rho, double* ut) {
     by_storage(g->prec, [&](auto tag) {
         using S = typename decltype(tag)::type;
-        k3_step<S, typename Store<S>::C, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
+        using C = typename Store<S>::C;
+        if constexpr (!MOM && !std::is_same<S, double>::value) {
+            if (g->kernel != 1) {
+                k3_step<S, C, false, 7, true><<<cell_grid(g), TB, 0, g->stream>>>(A, nullptr, nullptr);
+                return;
+            }
+        }
+        k3_step<S, C, MOM><<<cell_grid(g), TB, 0, g->stream>>>(A, rho, ut);
     });
 }
 
@@ -1080,6 +1111,21 @@ clbm_status clbm3_totals(clbm3_handle g, double out[4]) {
     for (int r = 0; r < g->n1; ++r) rest += g->cs.rho0 * geo[(size_t)r * Geo3::S + Geo3::J];
     out[0] = v[0] + rest * n23(g);
     for (int q = 1; q < 4; ++q) out[q] = v[q];
+    return CLBM_OK;
+}
+
+clbm_status clbm3_set_kernel(clbm3_handle g, int kernel) {
+    if (!g) return fail3(CLBM_EINVAL, "handle is NULL");
+    if (kernel < 0 || kernel > 2) return fail3(CLBM_EINVAL, "kernel %d is not 0, 1 or 2", kernel);
+    if (kernel == 2 && g->prec == CLBM_FP64)
+        return fail3(CLBM_EINVAL, "kernel 2 is an FP32-compute update; FP64 grids run kernel 1");
+    CK3(cudaSetDevice(g->device));
+    CK3(cudaStreamSynchronize(g->stream));
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);   // the captured steps launch the old kernel
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->gexec = nullptr;
+    g->graph = nullptr;
+    g->kernel = kernel;
     return CLBM_OK;
 }
 

@@ -238,3 +238,66 @@ def test_3d_restore_continues_bit_for_bit(prec):
     with pytest.raises(c.ClbmError):
         other.restore(blob)
 
+
+
+# the two forms of the FP32-compute update: pulled pairs kept in registers
+# (kernel 1) or in shared memory (kernel 2, more blocks per SM); the same
+# arithmetic in the same order, so the same bits
+def _gpu_kernel(case, prec, kernel):
+    g = case.gpu(prec)
+    g.set_kernel(kernel)
+    return g
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("n2,n3", [(13, 11), (1, 5), (7, 1)])
+def test_fp32_kernels_ragged_and_degenerate_columns(kernel, n2, n3):
+    """Ragged block tails, n2 = 1 (every q^2 neighbour is the cell itself),
+    n3 = 1."""
+    case = stretched_channel(n1=6, n2=n2, n3=n3, bc=(1, 0), U0=(0.02, 0.0), g=(0.0, 2e-6, 1e-6))
+    o = case.oracle()
+    g = _gpu_kernel(case, 1, kernel)
+    st = perturbed(o, 9, 2e-3)
+    o.set_state(st)
+    g.set_state(st)
+    o.step(60)
+    g.step(60)
+    rest = case.oracle().state()
+    assert rel(g.state() - rest, o.state() - rest) <= 1e-5
+    assert rel(g.moments()["Ut"], o.moments()["Ut"]) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 3e-3), (3, 3e-2)])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_16bit_storage_kernels_near_oracle(prec, tol, kernel):
+    case = stretched_channel(n2=7, bc=(1, 0), U0=(0.02, 0.0), g=(0.0, 1e-6, 2e-6))
+    o = case.oracle()
+    g = _gpu_kernel(case, prec, kernel)
+    o.step(200)
+    g.step(200)
+    assert rel(g.moments()["Ut"], o.moments()["Ut"]) <= tol
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_kernels_give_the_same_bits_and_fp64_keeps_registers(prec):
+    """The contracted annulus (CR = 0.35, moving inner wall), a perturbed
+    start, 80 steps (captured-graph replays included): both kernels write
+    identical states."""
+    e = I.polar_edges(1.0, 2.0, 8, 0.35)
+    case = Case3(8, 50, 3, 1, edges=e, step3=0.15, bc=(1, 0), U0=(0.05, 0.0), g=(0.0, 0.0, 1e-6))
+    st = perturbed(case.oracle(), 5, 1e-3)
+    out = []
+    for kernel in (1, 2):
+        g = _gpu_kernel(case, prec, kernel)
+        g.set_state(st)
+        g.step(80)
+        out.append(g.state())
+        g.close()
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
+    c = _clbm()
+    g = case.gpu(0)
+    g.set_kernel(1)
+    with pytest.raises(c.ClbmError):
+        g.set_kernel(2)
+    g.close()
