@@ -448,7 +448,9 @@ def config_of(wl, args):
             "tau": tau, "u_wall": uw,
             "storage": prec, "chunk": args.chunk,
             "kernel": {0: "auto", 1: "per-cell", 2: "tma-tiles", 3: "tma-pipeline",
-                       4: "tma-pipeline, two cells per thread"}[args.kernel],
+                       4: "tma-pipeline, two cells per thread",
+                       5: "tma-pipeline, multi-step launches",
+                       6: "tma-pipeline, two cells per thread, multi-step launches"}[args.kernel],
             "l2": "inputs larger than L2 (state %d MB)" % (2 * Q * n1 * n2 * STORAGE_BYTES[prec] >> 20),
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -469,7 +471,8 @@ def main():
     ap.add_argument("--kernel", type=int, default=0,
                     help="0 automatic, 1 one thread per cell, 2 TMA-staged tiles, "
                          "3 TMA-staged warp-specialised pipeline, 4 the same with two cells per "
-                         "thread in packed arithmetic")
+                         "thread in packed arithmetic, 5 / 6 kernels 3 / 4 with many time steps "
+                         "per launch")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving comparison (continuous batching vs serial solves)")
     ap.add_argument("--serve-requests", type=int, default=48)

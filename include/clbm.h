@@ -262,25 +262,33 @@ clbm_status clbm_set_stream(clbm_handle h, void* stream);
 /* period > 0: clbm_step records a CUDA event pair around every period-th
  * launch of the fused update (1: every launch; a larger period keeps the
  * events' own cost out of the timed stream); a graph replay is recorded as a
- * whole, one pair around its 10 back-to-back launches, whatever the period;
- * period 0 switches it off.
+ * whole, one pair around its 10 back-to-back launches, and so is a
+ * multi-step launch (kernels 5 and 6), counted as its number of time steps,
+ * whatever the period; period 0 switches it off.
  * clbm_kernel_time returns the recorded launches' summed duration (ms) and
  * their count since the last reset, and resets.  Synchronises. */
 clbm_status clbm_set_profiling(clbm_handle h, int period);
 clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
 
 /* Kernel of the bulk update: 0 automatic (general grids: 1; planar and polar
- * grids with TMA maps: 4 for FP16 / BF16 storage, 3 for FP32; else 1), 1 one
- * thread per cell with direct loads, 2 TMA-staged tiles with a shared output
- * tile (planar and polar grids), 3 TMA-staged tiles in a warp-specialised
- * pipeline (general grids: the state staged, the per-cell tables read by the
+ * grids with TMA maps: 4 for FP16 / BF16 storage, run as 6 when the grid
+ * has at least 8 tiles per SM, 3 for FP32; else 1), 1 one thread per cell
+ * with direct loads, 2 TMA-staged tiles with a shared output tile (planar
+ * and polar grids), 3 TMA-staged tiles in a warp-specialised pipeline
+ * (general grids: the state staged, the per-cell tables read by the
  * consumers), 4 the same pipeline with two neighbouring cells per thread in
- * packed FP32 arithmetic (planar and polar grids) (2-4: FP32 / FP16 / BF16
- * storage and rows of at least 16 bytes; the implicit-force passes always
- * use variant 1).  All run the same update; the packed form rounds each lane
- * as the scalar form but may contract a different multiply-add pairing, so
- * FP32 results agree to rounding, not bit for bit.  CLBM_EINVAL for a
- * variant the grid cannot use. */
+ * packed FP32 arithmetic (planar and polar grids), 5 / 6 kernels 3 / 4 with up
+ * to 1000 time steps per launch (planar and polar grids): the CTAs of one
+ * cooperative launch order the steps among themselves -- a tile of step
+ * s waits until step s - 1 has finished the row bands its pull reaches
+ * (Eq. 12: |c^1| <= 3 rows) -- so the ramp-up, tail and gap of a launch come
+ * once per run; a wait that gives up is reported as the pipeline's bounded
+ * waits are, CLBM_ETIMEOUT from clbm_moments (2-6: FP32 / FP16 / BF16 storage and rows of at least
+ * 16 bytes; the implicit-force passes always use variant 1).  All run the
+ * same update; 5 and 6 give the bits of 3 and 4; the packed form rounds each
+ * lane as the scalar form but may contract a different multiply-add
+ * pairing, so FP32 results agree to rounding, not bit for bit.  CLBM_EINVAL
+ * for a variant the grid cannot use. */
 clbm_status clbm_set_kernel(clbm_handle h, int variant);
 
 /* Number of kernel launches this grid has issued since creation. */

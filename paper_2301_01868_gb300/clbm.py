@@ -426,8 +426,9 @@ class Grid:
 
     def set_kernel(self, variant):
         """0 automatic, 1 one thread per cell, 2 TMA-staged tiles with a shared
-        output tile, 3 TMA-staged warp-specialised pipeline (the automatic
-        choice where the grid has TMA maps)."""
+        output tile, 3 TMA-staged warp-specialised pipeline, 4 the pipeline
+        with two cells per thread, 5 / 6 kernels 3 / 4 with many time steps
+        per launch (clbm.h)."""
         _check(lib().clbm_set_kernel(self._h, int(variant)))
 
     def launch_count(self):

@@ -206,6 +206,16 @@ int launch_step_tma_general(int Q, int prec, const TmaMaps& maps, const StepArgs
                             cudaStream_t s);
 int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
                     int pipelined, cudaStream_t s);
+// nsteps time steps of the pipelined update (mode 1: one cell per consumer
+// thread, 2: two) in one cooperative launch whose CTAs order the steps among
+// themselves: prog holds one progress word per CTA and the run's tile
+// counter (nsm + 1 words, zero when allocated), epoch a value no earlier
+// launch on prog used.  Returns the launch's CUDA error (cudaSuccess when it
+// was launched).
+int run_tiles(int Q, int mode, int n1, int n2);
+cudaError_t launch_step_tma_run(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
+                                int mode, int nsteps, unsigned long long* prog, unsigned epoch,
+                                cudaStream_t s);
 
 // Set the thread-local message returned by clbm_last_error (clbm_api.cu).
 void set_last_error(const char* msg);

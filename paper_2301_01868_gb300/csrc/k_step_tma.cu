@@ -25,6 +25,7 @@
 #include <cuda.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "clbm_batch.cuh"
 #include "clbm_cell.cuh"
@@ -674,6 +675,211 @@ __global__ void __launch_bounds__((PipeGeom<Q, S>::NTHREADS), 1)
     }, WsUpdate<Q, S, C>{});
 }
 
+// Progress between the CTAs of a multi-step run (k_fused_ws_run).  Each CTA
+// publishes, tagged with the launch's epoch, the run index of its oldest
+// tile not yet complete (release at GPU scope: the consumers' stores,
+// acquired by the producer through the stage's empty barrier, come with
+// it); tiles are handed out in run order, so every tile below the minimum
+// over the CTAs is complete.  A tile of step s > 0 in band b reads rows of
+// bands b - 1 .. b + 1 of step s - 1 (the pull reaches |c^1| <= 3 rows,
+// fewer than a band's; the periodic ghost columns and wall ghost rows a band
+// writes serve its own rows) and overwrites rows those bands' tiles read: it
+// waits until every tile of step s - 1 up to band b + 1 is complete, about a
+// step behind the tiles in flight, so the last known minimum normally
+// suffices.  Before it waits for real, the producer lets its consumers
+// finish every tile it issued and publishes that, so the CTA holding the
+// oldest incomplete tile always has its inputs: with every CTA resident (a
+// cooperative launch) the run cannot deadlock.  Waits are bounded (error
+// code 2).
+struct RunSync {
+    unsigned long long* prog;
+    unsigned epoch;
+    int per_step, cols, nbands, period;
+    unsigned known;          // the producer's last minimum over the CTAs
+    unsigned last;           // the CTA's last published value (published values only grow)
+    volatile int* abort;     // the CTA's stop flag (a consumer's wait gave up)
+
+    __device__ void publish(unsigned p) {
+        if (p <= last) return;
+        last = p;
+        const unsigned long long v = ((unsigned long long)epoch << 32) | p;
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(prog + blockIdx.x), "l"(v) : "memory");
+    }
+    __device__ unsigned scan() const {
+        unsigned m = 0xffffffffu;
+        for (int c = 0; c < (int)gridDim.x; ++c) {
+            unsigned long long v;
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(prog + c) : "memory");
+            const unsigned p = (unsigned)(v >> 32) == epoch ? (unsigned)v : 0u;
+            m = p < m ? p : m;
+        }
+        // acquire what the CTAs released; the TMA loads that follow read it
+        // through the async proxy
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        return m;
+    }
+    // iteration `it` of the CTA's tiles, run index `oldest` of its oldest incomplete tile
+    __device__ void consumed(int it, unsigned oldest) {
+        if (it % period == 0) publish(oldest);
+    }
+    template <typename D>
+    __device__ bool ready(unsigned e, D&& drain) {
+        const int s = (int)(e / (unsigned)per_step);
+        if (s == 0) return true;
+        const int band = (int)(e - (unsigned)s * per_step) / cols;
+        const unsigned need = (unsigned)(s - 1) * per_step + (unsigned)min(band + 2, nbands) * cols;
+        if (known >= need) return true;
+        known = scan();
+        if (known >= need) return true;
+        if (!drain()) return false;
+        publish(e);
+        for (int k = 0; k < (1 << 20) && !*abort; ++k) {
+            __nanosleep(256);
+            known = scan();
+            if (known >= need) return true;
+        }
+        return false;
+    }
+    template <typename D>
+    __device__ void finish(D&& drain) {
+        if (drain()) publish(0xffffffffu);
+    }
+};
+
+// A tile of a multi-step run as the stage's slot carries it: the step's
+// parity, the tile's origin, and stop (no tile: the run is over).
+struct RunTile {
+    int p, i0, j0, stop;
+};
+
+// nsteps time steps of the pipelined update in one launch.  The tiles of
+// steps 0, 1, ..., nsteps - 1 form one sequence (step by step, band-major
+// within a step); each CTA's producer takes the next one from a counter in
+// global memory, so all CTAs work on neighbouring tiles as in a single-step
+// launch (a static share per CTA lets them drift apart over the steps and
+// spread their reads: 0.145 ms per step against 0.116 on the 1024 x 4096
+// annulus), and the first bands of a step are updated while the last bands
+// of the step before are still in flight: a launch gap, ramp-up and tail
+// once per run instead of once per step.  Step s reads buffer src ^ (s & 1)
+// and writes the other; CPT as in ws_pipeline.  next: the run's counter
+// (zero at launch).
+template <int Q, typename S, typename C, int CPT>
+__global__ void __launch_bounds__((PipeGeom<Q, S, CPT, CPT == 2 ? PAIR_TR : 0>::NTHREADS), 1)
+    k_fused_ws_run(const __grid_constant__ TmaMaps maps, const StepArgs a, int src, int nsteps,
+                   unsigned long long* prog, unsigned epoch, int period) {
+    constexpr int TRO = CPT == 2 ? PAIR_TR : 0;
+    using G = TileGeom<Q, S, TRO>;
+    using P = PipeGeom<Q, S, CPT, TRO>;
+    using Update = typename std::conditional<CPT == 2, WsUpdatePair<Q, S>, WsUpdate<Q, S, C>>::type;
+    const int cols = (a.n2 + G::TJ - 1) / G::TJ;
+    const int nbands = (a.n1 + G::TR - 1) / G::TR;
+    const int per_step = nbands * cols;
+    const unsigned ntiles = (unsigned)per_step * (unsigned)nsteps;
+    unsigned long long* const next = prog + gridDim.x;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* const smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t* const full = (uint64_t*)(smem + P::STAGES * P::STAGE_BYTES);
+    uint64_t* const empty = full + P::STAGES;
+    volatile int* const s_abort = (volatile int*)(empty + P::STAGES);
+    volatile RunTile* const slots = (volatile RunTile*)(smem + P::STAGES * P::STAGE_BYTES + 2 * P::STAGES * 8 + 16);
+    auto stage_in = [&](int st) { return smem + st * P::STAGE_BYTES; };
+    auto stage_tab = [&](int st) { return smem + st * P::STAGE_BYTES + P::IN_BYTES; };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int st = 0; st < P::STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], P::CONSUMERS);
+        }
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == P::CONSUMERS) {  // producer
+        if (lane == 0) {
+            RunSync rs{prog, epoch, per_step, cols, nbands, period, 0u, 0u, s_abort};
+            bool stopped = false;
+            unsigned taken[P::STAGES];   // run index of the tile of each stage
+            int it = 0;
+            auto drain = [&]() {
+                for (int t = it > P::STAGES ? it - P::STAGES : 0; t < it; ++t)
+                    if (!mbar_wait(&empty[t % P::STAGES], (t / P::STAGES) & 1)) return false;
+                return true;
+            };
+            unsigned e = (unsigned)atomicAdd(next, 1ull);
+            for (;; ++it) {
+                const int st = it % P::STAGES;
+                if (it >= P::STAGES) {
+                    if (!mbar_wait(&empty[st], (it / P::STAGES - 1) & 1)) {
+                        *s_abort = 1;
+                        atomicExch(a.err, 1);
+                        break;
+                    }
+                    rs.consumed(it, taken[(it - P::STAGES + 1) % P::STAGES]);
+                }
+                if (*s_abort) break;
+                if (e >= ntiles) {   // the run is over: stop the consumers
+                    slots[st].stop = 1;
+                    mbar_arrive(&full[st]);
+                    stopped = true;
+                    break;
+                }
+                if (!rs.ready(e, drain)) {
+                    *s_abort = 1;
+                    atomicExch(a.err, 2);
+                    break;
+                }
+                // the next tile is taken now, its latency hidden behind this one's loads
+                const unsigned e_next = (unsigned)atomicAdd(next, 1ull);
+                const int s = (int)(e / (unsigned)per_step), t = (int)(e - (unsigned)s * per_step);
+                const int band = t / cols, col = t - band * cols, par = s & 1;
+                slots[st].p = par;
+                slots[st].i0 = band * G::TR;
+                slots[st].j0 = col * G::TJ;
+                slots[st].stop = 0;
+                taken[st] = e;
+                ws_issue<Q, S, C, TRO>(CPT == 2 ? maps.ld12[src ^ par] : maps.ld[src ^ par], band * G::TR,
+                                       col * G::TJ, a.n1, (const C*)a.tab, stage_in(st), stage_tab(st), &full[st]);
+                e = e_next;
+            }
+            // the loads of the last issued tiles must land before the CTA exits
+            // (after a stop, whose arrive completed one more phase of its
+            // stage, the tile issued STAGES iterations before it is known to
+            // have landed: its stage was released)
+            const int first = it > P::STAGES ? it - P::STAGES + (stopped ? 1 : 0) : 0;
+            for (int t = first; t < it; ++t) mbar_wait(&full[t % P::STAGES], (t / P::STAGES) & 1);
+            if (!*s_abort) rs.finish(drain);
+        }
+        return;
+    }
+
+    // consumers: the tiles the producer hands over, until the stop (a wait
+    // for the next tile may include the producer's wait for the step before:
+    // a longer bound than the single-step pipeline's)
+    WsLattice<S> lat{(S*)a.dst, a.ghost, a.wall_rho, a.wall_ut2, a.plane, a.ld, a.n1, a.n2,
+                     a.bc_lo, a.bc_hi, a.U0_lo, a.U0_hi};
+    const Consts<C> k = Consts<C>::make(a.k);
+    const int r = tid / (G::TJ / CPT), cc = (tid % (G::TJ / CPT)) * CPT;
+    for (int it = 0;; ++it) {
+        const int st = it % P::STAGES;
+        if (!mbar_wait_n(&full[st], (it / P::STAGES) & 1, 1 << 22)) {
+            *s_abort = 1;
+            atomicExch(a.err, 1);
+            break;
+        }
+        if (*s_abort || slots[st].stop) break;
+        const int par = slots[st].p;
+        lat.dst = par ? (S*)a.src : (S*)a.dst;   // written by even / odd steps
+        const WsTile<Q, S, C> tile{nullptr, (const C*)a.tab, lat, k, slots[st].i0, slots[st].j0};
+        Update{}(tile, (const S*)stage_in(st), (const C*)stage_tab(st), r, cc);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+    }
+}
+
 // A tile of the residual: what the producer needs (maps, table, n1, origin).
 template <typename C>
 struct ResTile {
@@ -772,6 +978,53 @@ static int run_ws2(const TmaMaps& maps, const StepArgs& a, int src, int nsm, cud
     const int grid = tiles < nsm ? tiles : nsm;
     k_fused_ws2<Q, S><<<grid, P::NTHREADS, P::SMEM, s>>>(maps, a, src);
     return 0;
+}
+
+template <int Q, typename S, int CPT>
+static cudaError_t run_ws_run(const TmaMaps& maps, const StepArgs& a, int src, int nsm, int nsteps,
+                              unsigned long long* prog, unsigned epoch, cudaStream_t s) {
+    constexpr int TRO = CPT == 2 ? PAIR_TR : 0;
+    using G = TileGeom<Q, S, TRO>;
+    using P = PipeGeom<Q, S, CPT, TRO>;
+    using C = typename Store<S>::C;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(k_fused_ws_run<Q, S, C, CPT>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    const int tiles = ((a.n1 + G::TR - 1) / G::TR) * ((a.n2 + G::TJ - 1) / G::TJ);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tiles < nsm ? tiles : nsm);
+    cfg.blockDim = dim3(P::NTHREADS);
+    cfg.dynamicSmemBytes = P::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: the run orders its steps itself
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // publish progress every `period` tiles: as rarely as the run allows
+    // (each is a release at GPU scope) while the slowest CTA's published
+    // tile stays more than a step's worth of tiles minus two bands behind
+    // the tiles in flight, so that waits are met without draining
+    const int cols = (a.n2 + G::TJ - 1) / G::TJ, grid = tiles < nsm ? tiles : nsm;
+    int period = 1;
+    while (period < 64 && (4 * period + P::STAGES + 2) * grid <= tiles - 2 * cols) period *= 2;
+    // the run's tile counter, after the grid's progress words
+    const cudaError_t e = cudaMemsetAsync(prog + grid, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k_fused_ws_run<Q, S, C, CPT>, maps, a, src, nsteps, prog, epoch, period);
+}
+
+template <int Q, typename S>
+static cudaError_t run_mode_run(int mode, const TmaMaps& maps, const StepArgs& a, int src, int nsm, int nsteps,
+                                unsigned long long* prog, unsigned epoch, cudaStream_t s) {
+    return mode == 2 ? run_ws_run<Q, S, 2>(maps, a, src, nsm, nsteps, prog, epoch, s)
+                     : run_ws_run<Q, S, 1>(maps, a, src, nsm, nsteps, prog, epoch, s);
 }
 
 template <int Q, typename S>
@@ -938,6 +1191,32 @@ int launch_step_tma(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int
         case 2: return run_mode<21, __half>(mode, maps, a, src, nsm, s);
         case 3: return run_mode<21, __nv_bfloat16>(mode, maps, a, src, nsm, s);
         default: return -1;
+    }
+}
+
+// Tiles per time step of the pipelined update (mode 1 or 2) on an n1 x n2 grid.
+int run_tiles(int Q, int mode, int n1, int n2) {
+    const int tr = mode == 2 ? PAIR_TR : Q == 9 ? TileGeom<9, float>::TR : TileGeom<21, float>::TR;
+    const int tj = TileGeom<21, float>::TJ;
+    return ((n1 + tr - 1) / tr) * ((n2 + tj - 1) / tj);
+}
+
+cudaError_t launch_step_tma_run(int Q, int prec, const TmaMaps& maps, const StepArgs& a, int src, int nsm,
+                                int mode, int nsteps, unsigned long long* prog, unsigned epoch,
+                                cudaStream_t s) {
+    if (Q == 9) {
+        switch (prec) {
+            case 1: return run_mode_run<9, float>(mode, maps, a, src, nsm, nsteps, prog, epoch, s);
+            case 2: return run_mode_run<9, __half>(mode, maps, a, src, nsm, nsteps, prog, epoch, s);
+            case 3: return run_mode_run<9, __nv_bfloat16>(mode, maps, a, src, nsm, nsteps, prog, epoch, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (prec) {
+        case 1: return run_mode_run<21, float>(mode, maps, a, src, nsm, nsteps, prog, epoch, s);
+        case 2: return run_mode_run<21, __half>(mode, maps, a, src, nsm, nsteps, prog, epoch, s);
+        case 3: return run_mode_run<21, __nv_bfloat16>(mode, maps, a, src, nsm, nsteps, prog, epoch, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

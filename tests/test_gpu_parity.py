@@ -183,20 +183,22 @@ def test_fp64_state_roundtrip_and_time():
 # ------------------------------------------------------------------ FP32
 # kernel 1: one thread per cell with direct loads; kernel 2: TMA-staged tiles;
 # kernel 3: the TMA-staged pipeline; kernel 4: the pipeline with two cells
-# per thread in packed arithmetic.
+# per thread in packed arithmetic; kernels 5 and 6: kernels 3 and 4 run as
+# multi-step launches (these small grids wait on the step before at almost
+# every tile).
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_fp32_planar_couette_config1(kernel):
     compare_run(planar_couette_cfg1(), 1, 1000, tol_u=1e-5, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("Q", [9, 21])
 def test_fp32_polar_couette_1000_steps(Q, kernel):
     compare_run(polar_case(Q, CR=POLAR_CR[Q]), 1, 1000, tol_u=1e-5, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [2, 3, 4])
+@pytest.mark.parametrize("kernel", [2, 3, 4, 5, 6])
 @pytest.mark.parametrize("Q", [9, 21])
 def test_fp32_tma_ragged_tiles_random_state(Q, kernel):
     """Sizes that leave partial 8 x 64 tiles in both directions, j-dependent
@@ -223,7 +225,7 @@ def test_tma_and_per_cell_kernels_agree_on_ragged_rows(prec, tol, n2):
     a.step(60)
     sa = a.state()
     dev = st - c.oracle().state()
-    for kernel in (2, 3, 4):
+    for kernel in (2, 3, 4, 5, 6):
         b = c.gpu(prec, kernel)
         b.set_state(st)
         b.step(60)
@@ -238,7 +240,7 @@ def test_rows_shorter_than_a_tma_chunk_use_the_per_cell_kernel(prec):
     c = _clbm()
     n1, n2 = 10, 3
     case = Case(21, n1, n2, O.PLANAR, I.uniform_edges(n1), bc=(1, 0), tau=0.9, U0=(0.02, 0.0))
-    for kernel in (2, 3, 4):
+    for kernel in (2, 3, 4, 5, 6):
         with pytest.raises(c.ClbmError):
             case.gpu(prec, kernel)
     if prec == 1:
@@ -256,7 +258,7 @@ def test_fp32_kernels_agree():
     assert vel_err(mb, ma) < 5e-6
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_fp32_stretched_poiseuille(kernel):
     """D2Q21 only: D2Q9 with the lagged force amplifies rounding on stretched
     grids (its odd-even wall mode), which would measure that growth."""
@@ -272,7 +274,7 @@ def test_fp32_random_state():
 
 # --------------------------------------------------------- 16-bit storage
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("prec,tol", [(2, 2e-3), (3, 5e-2)])
 def test_16bit_storage_polar_couette(prec, tol, kernel):
     compare_run(polar_case(21, uw=0.05), prec, 1000, tol_u=tol, kernel=kernel)
