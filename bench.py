@@ -598,6 +598,9 @@ def main():
             progress("precisions")
             out["batch"] = batch_record()
             progress("batch")
+            out["three_d"] = [three_d_record(w, 10, 3, 100)
+                              for w in ("annulus3d_d3q39_fp32_128x804x32", "annulus3d_d3q39_f16_128x804x32")]
+            progress("3-D")
             if not args.no_cpu_baseline:
                 out["configs"] = config_records()
                 progress("configs")
@@ -706,22 +709,20 @@ def cpu_baseline_3d(wl, target_s=10.0):
                       % (n, m1, m2, m3, dt)}
 
 
-def run_3d(args):
-    """--three-d WL: the D3Q39 update on an extruded annulus, timed like the
-    main line (chunk time steps per bench step, CUDA events on the grid's
-    stream); roofline on the whole step (ghost rows + update launches)."""
+def three_d_record(wl, steps, warmup, chunk, kernel=0, cpu=False):
+    """The D3Q39 update on an extruded annulus, timed like the main line
+    (chunk time steps per bench step, CUDA events on the grid's stream);
+    roofline on the whole step (ghost rows + update launches)."""
     import torch
     from paper_2301_01868_gb300 import clbm
-    wl = args.three_d
     prec, n1, n2, n3, e, dx, tau, U0 = annulus3d(wl)
     stream = torch.cuda.Stream()
     g = clbm.Grid3(n1, n2, n3, e, kind=clbm.ANNULUS3, step3=dx, precision=prec, bc_lo=clbm.MOVING,
                    bc_hi=clbm.NOSLIP, stream=stream)
     g.set_case(tau, 1.0, U0, 0.0)
-    if args.kernel:
-        g.set_kernel(args.kernel)
-    chunk = args.chunk
-    for _ in range(args.warmup):
+    if kernel:
+        g.set_kernel(kernel)
+    for _ in range(warmup):
         g.step(chunk)
     torch.cuda.synchronize()
     clocks = Clocks(smi_index(0))
@@ -729,22 +730,22 @@ def run_3d(args):
     clocks.start()
     time.sleep(0.3)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         g.step(chunk)
     ev1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     cells = n1 * n2 * n3
-    steps = chunk * args.steps
+    nsteps = chunk * steps
     sb = STORAGE_BYTES[prec]
     bytes_per_step = 2 * 39 * sb * cells
-    achieved = bytes_per_step / (ms * 1e-3 / steps) / 1e9
+    achieved = bytes_per_step / (ms * 1e-3 / nsteps) / 1e9
     peak, peak_src = peaks()
     tot = g.totals()
-    out = {"metric": "D3Q39 curvilinear MLUPS and % HBM roofline", "value": cells * steps / (ms * 1e-3) / 1e6,
-           "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    out = {"metric": "D3Q39 curvilinear MLUPS and % HBM roofline", "value": cells * nsteps / (ms * 1e-3) / 1e6,
+           "unit": "MLUPS", "n_gpus": 1, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f32 compute, f16 storage",
                      "bf16": "f32 compute, bf16 storage"}[prec], "data": "synthetic",
            "config": {"workload": wl, "lattice": "D3Q39", "n1": n1, "n2": n2, "n3": n3,
@@ -754,12 +755,18 @@ def run_3d(args):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src + " (hbm_gbs)",
                         "algorithmic_bytes_per_launch": bytes_per_step,
-                        "kernel_ms_avg": ms / steps, "timed": "whole time step: ghost-row and update launches"},
-           "gpu_launches": 2 * steps, "clocks": ck, "mass_after": tot[0]}
-    if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_3d(wl)
-    print(json.dumps(out))
+                        "kernel_ms_avg": ms / nsteps, "timed": "whole time step: ghost-row and update launches"},
+           "gpu_launches": 2 * nsteps, "clocks": ck, "mass_after": tot[0]}
     g.close()
+    if cpu:
+        out["cpu_baseline"] = cpu_baseline_3d(wl)
+    return out
+
+
+def run_3d(args):
+    """--three-d WL: only the 3-D record, one JSON line."""
+    print(json.dumps(three_d_record(args.three_d, args.steps, args.warmup, args.chunk, args.kernel,
+                                    cpu=not args.no_cpu_baseline)))
 
 
 def _fifo_latencies(reqs, service):
