@@ -272,7 +272,8 @@ clbm_status clbm_kernel_time(clbm_handle h, double* ms, long long* launches);
 
 /* Kernel of the bulk update: 0 automatic (general grids: 1; planar and polar
  * grids with TMA maps: 4 for FP16 / BF16 storage, run as 6 when the grid
- * has at least 8 tiles per SM, 3 for FP32; else 1), 1 one thread per cell
+ * has at least 8 tiles per SM and the GPU can hold every CTA of the
+ * cooperative launch, 3 for FP32; else 1), 1 one thread per cell
  * with direct loads, 2 TMA-staged tiles with a shared output tile (planar
  * and polar grids), 3 TMA-staged tiles in a warp-specialised pipeline
  * (general grids: the state staged, the per-cell tables read by the

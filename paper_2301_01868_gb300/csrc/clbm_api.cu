@@ -91,6 +91,7 @@ struct clbm_grid {
     int* err;               // device error word of bounded waits
     unsigned long long* prog;  // progress words and tile counter of the multi-step runs (nsm + 1, device)
     unsigned run_epoch;        // tag of the last multi-step run on prog
+    bool run_refused;          // a cooperative launch was refused: the automatic choice keeps to a launch per step
     // CUDA graph of GRAPH_STEPS update launches (an even count, so the two
     // state buffers end where they started), replayed by clbm_step; the key
     // is what the launches take, and a change of it rebuilds the graph
@@ -241,7 +242,7 @@ constexpr int RUN_MAX_STEPS = 1000;   // time steps per multi-step launch
 bool use_run(const clbm_grid* g) {
     if (!use_tma(g) || general_grid(g)) return false;
     if (g->variant == 5 || g->variant == 6) return true;
-    if (g->variant != 0 || g->prec < 2) return false;
+    if (g->variant != 0 || g->prec < 2 || g->run_refused) return false;
     return run_tiles(g->Q, tma_mode(g), g->n1, g->n2) >= RUN_TILES_PER_SM * g->nsm;
 }
 
@@ -708,6 +709,10 @@ static clbm_status launch_update(clbm_grid* g, const StepArgs& a) {
     return CLBM_OK;
 }
 
+// step_run's answer when the cooperative launch was refused under the
+// automatic choice (internal, never returned by the C ABI).
+constexpr clbm_status CLBM_EAGAIN_RUN = (clbm_status)-100;
+
 // nsteps time steps in one multi-step launch (recorded as a whole while
 // profiling, counted as nsteps launches of the update).
 static clbm_status step_run(clbm_grid* g, int nsteps) {
@@ -733,6 +738,12 @@ static clbm_status step_run(clbm_grid* g, int nsteps) {
                                               g->prog, g->run_epoch, g->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (e == cudaErrorCooperativeLaunchTooLarge && g->variant == 0) {
+            // not every CTA can be resident (another context holds SMs):
+            // nothing was launched, the caller steps one launch at a time
+            g->run_refused = true;
+            return CLBM_EAGAIN_RUN;
+        }
         return fail(CLBM_ECUDA, "multi-step update could not be launched: %s", cudaGetErrorString(e));
     }
     if (g->profiling) {
@@ -899,10 +910,13 @@ clbm_status clbm_step(clbm_handle g, long long n) {
     if (use_run(g)) {
         for (; s < n; s += RUN_MAX_STEPS) {
             st = step_run(g, (int)std::min<long long>(n - s, RUN_MAX_STEPS));
+            if (st == CLBM_EAGAIN_RUN) break;   // refused: the rest with a launch per step
             if (st != CLBM_OK) return st;
         }
-        CK(cudaGetLastError());
-        return CLBM_OK;
+        if (s >= n) {
+            CK(cudaGetLastError());
+            return CLBM_OK;
+        }
     }
     // long runs replay a captured graph of GRAPH_STEPS launches: one host call
     // per replay instead of one per launch, so the device never waits on the
