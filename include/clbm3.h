@@ -97,8 +97,9 @@ clbm_status clbm3_restore(clbm3_handle h, const void* buf);
 
 /* Advance n >= 0 time steps (Sec. 2: advection Eq. 12, moments Eqs. 7-10,
  * lagged force Eq. 15, Ut Eq. 18, f^eq Eq. 19, dPi Eq. 16, dN Eq. 17, BGK
- * Eqs. 6, 11; App. B walls): two launches per step (ghost rows, update),
- * asynchronous on the grid's stream.  Runs of more than 21 steps replay a
+ * Eqs. 6, 11; App. B walls): one launch per step, which also fills the
+ * ghost rows the next step reads (a second launch fills the current ones
+ * after a new state or case), asynchronous on the grid's stream.  Runs of more than 21 steps replay a
  * CUDA graph of 10 steps (rebuilt when the case changes; bitwise the plain
  * launches; plain launches on a stream that cannot be captured). */
 clbm_status clbm3_step(clbm3_handle h, long long n);

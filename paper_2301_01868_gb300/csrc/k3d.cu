@@ -3,8 +3,9 @@
 //
 // Layout: deviations sigma_a = N'_a - ref_a(i) in the storage type, one
 // plane per population of (n1 + 2H) x n2 x n3 values, rows 0..H-1 and
-// n1+H..n1+2H-1 the ghost rows of App. B (filled before every update by
-// k3_boundary from the rows inside and the last collision's wall moments),
+// n1+H..n1+2H-1 the ghost rows of App. B (written by the update itself for
+// the buffer it writes, from the mirrored cells' new values and moments;
+// by k3_boundary, from the stored state, after a new state or case),
 // q^2 and q^3 periodic by index wrap.  The geometry of a row (the grids are
 // invariant along q^2 and q^3) is evaluated once in FP64 (k3_geometry,
 // k3_reference) and condensed into a per-row table in the compute type
@@ -250,6 +251,43 @@ __global__ void __launch_bounds__(TB) k3_boundary(Args3 A, S* __restrict__ st) {
     }
 }
 
+// The ghost populations of depth m of one wall in column jk of the buffer
+// the update writes, from the mirrored fluid cell's new values (its row is
+// m, or n1 + 1 - m at the high wall) and moments -- what k3_boundary
+// computes from the stored state, with the same arithmetic, so that the
+// update leaves the next step's ghost rows filled.  own: the cell's offset
+// in its population plane.  The values were just stored by this thread and
+// are read back through the coherent path.
+template <typename S, typename C>
+__device__ __forceinline__ void ghost_column(const Args3& A, int wall, int m, int jk, unsigned own, C rho,
+                                             C u2, C u3) {
+    const int n23 = A.n2 * A.n3;
+    const int gi = wall == 0 ? 1 - m : A.n1 + m;           // ghost row (1-based)
+    const int mi = wall == 0 ? m : A.n1 + 1 - m;           // mirrored fluid row
+    const bool moving = (wall == 0 ? A.bc_lo : A.bc_hi) == CLBM_BC_MOVING;
+    const C U0 = C(wall == 0 ? A.U0_lo : A.U0_hi);
+    const double* g = A.geo + (size_t)(mi - 1) * Geo3::S;
+    const C coef = C(2.0 / T0) * C(g[Geo3::J]) * rho;
+    const S* src = (const S*)A.dst + own;
+    S* dst = (S*)A.dst + (size_t)(gi - 1 + H) * n23 + jk;
+    const size_t pl = (size_t)A.plane;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int c1 = c1_3(a);
+        if (wall == 0 ? c1 < m : c1 > -m) continue;
+        const int h = hat3(a);
+        C v;
+        if (moving) {
+            v = Store<S>::lds(src + (size_t)h * pl) +
+                coef * C(w3(h)) * (C(c2_3(h)) * (U0 - u2) + C(c3_3(h)) * (C(0) - u3));
+        } else {
+            const int b = opp3(a);
+            v = Store<S>::lds(src + (size_t)b * pl) + C(g[Geo3::REF + b] - g[Geo3::REF + h]);
+        }
+        Store<S>::st(dst + (size_t)a * pl, v);
+    }
+}
+
 template <typename C>
 __device__ __forceinline__ C ldt(const C* p) { return *p; }
 
@@ -467,6 +505,10 @@ __global__ void __launch_bounds__(TB, MINB)
         wall_ptr<C>(A.wall, 1, 1, m, n23)[jk] = V2;
         wall_ptr<C>(A.wall, 2, 1, m, n23)[jk] = V3;
     }
+    // and the ghost rows of the buffer written, which this cell mirrors
+    // (a block is one row: the branch is uniform)
+    if (i <= H) ghost_column<S, C>(A, 0, i, jk, own, rho, V2, V3);
+    if (i > A.n1 - H) ghost_column<S, C>(A, 1, A.n1 + 1 - i, jk, own, rho, V2, V3);
 }
 
 // State conversions between FP64 N' ([a][cell]) and stored deviations.
@@ -610,7 +652,7 @@ struct clbm3_grid {
     bool have_case;
     long long t;
     std::vector<double> hedges;
-    // CUDA graph of GRAPH3_STEPS time steps (ghost rows + update each; an
+    // CUDA graph of GRAPH3_STEPS time steps (one update launch each; an
     // even count, so cur ends where it started), keyed by the launch
     // arguments of its first step
     cudaGraph_t graph;
@@ -618,6 +660,7 @@ struct clbm3_grid {
     Args3 gargs;
     bool graphs_off;         // capture failed once (e.g. the legacy default stream)
     int kernel;              // update: 0 automatic, 1 pulled pairs in registers, 2 in shared memory
+    bool ghosts_ok;          // the current buffer's ghost rows are filled (the update fills the next one's)
 };
 
 namespace k3api {
@@ -714,7 +757,6 @@ constexpr int GRAPH3_STEPS = 10;
 // One time step with plain launches.
 void step3_plain(clbm3_grid* g) {
     const Args3 A = args(g);
-    launch_boundary(g, A);
     launch_cells<false>(g, A, nullptr, nullptr);
     g->cur ^= 1;
     g->t++;
@@ -742,7 +784,6 @@ void capture3(clbm3_grid* g) {
     const Args3 first = args(g);
     for (int k = 0; k < GRAPH3_STEPS; ++k) {
         const Args3 A = args(g);
-        launch_boundary(g, A);
         launch_cells<false>(g, A, nullptr, nullptr);
         g->cur ^= 1;
     }
@@ -891,6 +932,7 @@ clbm_status clbm3_set_case(clbm3_handle g, const clbm3_case* c) {
     CK3(cudaGetLastError());
     CK3(cudaStreamSynchronize(g->stream));
     g->t = 0;
+    g->ghosts_ok = false;
     return CLBM_OK;
 }
 
@@ -934,6 +976,7 @@ clbm_status clbm3_set_state(clbm3_handle g, const double* Np, const double* rho,
     });
     CK3(cudaGetLastError());
     CK3(cudaStreamSynchronize(g->stream));
+    g->ghosts_ok = false;
     return CLBM_OK;
 }
 
@@ -971,6 +1014,7 @@ clbm_status clbm3_set_equilibrium(clbm3_handle g, const double* rho, const doubl
     CK3(cudaGetLastError());
     CK3(cudaStreamSynchronize(g->stream));
     g->t = 0;
+    g->ghosts_ok = false;
     return CLBM_OK;
 }
 
@@ -1013,6 +1057,7 @@ clbm_status clbm3_restore(clbm3_handle g, const void* buf) {
     CK3(cudaMemcpyAsync(g->wall, p + sbb, wb, cudaMemcpyHostToDevice, g->stream));
     CK3(cudaStreamSynchronize(g->stream));
     g->t = h.t;
+    g->ghosts_ok = false;
     return CLBM_OK;
 }
 
@@ -1042,6 +1087,13 @@ clbm_status clbm3_step(clbm3_handle g, long long n) {
     if (n < 0) return fail3(CLBM_EINVAL, "n < 0");
     if (!g->have_case) return fail3(CLBM_EINVAL, "call clbm3_set_case first");
     CK3(cudaSetDevice(g->device));
+    // the update fills the ghost rows of the buffer it writes; those of the
+    // current buffer come from the boundary kernel after a new state or case
+    // (before any replay: a graph holds update launches only)
+    if (n > 0 && !g->ghosts_ok) {
+        launch_boundary(g, args(g));
+        g->ghosts_ok = true;
+    }
     long long s = 0;
     // long runs replay a captured graph (one host call per GRAPH3_STEPS
     // steps); two plain steps first set the kernels up and bring cur back
