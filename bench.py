@@ -712,7 +712,7 @@ def cpu_baseline_3d(wl, target_s=10.0):
 def three_d_record(wl, steps, warmup, chunk, kernel=0, cpu=False):
     """The D3Q39 update on an extruded annulus, timed like the main line
     (chunk time steps per bench step, CUDA events on the grid's stream);
-    roofline on the whole step (ghost rows + update launches)."""
+    roofline on the whole step (one update launch, ghost rows included)."""
     import torch
     from paper_2301_01868_gb300 import clbm
     prec, n1, n2, n3, e, dx, tau, U0 = annulus3d(wl)
@@ -755,8 +755,8 @@ def three_d_record(wl, steps, warmup, chunk, kernel=0, cpu=False):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src + " (hbm_gbs)",
                         "algorithmic_bytes_per_launch": bytes_per_step,
-                        "kernel_ms_avg": ms / nsteps, "timed": "whole time step: ghost-row and update launches"},
-           "gpu_launches": 2 * nsteps, "clocks": ck, "mass_after": tot[0]}
+                        "kernel_ms_avg": ms / nsteps, "timed": "whole time step (the update, which also fills the next step's ghost rows)"},
+           "gpu_launches": nsteps, "clocks": ck, "mass_after": tot[0]}
     g.close()
     if cpu:
         out["cpu_baseline"] = cpu_baseline_3d(wl)
