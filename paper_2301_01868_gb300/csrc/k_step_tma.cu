@@ -756,14 +756,14 @@ struct RunTile {
 // nsteps time steps of the pipelined update in one launch.  The tiles of
 // steps 0, 1, ..., nsteps - 1 form one sequence (step by step, band-major
 // within a step); each CTA's producer takes the next one from a counter in
-// global memory, so all CTAs work on neighbouring tiles as in a single-step
-// launch (a static share per CTA lets them drift apart over the steps and
-// spread their reads: 0.145 ms per step against 0.116 on the 1024 x 4096
-// annulus), and the first bands of a step are updated while the last bands
-// of the step before are still in flight: a launch gap, ramp-up and tail
-// once per run instead of once per step.  Step s reads buffer src ^ (s & 1)
-// and writes the other; CPT as in ws_pipeline.  next: the run's counter
-// (zero at launch).
+// global memory (prog[gridDim.x], zeroed before the launch), so that the
+// CTAs keep to neighbouring tiles as in a single-step launch, and the first
+// bands of a step are updated while the last bands of the step before are
+// still in flight: a launch gap, ramp-up and tail once per run instead of
+// once per step.  Step s reads buffer src ^ (s & 1) and writes the other;
+// CPT as in ws_pipeline; period: tiles between two progress publications.
+// 16-bit storage (issue-bound) gains from it; FP32 storage (HBM-bound) ran
+// slower than a launch per step however the tiles were shared out.
 template <int Q, typename S, typename C, int CPT>
 __global__ void __launch_bounds__((PipeGeom<Q, S, CPT, CPT == 2 ? PAIR_TR : 0>::NTHREADS), 1)
     k_fused_ws_run(const __grid_constant__ TmaMaps maps, const StepArgs a, int src, int nsteps,
