@@ -881,6 +881,17 @@ def batch_requests(n, seed=20230105):
     return out
 
 
+def batch_selection(n, select="first"):
+    """The lattices of a batched record: the first n of the seeded
+    configuration, or ("smallest") its n smallest of 512, to time and profile
+    the small lattices' share."""
+    if select == "smallest":
+        return sorted(batch_requests(512), key=lambda r: r.n1 * r.n2)[:n]
+    if select != "first":
+        raise ValueError("select must be 'first' or 'smallest'")
+    return batch_requests(n)
+
+
 def batch_record(n_lattices=512, steps=5000, warmup=3, baseline_steps=20, verbose=False, select="first"):
     """The batched form against per-lattice launches on the same lattices:
     MLUPS over all lattices for `steps` timed steps after warm-up (the
@@ -893,10 +904,7 @@ def batch_record(n_lattices=512, steps=5000, warmup=3, baseline_steps=20, verbos
     from paper_2301_01868_gb300 import clbm, serve
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    if select == "smallest":   # the n smallest of the configured 512 (profiling their share)
-        reqs = sorted(batch_requests(512), key=lambda r: r.n1 * r.n2)[:n_lattices]
-    else:
-        reqs = batch_requests(n_lattices)
+    reqs = batch_selection(n_lattices, select)
     t0 = time.perf_counter()
     grids = [serve.build_grid(r, clbm.FP32, stream) for r in reqs]
     setup_s = time.perf_counter() - t0
