@@ -11,7 +11,7 @@ struct BatchGrid {
     const void* tab;        // per-row coefficients (compute type)
     void* wall_rho;
     void* wall_ut2;
-    const double* ghost;
+    const void* ghost;      // compute type
     const double* geo;
     double* prev;           // Ut snapshot of the residual
     StepScalars k;

@@ -521,8 +521,8 @@ __device__ __forceinline__ void store_periodic(S* __restrict__ rowp, int j, int 
 // correction (2/T0) w J rho c^2 (U0^2 - Ut^2) of the mirrored node, whose
 // per-direction factor is coef.
 template <typename C>
-__device__ __forceinline__ C ghost_value(C x, const double* __restrict__ gt, C rho, C U0, C ut2) {
-    return x + (C(gt[0]) + C(gt[1]) * rho * (U0 - ut2));
+__device__ __forceinline__ C ghost_value(C x, const C* __restrict__ gt, C rho, C U0, C ut2) {
+    return x + (gt[0] + gt[1] * rho * (U0 - ut2));
 }
 
 // Periodic ghost column of interior column j when a row has at least 2 GC
@@ -556,7 +556,7 @@ template <int Q, typename S>
 struct EdgeFill {
     using C = typename Store<S>::C;
     S* st;                   // state buffer being written (row 0, column 0)
-    const double* ghost;     // [2][H][Q] x {offset, coefficient}
+    const C* ghost;          // [2][H][Q] x {offset, coefficient}, compute type
     long long plane;
     int ld, n1, n2, bc_lo, bc_hi;
     C U0_lo, U0_hi;
@@ -582,7 +582,7 @@ struct EdgeFill {
                 const int k = i + 1;
                 const int a = bc_lo == 0 ? opp_of(b) : hat_of(b);
                 if (c1_of(a) >= k) {
-                    const double* gt = ghost + 2 * (((k - 1) * Q + a) * gcols + (gcols > 1 ? j : 0));
+                    const C* gt = ghost + 2 * (((k - 1) * Q + a) * gcols + (gcols > 1 ? j : 0));
                     store_periodic<S, C>(st + a * plane + (long long)(H - k) * ld, j, n2,
                                          ghost_value<C>(v, gt, rho, U0_lo, ut2));
                 }
@@ -591,7 +591,7 @@ struct EdgeFill {
                 const int k = n1 - i;
                 const int a = bc_hi == 0 ? opp_of(b) : hat_of(b);
                 if (c1_of(a) <= -k) {
-                    const double* gt = ghost + 2 * (((H + k - 1) * Q + a) * gcols + (gcols > 1 ? j : 0));
+                    const C* gt = ghost + 2 * (((H + k - 1) * Q + a) * gcols + (gcols > 1 ? j : 0));
                     store_periodic<S, C>(st + a * plane + (long long)(n1 + H + k - 1) * ld, j, n2,
                                          ghost_value<C>(v, gt, rho, U0_hi, ut2));
                 }

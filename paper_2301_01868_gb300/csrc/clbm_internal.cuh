@@ -112,7 +112,7 @@ struct StepArgs {
     const void* tab;        // per-row coefficients, compute type
     void* wall_rho;         // [2][h][n2] compute type
     void* wall_ut2;
-    const double* ghost;    // [2][h][Q][2]
+    const void* ghost;      // [2][h][Q][2], compute type
     int n1, n2, ld, h;
     long long plane;        // elements per population plane = (n1+2h)*ld
     double tau, rho0, g1, g2, U0_lo, U0_hi;
@@ -151,7 +151,7 @@ constexpr int NRED = 10;  // reduced quantities per block
 void launch_geometry(int Q, const double* pos, int n1, int ncol, double dx, int moments,
                      double* geo, cudaStream_t stream);
 void launch_reference(int Q, double* geo, int count, double rho0, cudaStream_t stream);
-void launch_tables(int Q, int prec, const double* geo, void* tab, double* ghost, int n1, int n2,
+void launch_tables(int Q, int prec, const double* geo, void* tab, void* ghost, int n1, int n2,
                    int ncol, int bc_lo, int bc_hi, cudaStream_t stream);
 void launch_boundary(int Q, int prec, const StepArgs& a, void* state, cudaStream_t stream);
 void launch_step(int Q, int prec, const StepArgs& a, cudaStream_t stream);

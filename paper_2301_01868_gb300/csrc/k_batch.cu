@@ -51,7 +51,7 @@ __device__ __forceinline__ void batch_cell(const BatchGrid& g, int src, int i, i
         for (int al = 0; al < Q; ++al) put(al, out[al]);
     }
     if (EdgeFill<Q, S>::needed(i, g.n1, g.n2)) {
-        const EdgeFill<Q, S> ef{(S*)g.phys[src ^ 1], g.ghost, g.plane, g.ld, g.n1, g.n2, g.bc_lo,
+        const EdgeFill<Q, S> ef{(S*)g.phys[src ^ 1], (const C*)g.ghost, g.plane, g.ld, g.n1, g.n2, g.bc_lo,
                                 g.bc_hi, C(g.U0_lo), C(g.U0_hi), g.n2 < 2 * GC, 1};
         ef.fill(i, j, dst, g.plane, c.rho, c.Ut2);
     }
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128) k_batch_boundary(const BatchGrid* __restr
                 const int c1 = c1_of(al);
                 if (wall == 0 ? (c1 < k) : (c1 > -k)) continue;
                 const int b = bc == 0 ? opp_of(al) : hat_of(al);
-                const double* gt = g.ghost + 2 * ((wall * H + (k - 1)) * Q + al);
+                const C* gt = (const C*)g.ghost + 2 * ((wall * H + (k - 1)) * Q + al);
                 const C x = C(Store<S>::ld(st + b * P + (long long)mr * g.ld + j + GC));
                 store_periodic<S, C>(st + al * P + (long long)gr * g.ld, j, g.n2,
                                      ghost_value<C>(x, gt, wr, U0, wu));

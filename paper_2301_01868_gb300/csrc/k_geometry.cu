@@ -251,9 +251,11 @@ __global__ void k_tables_cell(const double* __restrict__ geo, C* __restrict__ ta
 // unless the grid is general): the stored ghost value of direction a at
 // depth k is sigma_b(m) + offset + coefficient * rho (U0 - Ut^2) with
 // b = a* (no-slip) or a-hat (moving wall) and m the mirrored row of the same
-// column; the offset converts between the two cells' references.
-template <int Q>
-__global__ void k_ghost(const double* __restrict__ geo, double* __restrict__ ghost, int n1, int ncol,
+// column; the offset converts between the two cells' references.  Stored in
+// the compute type C (formed in FP64, rounded once here rather than at every
+// use by the update's ghost fill).
+template <int Q, typename C>
+__global__ void k_ghost(const double* __restrict__ geo, C* __restrict__ ghost, int n1, int ncol,
                         int bc_lo, int bc_hi) {
     constexpr int H = Lat<Q>::H;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -269,8 +271,8 @@ __global__ void k_ghost(const double* __restrict__ geo, double* __restrict__ gho
     if (bc == 1)  // App. B moving wall, reading (2/T0) w J rho c^2 (U0^2 - Ut^2)
         coef = 2.0 / Lat<Q>::T0 * Lat<Q>::w(b) *
                geo[((size_t)(m - 1) * ncol + jc) * Geo::stride(Q) + Geo::J] * c2_of(b);
-    ghost[2 * t] = off;
-    ghost[2 * t + 1] = coef;
+    ghost[2 * t] = C(off);
+    ghost[2 * t + 1] = C(coef);
 }
 
 }  // namespace
@@ -289,7 +291,7 @@ void launch_reference(int Q, double* geo, int count, double rho0, cudaStream_t s
 }
 
 template <int Q>
-static void tables(int prec, const double* geo, void* tab, double* ghost, int n1, int n2, int ncol,
+static void tables(int prec, const double* geo, void* tab, void* ghost, int n1, int n2, int ncol,
                    int bc_lo, int bc_hi, cudaStream_t s) {
     constexpr int H = Lat<Q>::H;
     if (ncol > 1) {
@@ -302,10 +304,11 @@ static void tables(int prec, const double* geo, void* tab, double* ghost, int n1
         else k_tables<Q, float><<<g, b, 0, s>>>(geo, (float*)tab, n1);
     }
     const int nt = 2 * H * Q * ncol;
-    k_ghost<Q><<<(nt + 127) / 128, 128, 0, s>>>(geo, ghost, n1, ncol, bc_lo, bc_hi);
+    if (prec == 0) k_ghost<Q, double><<<(nt + 127) / 128, 128, 0, s>>>(geo, (double*)ghost, n1, ncol, bc_lo, bc_hi);
+    else k_ghost<Q, float><<<(nt + 127) / 128, 128, 0, s>>>(geo, (float*)ghost, n1, ncol, bc_lo, bc_hi);
 }
 
-void launch_tables(int Q, int prec, const double* geo, void* tab, double* ghost, int n1, int n2,
+void launch_tables(int Q, int prec, const double* geo, void* tab, void* ghost, int n1, int n2,
                    int ncol, int bc_lo, int bc_hi, cudaStream_t s) {
     if (Q == 9) tables<9>(prec, geo, tab, ghost, n1, n2, ncol, bc_lo, bc_hi, s);
     else tables<21>(prec, geo, tab, ghost, n1, n2, ncol, bc_lo, bc_hi, s);

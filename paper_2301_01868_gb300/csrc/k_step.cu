@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(128, ITER ? 2 : (GEN ? 3 : 4)) k_fused_step(co
         for (int al = 0; al < Q; ++al) put(al, out[al]);
     }
     if (EdgeFill<Q, S>::needed(i, a.n1, a.n2)) {
-        const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo, a.bc_hi,
+        const EdgeFill<Q, S> ef{(S*)a.dst, (const C*)a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo, a.bc_hi,
                                 C(a.U0_lo), C(a.U0_hi), a.n2 < 2 * GC, a.ncol};
         ef.fill(i, j, dst, a.plane, c.rho, c.Ut2);
     }
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128) k_boundary(const StepArgs a, S* __restric
             const int c1 = c1_of(al);
             if (wall == 0 ? (c1 < k) : (c1 > -k)) continue;
             const int b = bc == 0 ? opp_of(al) : hat_of(al);
-            const double* gt = a.ghost + 2 * (((wall * H + (k - 1)) * Q + al) * a.ncol + (a.ncol > 1 ? j : 0));
+            const C* gt = (const C*)a.ghost + 2 * (((wall * H + (k - 1)) * Q + al) * a.ncol + (a.ncol > 1 ? j : 0));
             const C x = C(Store<S>::ld(st + b * P + (long long)mr * a.ld + j + GC));
             store_periodic<S, C>(st + al * P + (long long)gr * a.ld, j, a.n2,
                                  ghost_value<C>(x, gt, wr, U0, wu));

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__((TileGeom<Q, S>::NT), 1)
                 Store<S>::st(out + al * (G::TR * G::TJ), v);
             });
             if (i < H || i >= a.n1 - H) {
-                const EdgeFill<Q, S> ef{(S*)a.dst, a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo,
+                const EdgeFill<Q, S> ef{(S*)a.dst, (const typename Store<S>::C*)a.ghost, a.plane, a.ld, a.n1, a.n2, a.bc_lo,
                                         a.bc_hi, C(a.U0_lo), C(a.U0_hi), false, 1};
                 ef.fill(i, j, out, G::TR * G::TJ, c.rho, c.Ut2);
             }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__((TileGeom<Q, S>::NT), 1)
 template <typename S>
 struct WsLattice {
     S* dst;                 // state buffer written (row 0, column 0)
-    const double* ghost;
+    const void* ghost;        // compute type
     void* wall_rho;
     void* wall_ut2;
     long long plane;
@@ -326,7 +326,7 @@ __device__ __forceinline__ void ws_update_cell_tb(const WsLattice<S>& L, const C
         if (dw != 0) StStream<S>::str(dst + (al * pl + dw), v);
     });
     if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
-        const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
+        const EdgeFill<Q, S> ef{L.dst, (const typename Store<S>::C*)L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
                                 C(L.U0_lo), C(L.U0_hi), L.n2 < 2 * GC, gcols};
         ef.fill(i, j, dst, L.plane, c.rho, c.Ut2);
     }
@@ -574,7 +574,7 @@ __device__ __forceinline__ void ws_update_pair(const WsLattice<S>& L, const Cons
         if (dwb != 0) __stcs(dst + (al * pl + 1 + dwb), S(v.v.y));
     });
     if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
-        const EdgeFill<Q, S> ef{L.dst, L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
+        const EdgeFill<Q, S> ef{L.dst, (const typename Store<S>::C*)L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
                                 float(L.U0_lo), float(L.U0_hi), L.n2 < 2 * GC, 1};
         ef.fill(i, j, dst, L.plane, c.rho.v.x, c.Ut2.v.x);
         if (both) ef.fill(i, j + 1, dst + 1, L.plane, c.rho.v.y, c.Ut2.v.y);
