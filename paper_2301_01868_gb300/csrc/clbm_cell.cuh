@@ -568,6 +568,12 @@ struct EdgeFill {
     }
 
     __device__ __noinline__ void fill(int i, int j, const S* vp, long long vstride, C rho, C ut2) const {
+        fill_inline(i, j, vp, vstride, rho, ut2);
+    }
+    // the same in line, for the kernels whose registers hold it without
+    // spilling (the one-cell pipeline: no out-of-line call on its wall rows)
+    __device__ __forceinline__ void fill_inline(int i, int j, const S* vp, long long vstride, C rho,
+                                                C ut2) const {
         constexpr int H = Lat<Q>::H;
         // all read-backs first (independent loads in flight together), then
         // the stores; unrolled so that every direction's maps fold

@@ -328,7 +328,7 @@ __device__ __forceinline__ void ws_update_cell_tb(const WsLattice<S>& L, const C
     if (EdgeFill<Q, S>::needed(i, L.n1, L.n2)) {
         const EdgeFill<Q, S> ef{L.dst, (const typename Store<S>::C*)L.ghost, L.plane, L.ld, L.n1, L.n2, L.bc_lo, L.bc_hi,
                                 C(L.U0_lo), C(L.U0_hi), L.n2 < 2 * GC, gcols};
-        ef.fill(i, j, dst, L.plane, c.rho, c.Ut2);
+        ef.fill_inline(i, j, dst, L.plane, c.rho, c.Ut2);
     }
     if (i < H) {
         const int idx = i * L.n2 + j;
